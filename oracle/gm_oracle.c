@@ -1,0 +1,592 @@
+/*
+ * gm_oracle.c -- plain, slow, single-threaded FP64 CPU oracle of the
+ * adaptive Genz-Malik quadrature of "Adaptive Multidimensional Quadrature on
+ * Multi-GPU Systems" (arXiv 2511.01573).
+ *
+ * TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg are its only users.  The product path never
+ * loads it.  Nothing here is shared with the CUDA library.
+ *
+ * What each part follows:
+ *   - weighted-sum rule                      paper Sec. 2 (first display)
+ *   - fully symmetric Genz-Malik rule        paper Sec. 2, ref. [genz-malik];
+ *     degree 7 with an embedded degree-5 rule; generators lambda2 = sqrt(9/70),
+ *     lambda3 = lambda4 = sqrt(9/10), lambda5 = sqrt(9/19) and the class
+ *     weights of Genz & Malik (1980).  The paper calls the rule "9-order";
+ *     the node count 2^d + 2d^2 + 2d + 1 is the degree-7 rule's.
+ *   - local error estimate                   paper Sec. 2 (error estimator):
+ *     |I7 - I5| from the embedded rule on the same nodes.
+ *   - split axis by fourth differences       paper Sec. 2 (last paragraph)
+ *   - breadth-first refine-all loop          paper Sec. 3, Fig. 1a: evaluate
+ *     all regions, check global convergence, classify (retire negligible
+ *     regions), bisect the rest along their axis, repeat.
+ *   - initial uniform partition              paper Sec. 3
+ *   - numerical guards                       paper Sec. 3 (round-off guards)
+ *   - stopping criterion eps <= max(1e-16, |I| tau_rel)   paper Sec. 4
+ *   - test integrands f1..f7                 paper Sec. 4 (integrand list)
+ *
+ * Readings where the paper is silent (classifier form, guard form, tie
+ * rules, partition count, summation order, child order) are stated at the
+ * function that implements each one.
+ *
+ * Compile with -ffp-contract=off: every product and sum below is rounded
+ * separately, and fma() appears only where the definition asks for it.
+ */
+#include "gm_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Rule constants (Genz & Malik 1980, as cited in paper Sec. 2).            */
+/* ------------------------------------------------------------------------ */
+
+int64_t or_num_nodes(int d) {
+  /* centre + 2d (lambda2) + 2d (lambda3) + 2d(d-1) (lambda4 pairs) + 2^d */
+  return ((int64_t)1 << d) + 2 * (int64_t)d * d + 2 * (int64_t)d + 1;
+}
+
+void or_lambdas(double lam[4]) {
+  lam[0] = sqrt(9.0 / 70.0); /* lambda2 */
+  lam[1] = sqrt(9.0 / 10.0); /* lambda3 */
+  lam[2] = sqrt(9.0 / 10.0); /* lambda4 */
+  lam[3] = sqrt(9.0 / 19.0); /* lambda5 */
+}
+
+/* Weights normalised to a unit-volume region (they sum to 1 over all nodes;
+ * the rule value is vol * sum_c w_c S_c). */
+void or_weights(int d, double w7[5], double w5[5]) {
+  double dd = (double)d;
+  w7[0] = (12824.0 - 9120.0 * dd + 400.0 * dd * dd) / 19683.0;
+  w7[1] = 980.0 / 6561.0;
+  w7[2] = (1820.0 - 400.0 * dd) / 19683.0;
+  w7[3] = 200.0 / 19683.0;
+  w7[4] = 6859.0 / (19683.0 * ldexp(1.0, d));
+  w5[0] = (729.0 - 950.0 * dd + 50.0 * dd * dd) / 729.0;
+  w5[1] = 245.0 / 486.0;
+  w5[2] = (265.0 - 100.0 * dd) / 1458.0;
+  w5[3] = 25.0 / 729.0;
+  w5[4] = 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Integrands (paper Sec. 4 list; Genz families).                           */
+/* ------------------------------------------------------------------------ */
+
+double or_family_eval(const double *x, int d, const void *ctx) {
+  const or_family *F = (const or_family *)ctx;
+  const double *a = F->a, *u = F->u;
+  int j;
+  double s, t, p;
+  switch (F->family) {
+  case OR_OSCILLATORY: /* cos(2 pi u_1 + sum a_j x_j) */
+    s = 2.0 * M_PI * u[0];
+    for (j = 0; j < d; ++j) s = s + a[j] * x[j];
+    return cos(s);
+  case OR_PRODUCT_PEAK: /* prod_j 1/(a_j^-2 + (x_j-u_j)^2) */
+    p = 1.0;
+    for (j = 0; j < d; ++j) {
+      t = x[j] - u[j];
+      p = p * (1.0 / (1.0 / (a[j] * a[j]) + t * t));
+    }
+    return p;
+  case OR_CORNER_PEAK: /* (1 + sum a_j x_j)^-(d+1) */
+    s = 1.0;
+    for (j = 0; j < d; ++j) s = s + a[j] * x[j];
+    return pow(s, -(double)(d + 1));
+  case OR_GAUSSIAN: /* exp(-sum a_j^2 (x_j-u_j)^2) */
+    s = 0.0;
+    for (j = 0; j < d; ++j) {
+      t = x[j] - u[j];
+      s = s + (a[j] * a[j]) * (t * t);
+    }
+    return exp(-s);
+  case OR_C0: /* exp(-sum a_j |x_j-u_j|) */
+    s = 0.0;
+    for (j = 0; j < d; ++j) s = s + a[j] * fabs(x[j] - u[j]);
+    return exp(-s);
+  case OR_DISCONTINUOUS: /* 0 if any x_j > u_j, else exp(sum a_j x_j) */
+    s = 0.0;
+    for (j = 0; j < d; ++j) {
+      if (x[j] > u[j]) return 0.0;
+      s = s + a[j] * x[j];
+    }
+    return exp(s);
+  case OR_POLY_SUMSQ11: /* (sum x_j^2)^11 */
+    s = 0.0;
+    for (j = 0; j < d; ++j) s = s + x[j] * x[j];
+    return pow(s, 11.0);
+  default:
+    return NAN;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The rule on one region (paper Sec. 2).                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Node coordinate: x_k = fma(+-lambda, h_k, c_k), one rounding, the same
+ * expression on every implementation so that the nodes agree bit for bit. */
+static double node_coord(double sl, double h, double c) { return fma(sl, h, c); }
+
+/*
+ * Split-axis choice (paper Sec. 2: largest fourth-difference estimate).
+ *   D_k = | f(c+l2 e_k) + f(c-l2 e_k) - 2 f(c)
+ *           - (l2^2/l3^2) (f(c+l3 e_k) + f(c-l3 e_k) - 2 f(c)) |,  l2^2/l3^2 = 1/7
+ * axis = lowest k attaining max D_k.  If max D_k <= 1e-14 |f(c)| + 1e-300
+ * (every difference at round-off level) the axis with the largest h_k is
+ * taken instead (lowest index on ties).  A choice is flagged as a near-tie
+ * when the runner-up is within 1e-12 D_max + 1e-13 (scale_max + scale_2nd)
+ * of D_max, or D_max is within that band of the flat threshold, where
+ * scale_k = sum of the magnitudes of the node values entering D_k.
+ */
+void or_rule(int d, const double *c, const double *h, or_integrand f,
+             const void *ctx, double *D, or_rule_out *out) {
+  double lam[4], w7[5], w5[5];
+  double *x = (double *)malloc(sizeof(double) * (size_t)d);
+  double *Dk = D ? D : (double *)malloc(sizeof(double) * (size_t)d);
+  double *Sk = (double *)malloc(sizeof(double) * (size_t)d);
+  const double r = 1.0 / 7.0; /* lambda2^2 / lambda3^2 */
+  double S[5] = {0, 0, 0, 0, 0}, A[5] = {0, 0, 0, 0, 0};
+  double vol = 1.0, f0, v;
+  int k, j;
+  int64_t m, nm;
+
+  or_lambdas(lam);
+  or_weights(d, w7, w5);
+  for (k = 0; k < d; ++k) vol = vol * (2.0 * h[k]);
+  for (k = 0; k < d; ++k) x[k] = c[k];
+
+  /* class 1: the centre */
+  f0 = f(x, d, ctx);
+  S[0] = f0;
+  A[0] = fabs(f0);
+
+  /* classes 2 and 3: +-lambda2 e_k and +-lambda3 e_k */
+  for (k = 0; k < d; ++k) {
+    double f2p, f2m, f3p, f3m;
+    x[k] = node_coord(lam[0], h[k], c[k]);
+    f2p = f(x, d, ctx);
+    x[k] = node_coord(-lam[0], h[k], c[k]);
+    f2m = f(x, d, ctx);
+    x[k] = node_coord(lam[1], h[k], c[k]);
+    f3p = f(x, d, ctx);
+    x[k] = node_coord(-lam[1], h[k], c[k]);
+    f3m = f(x, d, ctx);
+    x[k] = c[k];
+    S[1] = S[1] + f2p;
+    S[1] = S[1] + f2m;
+    S[2] = S[2] + f3p;
+    S[2] = S[2] + f3m;
+    A[1] = A[1] + fabs(f2p) + fabs(f2m);
+    A[2] = A[2] + fabs(f3p) + fabs(f3m);
+    Dk[k] = fabs((f2p + f2m - 2.0 * f0) - r * (f3p + f3m - 2.0 * f0));
+    Sk[k] = fabs(f2p) + fabs(f2m) + fabs(f3p) + fabs(f3m) + 4.0 * fabs(f0);
+  }
+
+  /* class 4: +-lambda4 e_j +-lambda4 e_k, j < k */
+  for (j = 0; j < d; ++j) {
+    for (k = j + 1; k < d; ++k) {
+      int sj, sk;
+      for (sj = 0; sj < 2; ++sj) {
+        for (sk = 0; sk < 2; ++sk) {
+          x[j] = node_coord(sj ? -lam[2] : lam[2], h[j], c[j]);
+          x[k] = node_coord(sk ? -lam[2] : lam[2], h[k], c[k]);
+          v = f(x, d, ctx);
+          S[3] = S[3] + v;
+          A[3] = A[3] + fabs(v);
+        }
+      }
+      x[j] = c[j];
+      x[k] = c[k];
+    }
+  }
+
+  /* class 5: (+-lambda5, ..., +-lambda5), all 2^d sign patterns; bit k of m
+   * set means the minus sign on axis k */
+  nm = (int64_t)1 << d;
+  for (m = 0; m < nm; ++m) {
+    for (k = 0; k < d; ++k)
+      x[k] = node_coord(((m >> k) & 1) ? -lam[3] : lam[3], h[k], c[k]);
+    v = f(x, d, ctx);
+    S[4] = S[4] + v;
+    A[4] = A[4] + fabs(v);
+  }
+
+  /* rule values (weighted sums of class sums, scaled by the volume) */
+  out->i7 = vol * (w7[0] * S[0] + w7[1] * S[1] + w7[2] * S[2] + w7[3] * S[3] +
+                   w7[4] * S[4]);
+  out->i5 = vol * (w5[0] * S[0] + w5[1] * S[1] + w5[2] * S[2] + w5[3] * S[3]);
+  out->err = fabs(out->i7 - out->i5);
+  for (k = 0; k < 5; ++k) {
+    out->s[k] = S[k];
+    out->sabs[k] = A[k];
+  }
+  out->vol = vol;
+  out->f0 = f0;
+
+  /* split axis */
+  {
+    int best = 0, second = -1, hb = 0;
+    double flat_thr = 1e-14 * fabs(f0) + 1e-300, band;
+    for (k = 1; k < d; ++k)
+      if (Dk[k] > Dk[best]) best = k;
+    for (k = 0; k < d; ++k)
+      if (k != best && (second < 0 || Dk[k] > Dk[second])) second = k;
+    band = 1e-12 * Dk[best] + 1e-13 * Sk[best];
+    if (second >= 0) band = band + 1e-13 * Sk[second];
+    out->axis_tie = 0;
+    if (second >= 0 && Dk[best] - Dk[second] <= band) out->axis_tie = 1;
+    if (fabs(Dk[best] - flat_thr) <= band) out->axis_tie = 1;
+    out->flat = Dk[best] <= flat_thr;
+    if (out->flat) {
+      for (k = 1; k < d; ++k)
+        if (h[k] > h[hb]) hb = k;
+      out->axis = hb;
+    } else {
+      out->axis = best;
+    }
+  }
+
+  /* numerical guard: bisection along the axis must change the centre */
+  {
+    int s = out->axis;
+    double hh = 0.5 * h[s];
+    out->split_bad = (hh == 0.0) || (c[s] - hh == c[s]) || (c[s] + hh == c[s]);
+  }
+
+  free(x);
+  free(Sk);
+  if (!D) free(Dk);
+}
+
+void or_rule_regions(const or_family *fam, int64_t n, const double *c,
+                     const double *h, double *i7, double *i5, double *err,
+                     double *vol, int32_t *axis, int32_t *axis_tie,
+                     int32_t *split_bad, double *i7abs) {
+  int64_t r;
+  int d = fam->d;
+  double w7[5], w5[5];
+  or_weights(d, w7, w5);
+  for (r = 0; r < n; ++r) {
+    or_rule_out o;
+    or_rule(d, c + r * d, h + r * d, or_family_eval, fam, NULL, &o);
+    if (i7) i7[r] = o.i7;
+    if (i5) i5[r] = o.i5;
+    if (err) err[r] = o.err;
+    if (vol) vol[r] = o.vol;
+    if (axis) axis[r] = o.axis;
+    if (axis_tie) axis_tie[r] = o.axis_tie;
+    if (split_bad) split_bad[r] = o.split_bad;
+    if (i7abs)
+      i7abs[r] = o.vol * (fabs(w7[0]) * o.sabs[0] + fabs(w7[1]) * o.sabs[1] +
+                          fabs(w7[2]) * o.sabs[2] + fabs(w7[3]) * o.sabs[3] +
+                          fabs(w7[4]) * o.sabs[4]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Global sums.                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Summation order (a reading: the paper fixes none).  The sum of v[0..n) is
+ * the binary tree over the index range zero-padded to the next power of
+ * two: sum(range) = sum(left half) + sum(right half). */
+static double tree_sum(const double *v, int64_t n, int64_t lo, int64_t len) {
+  if (lo >= n) return 0.0;
+  if (len == 1) return v[lo];
+  return tree_sum(v, n, lo, len / 2) + tree_sum(v, n, lo + len / 2, len / 2);
+}
+
+double or_pairwise_sum(const double *v, int64_t n) {
+  int64_t len = 1;
+  if (n <= 0) return 0.0;
+  while (len < n) len *= 2;
+  return tree_sum(v, n, 0, len);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial uniform partition (paper Sec. 3; count is a reading).            */
+/* ------------------------------------------------------------------------ */
+
+/* Largest s >= 1 with s^d <= min(4096, cap). */
+int32_t or_auto_splits(int d, int64_t cap) {
+  int64_t lim = cap < 4096 ? cap : 4096;
+  int32_t s = 1;
+  for (;;) {
+    int64_t p = 1;
+    int k, over = 0;
+    for (k = 0; k < d; ++k) {
+      p *= (s + 1);
+      if (p > lim) {
+        over = 1;
+        break;
+      }
+    }
+    if (over) break;
+    s += 1;
+  }
+  return s;
+}
+
+/* s^d boxes, axis-0 index fastest; along axis k, box i has
+ * h_k = (hi_k - lo_k) / (2 s) and c_k = lo_k + (2 i + 1) h_k. */
+int64_t or_partition(int d, const double *lo, const double *hi, int32_t s,
+                     double *c, double *h) {
+  int64_t n = 1, q;
+  int k;
+  for (k = 0; k < d; ++k) n *= s;
+  for (q = 0; q < n; ++q) {
+    int64_t rem = q;
+    for (k = 0; k < d; ++k) {
+      int64_t i = rem % s;
+      double hk = (hi[k] - lo[k]) / (2.0 * (double)s);
+      rem /= s;
+      h[q * d + k] = hk;
+      c[q * d + k] = lo[k] + (double)(2 * i + 1) * hk;
+    }
+  }
+  return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Classification (paper Sec. 3 heuristic classifier + round-off guards).   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Reading of the classifier ("discard regions whose contribution to the
+ * error is negligible"):
+ *   classifier 0 (volume share): retire r if err_r <= budget * (vol_r / vol_omega),
+ *       budget = max(abs_tol, rel_tol |I|) from this sweep's global estimate;
+ *   classifier 1 (local relative): retire r if err_r <= rel_tol |I7_r|.
+ * Round-off guards (paper Sec. 3): also retire r if err_r <= 50 u |I7_r|
+ * with u = 2^-53, or if bisecting r along its axis is not representable.
+ * Retired values are summed with the pairwise tree over the whole list, a
+ * split region contributing zero.  A decision is counted as a near-tie when
+ * moving err_r by b = 1e-13 scale_r + 1e-12 err_r and the volume-share
+ * threshold by 1e-12 thr_r can change it (scale_r = vol_r sum |w_c| sum |f|
+ * over the class, or |I7_r| when no scale is given): these are the
+ * decisions two correct FP64 implementations may take differently.
+ */
+int64_t or_classify(int d, int64_t n, const double *i7, const double *err,
+                    const double *vol, const int32_t *split_bad,
+                    const double *scale, double vol_omega, double budget,
+                    double rel_tol, int32_t classifier, uint8_t *flags,
+                    double *ret_i, double *ret_e, int64_t *near_ties) {
+  const double u = ldexp(1.0, -53);
+  double *vi = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *ve = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  int64_t r, nsplit = 0, ties = 0;
+  (void)d;
+  for (r = 0; r < n; ++r) {
+    double thr, g, b, bt;
+    int retire, loose, tight;
+    if (classifier == 1)
+      thr = rel_tol * fabs(i7[r]);
+    else
+      thr = budget * (vol[r] / vol_omega);
+    g = 50.0 * u * fabs(i7[r]);
+    retire = (err[r] <= thr) || (err[r] <= g) || split_bad[r];
+    b = 1e-13 * (scale ? scale[r] : fabs(i7[r])) + 1e-12 * err[r];
+    bt = 1e-12 * thr;
+    loose = (err[r] - b <= thr + bt) || (err[r] - b <= g) || split_bad[r];
+    tight = (err[r] + b <= thr - bt) || (err[r] + b <= g) || split_bad[r];
+    if (loose != tight) ties++;
+    flags[r] = retire ? 0 : 1;
+    vi[r] = retire ? i7[r] : 0.0;
+    ve[r] = retire ? err[r] : 0.0;
+    nsplit += retire ? 0 : 1;
+  }
+  *ret_i = or_pairwise_sum(vi, n);
+  *ret_e = or_pairwise_sum(ve, n);
+  if (near_ties) *near_ties = ties;
+  free(vi);
+  free(ve);
+  return nsplit;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bisection with compaction (paper Sec. 3: split along the assigned axis). */
+/* ------------------------------------------------------------------------ */
+
+/* Child order (a reading): left children of the split regions, in input
+ * order, fill [0, n_split); right children fill [n_split, 2 n_split).
+ * Along the axis s: h' = h_s / 2, c' = c_s -+ h'. */
+int64_t or_bisect(int d, int64_t n, const double *c, const double *h,
+                  const int32_t *axis, const uint8_t *flags, double *c_out,
+                  double *h_out) {
+  int64_t r, ns = 0, p = 0;
+  int k;
+  for (r = 0; r < n; ++r) ns += flags[r] ? 1 : 0;
+  for (r = 0; r < n; ++r) {
+    int s;
+    double hh;
+    if (!flags[r]) continue;
+    s = axis[r];
+    hh = 0.5 * h[r * d + s];
+    for (k = 0; k < d; ++k) {
+      c_out[p * d + k] = c[r * d + k];
+      h_out[p * d + k] = h[r * d + k];
+      c_out[(ns + p) * d + k] = c[r * d + k];
+      h_out[(ns + p) * d + k] = h[r * d + k];
+    }
+    c_out[p * d + s] = c[r * d + s] - hh;
+    h_out[p * d + s] = hh;
+    c_out[(ns + p) * d + s] = c[r * d + s] + hh;
+    h_out[(ns + p) * d + s] = hh;
+    p++;
+  }
+  return ns;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The adaptive loop (paper Sec. 3, Fig. 1a; stopping rule paper Sec. 4).   */
+/* ------------------------------------------------------------------------ */
+
+int32_t or_integrate(const or_family *fam, const double *lo, const double *hi,
+                     const or_options *opt, or_result *res, or_trace *trace,
+                     int32_t max_trace) {
+  const int d = fam->d;
+  int64_t cap = opt->max_regions;
+  int32_t s, iters = 0, max_iters = opt->max_iters > 0 ? opt->max_iters : 1000;
+  int64_t n, r, ties_total = 0;
+  double vol_omega = 1.0, I_ret = 0.0, E_ret = 0.0;
+  double *c, *h, *c2, *h2, *i7, *err, *vol, *scl;
+  int32_t *axis, *bad, *atie;
+  uint8_t *flags;
+  int32_t status = 0;
+  int k;
+
+  memset(res, 0, sizeof(*res));
+  if (d < 1 || d > 20 || cap < 1 || !(opt->rel_tol >= 0.0) ||
+      !(opt->abs_tol >= 0.0)) {
+    res->status = -1;
+    return -1;
+  }
+  for (k = 0; k < d; ++k) {
+    if (!(hi[k] > lo[k])) {
+      res->status = -1;
+      return -1;
+    }
+    vol_omega = vol_omega * (hi[k] - lo[k]);
+  }
+  s = opt->init_splits > 0 ? opt->init_splits : or_auto_splits(d, cap);
+  n = 1;
+  for (k = 0; k < d; ++k) n *= s;
+  if (n > cap) {
+    res->status = -1;
+    return -1;
+  }
+
+  c = (double *)malloc(sizeof(double) * (size_t)(cap * d));
+  h = (double *)malloc(sizeof(double) * (size_t)(cap * d));
+  c2 = (double *)malloc(sizeof(double) * (size_t)(cap * d));
+  h2 = (double *)malloc(sizeof(double) * (size_t)(cap * d));
+  i7 = (double *)malloc(sizeof(double) * (size_t)cap);
+  err = (double *)malloc(sizeof(double) * (size_t)cap);
+  vol = (double *)malloc(sizeof(double) * (size_t)cap);
+  scl = (double *)malloc(sizeof(double) * (size_t)cap);
+  axis = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+  bad = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+  atie = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+  flags = (uint8_t *)malloc((size_t)cap);
+  if (!c || !h || !c2 || !h2 || !i7 || !err || !vol || !scl || !axis || !bad ||
+      !atie || !flags) {
+    status = -2;
+    goto done;
+  }
+
+  or_partition(d, lo, hi, s, c, h);
+
+  for (;;) {
+    double I, E, budget, ret_i, ret_e;
+    int64_t nsplit, ties = 0;
+    /* evaluate every active region */
+    or_rule_regions(fam, n, c, h, i7, NULL, err, vol, axis, atie, bad, scl);
+    res->regions_evaluated += n;
+    res->function_evals += n * or_num_nodes(d);
+    iters++;
+    /* global estimates */
+    I = I_ret + or_pairwise_sum(i7, n);
+    E = E_ret + or_pairwise_sum(err, n);
+    res->integral = I;
+    res->error = E;
+    res->final_active = n;
+    budget = fmax(opt->abs_tol, opt->rel_tol * fabs(I));
+    if (trace && iters <= max_trace) {
+      or_trace *t = &trace[iters - 1];
+      t->n = n;
+      t->n_split = -1;
+      t->near_ties = 0;
+      t->I = I;
+      t->E = E;
+      t->I_ret = I_ret;
+      t->E_ret = E_ret;
+      t->budget = budget;
+    }
+    if (!isfinite(I) || !isfinite(E)) {
+      status = -4;
+      break;
+    }
+    if (E <= budget) {
+      status = 0;
+      break;
+    }
+    if (iters >= max_iters) {
+      status = 2;
+      break;
+    }
+    /* classify, retire, count */
+    nsplit = or_classify(d, n, i7, err, vol, bad, scl, vol_omega, budget,
+                         opt->rel_tol, opt->classifier, flags, &ret_i, &ret_e,
+                         &ties);
+    for (r = 0; r < n; ++r)
+      if (flags[r] && atie[r]) ties++;
+    ties_total += ties;
+    I_ret = I_ret + ret_i;
+    E_ret = E_ret + ret_e;
+    if (trace && iters <= max_trace) {
+      or_trace *t = &trace[iters - 1];
+      t->n_split = nsplit;
+      t->near_ties = ties;
+      t->I_ret = I_ret;
+      t->E_ret = E_ret;
+    }
+    if (nsplit == 0) {
+      status = 3;
+      break;
+    }
+    if (2 * nsplit > cap) {
+      status = 1;
+      break;
+    }
+    /* bisect the survivors */
+    or_bisect(d, n, c, h, axis, flags, c2, h2);
+    n = 2 * nsplit;
+    {
+      double *t;
+      t = c; c = c2; c2 = t;
+      t = h; h = h2; h2 = t;
+    }
+  }
+
+done:
+  res->iterations = iters;
+  res->status = status;
+  res->near_ties = ties_total;
+  free(c);
+  free(h);
+  free(c2);
+  free(h2);
+  free(i7);
+  free(err);
+  free(vol);
+  free(scl);
+  free(axis);
+  free(bad);
+  free(atie);
+  free(flags);
+  return status;
+}

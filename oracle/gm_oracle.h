@@ -1,0 +1,133 @@
+/*
+ * gm_oracle.h -- plain FP64 CPU oracle of the adaptive Genz-Malik quadrature.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library: every constant below is
+ * recomputed here from the published formulas.
+ *
+ * Region layout in this oracle is plain array-of-structures: region r has
+ * centre c[r*d + k] and half-width h[r*d + k], k = 0..d-1.
+ */
+#ifndef GM_ORACLE_H
+#define GM_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* f(x) for x in R^d; ctx is opaque user data. */
+typedef double (*or_integrand)(const double *x, int d, const void *ctx);
+
+/* Built-in integrand families (paper Sec. 4 test functions and the Genz
+ * families they instantiate). */
+enum {
+  OR_OSCILLATORY = 0,   /* cos(2*pi*u_1 + sum a_j x_j)                    */
+  OR_PRODUCT_PEAK = 1,  /* prod 1/(a_j^-2 + (x_j-u_j)^2)                  */
+  OR_CORNER_PEAK = 2,   /* (1 + sum a_j x_j)^-(d+1)                       */
+  OR_GAUSSIAN = 3,      /* exp(-sum a_j^2 (x_j-u_j)^2)                    */
+  OR_C0 = 4,            /* exp(-sum a_j |x_j-u_j|)                        */
+  OR_DISCONTINUOUS = 5, /* 0 if any x_j > u_j, else exp(sum a_j x_j)      */
+  OR_POLY_SUMSQ11 = 6   /* (sum x_j^2)^11                                 */
+};
+
+typedef struct {
+  int32_t family;
+  int32_t d;
+  const double *a; /* length d */
+  const double *u; /* length d */
+} or_family;
+
+/* Result of the rule on one region. */
+typedef struct {
+  double i7, i5, err; /* degree-7 value, embedded degree-5 value, |i7-i5|  */
+  double s[5];        /* class sums S1..S5                                  */
+  double sabs[5];     /* sums of |f| per class (magnitude of the terms)     */
+  double vol;         /* prod_k 2 h_k                                       */
+  double f0;          /* f at the centre                                    */
+  int32_t axis;       /* chosen split axis                                  */
+  int32_t axis_tie;   /* 1 if the axis choice is a near-tie                 */
+  int32_t flat;       /* 1 if every fourth difference is at noise level     */
+  int32_t split_bad;  /* 1 if bisection along axis is not representable     */
+} or_rule_out;
+
+typedef struct {
+  double rel_tol;
+  double abs_tol;
+  int64_t max_regions;
+  int32_t init_splits; /* 0 = automatic */
+  int32_t max_iters;   /* 0 = 1000 */
+  int32_t classifier;  /* 0 = volume share, 1 = local relative */
+} or_options;
+
+typedef struct {
+  double integral, error;
+  int64_t regions_evaluated, function_evals, final_active;
+  int32_t iterations, status;
+  int64_t near_ties; /* decisions within the near-tie band over the run */
+} or_result;
+
+/* Per-sweep trace record (optional). */
+typedef struct {
+  int64_t n, n_split, near_ties;
+  double I, E, I_ret, E_ret, budget;
+} or_trace;
+
+/* Rule description. */
+int64_t or_num_nodes(int d);
+void or_lambdas(double lam[4]);                 /* lambda2..lambda5          */
+void or_weights(int d, double w7[5], double w5[5]);
+
+/* One built-in integrand at one point; ctx is an or_family*. */
+double or_family_eval(const double *x, int d, const void *ctx);
+
+/* Genz-Malik degree-7 rule with embedded degree-5 rule on one region.
+ * D (length d, may be NULL) receives the fourth differences. */
+void or_rule(int d, const double *c, const double *h, or_integrand f,
+             const void *ctx, double *D, or_rule_out *out);
+
+/* The rule over n regions of a built-in family (AoS c, h).  Output arrays
+ * of length n; any may be NULL. */
+void or_rule_regions(const or_family *fam, int64_t n, const double *c,
+                     const double *h, double *i7, double *i5, double *err,
+                     double *vol, int32_t *axis, int32_t *axis_tie,
+                     int32_t *split_bad, double *i7abs);
+
+/* Pairwise (binary tree over a zero-padded power of two) sum. */
+double or_pairwise_sum(const double *v, int64_t n);
+
+/* Initial uniform partition: returns s used; writes s^d regions. */
+int32_t or_auto_splits(int d, int64_t cap);
+int64_t or_partition(int d, const double *lo, const double *hi, int32_t s,
+                     double *c, double *h);
+
+/* Classification of one sweep.  flags[r] = 1 split, 0 retire.  Returns the
+ * number of split regions; retired sums and near-tie count via pointers.
+ * scale (may be NULL) is the per-region magnitude used for the near-tie
+ * band. */
+int64_t or_classify(int d, int64_t n, const double *i7, const double *err,
+                    const double *vol, const int32_t *split_bad,
+                    const double *scale, double vol_omega, double budget,
+                    double rel_tol, int32_t classifier, uint8_t *flags,
+                    double *ret_i, double *ret_e, int64_t *near_ties);
+
+/* Bisection + compaction: left children of split regions in input order at
+ * [0, n_split), right children at [n_split, 2 n_split). */
+int64_t or_bisect(int d, int64_t n, const double *c, const double *h,
+                  const int32_t *axis, const uint8_t *flags, double *c_out,
+                  double *h_out);
+
+/* The whole adaptive loop.  trace (may be NULL) receives up to max_trace
+ * records.  Status codes: 0 converged, 1 region cap reached, 2 iteration
+ * limit, 3 every region retired before the tolerance was met,
+ * -1 invalid argument, -2 out of memory, -4 non-finite integrand. */
+int32_t or_integrate(const or_family *fam, const double *lo, const double *hi,
+                     const or_options *opt, or_result *res, or_trace *trace,
+                     int32_t max_trace);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
