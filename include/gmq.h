@@ -1,0 +1,249 @@
+/*
+ * gmq.h -- C ABI of the GB300 adaptive Genz-Malik quadrature library.
+ *
+ * The library integrates f over a d-dimensional hyper-rectangle
+ * Omega = [lo_1,hi_1] x ... x [lo_d,hi_d] to a relative/absolute tolerance
+ * and returns the integral, its error estimate, and region and evaluation
+ * counts (problem statement: paper Sec. 2, first display; stopping rule
+ * eps <= max(abs_tol, rel_tol |I|): paper Sec. 4).  Every refinement sweep
+ * runs on one GPU over a device-resident structure-of-arrays list of regions
+ * (paper Sec. 3):
+ *   1. the Genz-Malik degree-7 rule with its embedded degree-5 rule on every
+ *      region, giving I_r, eps_r = |I7_r - I5_r| and the split axis from
+ *      per-axis fourth differences (paper Sec. 2);
+ *   2. the global sums I, eps and the convergence test (paper Sec. 3, 4);
+ *   3. the classifier that retires regions with negligible error into
+ *      running sums, with round-off guards (paper Sec. 3);
+ *   4. bisection of the surviving regions along their axis through a
+ *      scan-based compaction (paper Sec. 3, fused filter + split).
+ *
+ * Conventions for every call:
+ *   - Every call returns a gmq_status and never throws or aborts.
+ *   - Host pointers (gmq_problem arrays, gmq_options, gmq_result, seed
+ *     outputs) are read or written during the call only; the caller keeps
+ *     ownership.
+ *   - Pointers named d_* are device pointers in the context's device memory
+ *     (for example from torch.empty(..., device="cuda")); they are read or
+ *     written on the context stream and the call waits for that work before
+ *     returning, unless stated otherwise.
+ *   - Region arrays are structure-of-arrays with leading dimension ld:
+ *     centre k of region r is d_center[k*ld + r], half-width d_halfw[k*ld + r],
+ *     0 <= k < dim, 0 <= r < n, ld >= n.
+ *   - Calls on one context are not thread-safe; use one context per thread.
+ */
+#ifndef GMQ_H
+#define GMQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest supported dimension. */
+#define GMQ_MAX_DIM 16
+
+typedef enum gmq_status {
+  GMQ_OK = 0,              /* converged: error <= max(abs_tol, rel_tol |I|)   */
+  GMQ_CAP_REACHED = 1,     /* next sweep would exceed max_regions; best estimate returned */
+  GMQ_MAX_ITERS = 2,       /* max_iters sweeps done; best estimate returned   */
+  GMQ_ROUNDOFF_LIMIT = 3,  /* every region retired (round-off guards) before the
+                              tolerance was met; best estimate returned        */
+  GMQ_ERR_INVALID = -1,    /* bad argument                                    */
+  GMQ_ERR_OOM = -2,        /* device memory (or the caller's pool) too small  */
+  GMQ_ERR_CUDA = -3,       /* a CUDA call failed                              */
+  GMQ_ERR_NONFINITE = -4,  /* the integrand produced a NaN or an infinity     */
+  GMQ_ERR_TIMEOUT = -5     /* a bounded device wait gave up                   */
+} gmq_status;
+
+/* Built-in integrands (paper Sec. 4 test functions; Genz families).
+ * a and u are per-axis parameters of length dim. */
+typedef enum gmq_family {
+  GMQ_OSCILLATORY = 0,   /* cos(2 pi u_1 + sum_j a_j x_j)                 */
+  GMQ_PRODUCT_PEAK = 1,  /* prod_j 1 / (a_j^-2 + (x_j - u_j)^2)           */
+  GMQ_CORNER_PEAK = 2,   /* (1 + sum_j a_j x_j)^-(dim+1)                  */
+  GMQ_GAUSSIAN = 3,      /* exp(-sum_j a_j^2 (x_j - u_j)^2)               */
+  GMQ_C0 = 4,            /* exp(-sum_j a_j |x_j - u_j|)                   */
+  GMQ_DISCONTINUOUS = 5, /* 0 if any x_j > u_j, else exp(sum_j a_j x_j)   */
+  GMQ_POLY_SUMSQ11 = 6,  /* (sum_j x_j^2)^11 (a, u unused)                */
+  GMQ_NUM_FAMILIES = 7
+} gmq_family;
+
+typedef enum gmq_precision {
+  GMQ_FP64 = 0,  /* every step in FP64                                       */
+  GMQ_MIXED = 1  /* integrand in FP32 with compensated (two-sum) class sums;
+                    error difference, axis choice and global sums in FP64   */
+} gmq_precision;
+
+typedef enum gmq_classifier {
+  GMQ_VOLUME_SHARE = 0, /* retire r if eps_r <= max(abs_tol, rel_tol |I|) * vol_r / vol(Omega) */
+  GMQ_LOCAL_REL = 1     /* retire r if eps_r <= rel_tol |I_r|                                    */
+} gmq_classifier;
+
+typedef struct gmq_problem {
+  int32_t dim;       /* 1 <= dim <= GMQ_MAX_DIM                             */
+  int32_t family;    /* gmq_family                                          */
+  const double *lo;  /* host, length dim; NULL means all zeros              */
+  const double *hi;  /* host, length dim; NULL means all ones; hi > lo      */
+  const double *a;   /* host, length dim (may be NULL for POLY_SUMSQ11)     */
+  const double *u;   /* host, length dim (may be NULL for POLY_SUMSQ11)     */
+} gmq_problem;
+
+typedef struct gmq_options {
+  double rel_tol;      /* relative tolerance tau_rel >= 0                   */
+  double abs_tol;      /* absolute floor (paper: 1e-16)                     */
+  int64_t max_regions; /* region cap per sweep; sizes the region pool       */
+  int32_t init_splits; /* s: the initial partition has s^dim boxes;
+                          0 = largest s with s^dim <= min(4096, max_regions) */
+  int32_t max_iters;   /* sweep limit; 0 = 1000                             */
+  int32_t precision;   /* gmq_precision                                     */
+  int32_t classifier;  /* gmq_classifier                                    */
+  int32_t lanes;       /* threads per region in the rule kernel: 0 = chosen
+                          per sweep by the library, else 1, 4 or 32          */
+  int32_t reserved;    /* must be 0                                         */
+} gmq_options;
+
+typedef struct gmq_result {
+  double integral;           /* I: retired sums + active regions' I7_r     */
+  double error;              /* eps: the same for |I7_r - I5_r|            */
+  int64_t regions_evaluated; /* rule applications over all sweeps          */
+  int64_t function_evals;    /* regions_evaluated * (2^d + 2d^2 + 2d + 1)  */
+  int64_t final_active;      /* regions in the last evaluated sweep        */
+  int32_t iterations;        /* sweeps evaluated                           */
+  int32_t status;            /* gmq_status of the run                      */
+} gmq_result;
+
+/* One record per sweep of the last gmq_integrate call. */
+typedef struct gmq_sweep {
+  int64_t n;        /* regions evaluated in the sweep                      */
+  int64_t n_split;  /* regions bisected (-1 if the loop stopped first)     */
+  double I, E;      /* global estimates after the sweep's evaluation       */
+  double I_ret, E_ret; /* retired sums after the sweep's classification   */
+  double budget;    /* max(abs_tol, rel_tol |I|)                            */
+} gmq_sweep;
+
+typedef struct gmq_context gmq_context;
+
+/* Create a context on CUDA device `device`.  pool_bytes_hint > 0 reserves
+ * that much device memory up front for the region pool (otherwise the pool
+ * grows on demand).  *out receives the context; destroy it with
+ * gmq_destroy. */
+gmq_status gmq_create(gmq_context **out, int device, size_t pool_bytes_hint);
+
+/* Free the context and the device memory it owns (not a caller pool). */
+gmq_status gmq_destroy(gmq_context *ctx);
+
+/* Run all later work of the context on this cudaStream_t (NULL = the legacy
+ * default stream).  The stream must belong to the context's device. */
+gmq_status gmq_set_stream(gmq_context *ctx, void *cuda_stream);
+
+/* Use caller-owned device memory [dev_ptr, dev_ptr + bytes) as the region
+ * pool instead of allocating.  The memory must stay valid until the context
+ * is destroyed or another pool is set; dev_ptr must be 256-byte aligned.
+ * gmq_integrate then returns GMQ_ERR_OOM if the pool is too small
+ * (see gmq_pool_bytes).  Passing NULL returns to library-owned memory. */
+gmq_status gmq_set_pool(gmq_context *ctx, void *dev_ptr, size_t bytes);
+
+/* Device bytes the region pool needs for dimension dim and max_regions. */
+gmq_status gmq_pool_bytes(int32_t dim, int64_t max_regions, size_t *bytes);
+
+/* Fill opt with defaults: rel_tol 1e-6, abs_tol 1e-16, max_regions 2^22,
+ * automatic partition, 1000 sweeps, FP64, volume-share classifier, lanes 0. */
+gmq_status gmq_default_options(gmq_options *opt);
+
+/* Integrate (paper Sec. 3 loop).  Synchronous on the context stream.  A
+ * positive status still fills *out with the best estimate. */
+gmq_status gmq_integrate(gmq_context *ctx, const gmq_problem *prob,
+                         const gmq_options *opt, gmq_result *out);
+
+/* Copy up to max records of the last gmq_integrate call's per-sweep trace;
+ * *count receives the number of records available. */
+gmq_status gmq_last_trace(gmq_context *ctx, gmq_sweep *out, int32_t max,
+                          int32_t *count);
+
+/* Seeded Genz parameters (no counterpart in the paper; the paper's
+ * integrands use fixed parameters).  SplitMix64 stream with initial state
+ * (seed << 16) ^ (family << 8) ^ dim; a_j = top-53-bit doubles in [0,1)
+ * rescaled so that sum_j a_j = target_sum, then u_j in [0,1).  a_out and
+ * u_out are host arrays of length dim. */
+gmq_status gmq_seed_genz(uint64_t seed, int32_t family, int32_t dim,
+                         double target_sum, double *a_out, double *u_out);
+
+/* Human-readable name of a status code (static string). */
+const char *gmq_status_string(gmq_status s);
+
+/* Number of kernels the context has launched since creation. */
+gmq_status gmq_launch_count(gmq_context *ctx, int64_t *count);
+
+/* Kernel timing.  While enabled, the context brackets each kernel it
+ * launches with CUDA events on its stream and, when the call waits for the
+ * stream, adds the measured durations to per-kernel totals.  kernel: 0 rule
+ * evaluation, 1 global sums, 2 classify, 3 split, 4 partition.  `regions`
+ * counts the regions the launches processed.  Enabling adds two event
+ * records per launch. */
+typedef struct gmq_kernel_stats {
+  int64_t launches;
+  int64_t regions;
+  double ms;
+} gmq_kernel_stats;
+
+gmq_status gmq_profile_enable(gmq_context *ctx, int32_t on);
+gmq_status gmq_profile_reset(gmq_context *ctx);
+gmq_status gmq_profile_read(gmq_context *ctx, int32_t kernel, gmq_kernel_stats *out);
+
+/* ---- step-level calls on caller device memory (one sweep's pieces) ---- */
+
+/* Rule evaluation (paper Sec. 2) on n regions.  Outputs, each of length n:
+ * d_integral[r] = I7_r; d_error[r] = |I7_r - I5_r|; d_volfrac[r] =
+ * vol_r / vol(Omega) with vol_r = prod_k 2 h_k and vol(Omega) from the
+ * problem's lo, hi; d_axis[r] = split axis in bits 0..6, bit 7 set when
+ * bisecting along that axis cannot move the centre (round-off guard).
+ * precision: gmq_precision; lanes: 0, 1, 4 or 32 as in gmq_options.
+ * d_volfrac may be NULL. */
+gmq_status gmq_eval_rule(gmq_context *ctx, const gmq_problem *prob,
+                         int32_t precision, int32_t lanes, int64_t n,
+                         const double *d_center, const double *d_halfw,
+                         int64_t ld, double *d_integral, double *d_error,
+                         double *d_volfrac, uint8_t *d_axis);
+
+/* Classification and bisection of one sweep (paper Sec. 3) given the rule
+ * outputs above and the sweep's budget = max(abs_tol, rel_tol |I|).
+ * Region r is retired if eps_r <= budget * volfrac_r (GMQ_VOLUME_SHARE) or
+ * eps_r <= rel_tol |I_r| (GMQ_LOCAL_REL), or eps_r <= 50 * 2^-53 |I_r|, or
+ * bit 7 of d_axis[r] is set; otherwise it is split.  The left children of
+ * the split regions, in input order, are written to slots [0, n_split) of
+ * the output arrays and the right children to [n_split, 2 n_split).
+ * If 2 n_split > cap_out nothing is written and GMQ_CAP_REACHED is returned
+ * (n_split and the sums are still reported).  d_flags (may be NULL)
+ * receives 1 for split, 0 for retired.  *retired_integral and
+ * *retired_error receive the pairwise-tree sums over the list of the
+ * retired regions' I_r and eps_r (split regions count as zero). */
+gmq_status gmq_classify_split(gmq_context *ctx, int32_t dim, int64_t n,
+                              const double *d_center, const double *d_halfw,
+                              int64_t ld, const double *d_integral,
+                              const double *d_error, const double *d_volfrac,
+                              const uint8_t *d_axis, double budget,
+                              double rel_tol, int32_t classifier,
+                              double *d_center_out, double *d_halfw_out,
+                              int64_t ld_out, int64_t cap_out,
+                              uint8_t *d_flags, int64_t *n_split,
+                              double *retired_integral, double *retired_error);
+
+/* Pairwise-tree sum of d_v[0..n): sum(range) = sum(left half) +
+ * sum(right half) over the range zero-padded to a power of two.  The same
+ * order is used for every global sum of the loop. */
+gmq_status gmq_tree_sum(gmq_context *ctx, int64_t n, const double *d_v,
+                        double *sum);
+
+/* Initial uniform partition (paper Sec. 3): s^dim boxes of equal size,
+ * the axis-0 index fastest; along axis k box i has h_k = (hi_k - lo_k)/(2s)
+ * and c_k = lo_k + (2i + 1) h_k.  ld >= s^dim. */
+gmq_status gmq_partition(gmq_context *ctx, int32_t dim, const double *lo,
+                         const double *hi, int32_t s, double *d_center,
+                         double *d_halfw, int64_t ld);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMQ_H */

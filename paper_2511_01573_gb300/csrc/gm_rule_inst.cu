@@ -1,0 +1,12 @@
+// gm_rule_inst.cu -- instantiates the rule kernel for one integrand family.
+// The build compiles this file once per family with -DGMQ_FAM=<code>, so the
+// instantiations compile in parallel.
+#include "gm_rule.cuh"
+
+#ifndef GMQ_FAM
+#error "compile with -DGMQ_FAM=<family code>"
+#endif
+
+namespace gmq {
+GMQ_DEFINE_RULE_FAMILY(GMQ_FAM)
+}  // namespace gmq

@@ -1,0 +1,820 @@
+// gmq_api.cu -- host side of the library: the C ABI declared in gmq.h, the
+// context and its region pool, and the adaptive loop that drives the sweep
+// kernels (paper Sec. 3, Fig. 1a; stopping rule paper Sec. 4).
+//
+// Per sweep the host enqueues, on the context stream:
+//   rule evaluation (K1) -> global sums + convergence test -> classify ->
+//   split into the other half of the ping-pong pool,
+// then copies the 80-byte device status to pinned host memory and waits on
+// it: the only host<->device traffic of a sweep.  Every kernel after the
+// sums checks the device status and returns at once when the loop is done,
+// so a converged sweep does no classification or splitting work.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gm_rule.cuh"
+#include "gmq_common.cuh"
+#include "sweep_kernels.cuh"
+
+using namespace gmq;
+
+namespace gmq {
+template <int FAM>
+cudaError_t launch_rule_family(int precision, int T, const RuleArgs& A, cudaStream_t s);
+}
+
+struct gmq_context {
+  int device = 0;
+  int sm_count = 1;
+  cudaStream_t stream = nullptr;
+  char* own = nullptr;
+  size_t own_bytes = 0;
+  char* ext = nullptr;
+  size_t ext_bytes = 0;
+  char* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  DevStatus* h_status = nullptr;  // pinned
+  std::vector<gmq_sweep> trace;
+  int64_t launches = 0;
+  // kernel timing (gmq_profile_*)
+  bool prof_on = false;
+  bool ev_made = false;
+  cudaEvent_t ev[5][2] = {};
+  bool pending[5] = {};
+  int64_t pend_regions[5] = {};
+  gmq_kernel_stats stats[5] = {};
+};
+
+namespace {
+
+constexpr int64_t kMaxRegions = (int64_t)1 << 30;
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int64_t num_nodes(int d) { return ((int64_t)1 << d) + 2 * (int64_t)d * d + 2 * (int64_t)d + 1; }
+
+// Region pool of one integration: two region lists (ping-pong), the rule
+// outputs, the decision bytes, per-tile arrays and the device status.
+struct PoolLayout {
+  int64_t ld = 0, nb = 0;
+  size_t cA = 0, hA = 0, cB = 0, hB = 0, i7 = 0, err = 0, vf = 0, axis = 0, flags = 0;
+  size_t cnt = 0, off = 0, ba = 0, bb = 0, st = 0, total = 0;
+};
+
+PoolLayout pool_layout(int d, int64_t cap) {
+  PoolLayout L;
+  L.ld = (cap + 31) / 32 * 32;
+  L.nb = (cap + kTile - 1) / kTile;
+  size_t p = 0;
+  const size_t list = align256(sizeof(double) * (size_t)d * (size_t)L.ld);
+  const size_t vec = align256(sizeof(double) * (size_t)L.ld);
+  const size_t bytes = align256((size_t)L.ld);
+  L.cA = p; p += list;
+  L.hA = p; p += list;
+  L.cB = p; p += list;
+  L.hB = p; p += list;
+  L.i7 = p; p += vec;
+  L.err = p; p += vec;
+  L.vf = p; p += vec;
+  L.axis = p; p += bytes;
+  L.flags = p; p += bytes;
+  L.cnt = p; p += align256(sizeof(int) * (size_t)L.nb);
+  L.off = p; p += align256(sizeof(long long) * (size_t)L.nb);
+  L.ba = p; p += align256(sizeof(double) * (size_t)L.nb);
+  L.bb = p; p += align256(sizeof(double) * (size_t)L.nb);
+  L.st = p; p += align256(sizeof(DevStatus));
+  L.total = p;
+  return L;
+}
+
+RuleConst rule_const(int d, const double* lo, const double* hi) {
+  RuleConst R;
+  const double dd = (double)d;
+  R.lam2 = std::sqrt(9.0 / 70.0);
+  R.lam3 = std::sqrt(9.0 / 10.0);
+  R.lam5 = std::sqrt(9.0 / 19.0);
+  R.w7[0] = (12824.0 - 9120.0 * dd + 400.0 * dd * dd) / 19683.0;
+  R.w7[1] = 980.0 / 6561.0;
+  R.w7[2] = (1820.0 - 400.0 * dd) / 19683.0;
+  R.w7[3] = 200.0 / 19683.0;
+  R.w7[4] = 6859.0 / (19683.0 * std::ldexp(1.0, d));
+  R.w5[0] = (729.0 - 950.0 * dd + 50.0 * dd * dd) / 729.0;
+  R.w5[1] = 245.0 / 486.0;
+  R.w5[2] = (265.0 - 100.0 * dd) / 1458.0;
+  R.w5[3] = 25.0 / 729.0;
+  R.w5[4] = 0.0;
+  R.ratio = 1.0 / 7.0;
+  double v = 1.0;
+  for (int k = 0; k < d; ++k) {
+    const double l = lo ? lo[k] : 0.0, h = hi ? hi[k] : 1.0;
+    v = v * (h - l);
+  }
+  R.vol_omega = v;
+  R.nodes = num_nodes(d);
+  return R;
+}
+
+FamParams fam_params(const gmq_problem* p) {
+  FamParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.d = p->dim;
+  P.family = p->family;
+  for (int j = 0; j < p->dim; ++j) {
+    P.a[j] = p->a ? p->a[j] : 0.0;
+    P.u[j] = p->u ? p->u[j] : 0.0;
+    if (p->family == GMQ_PRODUCT_PEAK) P.b[j] = 1.0 / (P.a[j] * P.a[j]);
+    if (p->family == GMQ_GAUSSIAN) P.b[j] = P.a[j] * P.a[j];
+  }
+  if (p->family == GMQ_OSCILLATORY) P.c0 = 2.0 * M_PI * P.u[0];
+  return P;
+}
+
+gmq_status validate_problem(const gmq_problem* p) {
+  if (!p) return GMQ_ERR_INVALID;
+  if (p->dim < 1 || p->dim > GMQ_MAX_DIM) return GMQ_ERR_INVALID;
+  if (p->family < 0 || p->family >= GMQ_NUM_FAMILIES) return GMQ_ERR_INVALID;
+  if (p->family != GMQ_POLY_SUMSQ11 && (!p->a || !p->u)) return GMQ_ERR_INVALID;
+  for (int k = 0; k < p->dim; ++k) {
+    const double l = p->lo ? p->lo[k] : 0.0, h = p->hi ? p->hi[k] : 1.0;
+    if (!std::isfinite(l) || !std::isfinite(h) || !(h > l)) return GMQ_ERR_INVALID;
+    if (p->a && !std::isfinite(p->a[k])) return GMQ_ERR_INVALID;
+    if (p->u && !std::isfinite(p->u[k])) return GMQ_ERR_INVALID;
+  }
+  return GMQ_OK;
+}
+
+int auto_splits(int d, int64_t cap) {
+  const int64_t lim = std::min<int64_t>(cap, 4096);
+  int s = 1;
+  for (;;) {
+    int64_t p = 1;
+    bool over = false;
+    for (int k = 0; k < d; ++k) {
+      p *= (s + 1);
+      if (p > lim) {
+        over = true;
+        break;
+      }
+    }
+    if (over) break;
+    ++s;
+  }
+  return s;
+}
+
+// Threads per region for a sweep of n regions: one thread per region once
+// there are enough regions to give every SM about eight warps; otherwise
+// split each region's nodes over 4 or 32 lanes.
+int choose_lanes(int req, int64_t n, int d, int sms) {
+  if (req) return req;
+  const int64_t nodes = num_nodes(d);
+  const int64_t want = (int64_t)sms * 256;
+  if (n >= want || nodes < 16) return 1;
+  if (n * 4 >= want || nodes < 128) return 4;
+  return 32;
+}
+
+cudaError_t launch_rule(int fam, int precision, int T, const RuleArgs& A, cudaStream_t s) {
+  switch (fam) {
+    case GMQ_OSCILLATORY: return launch_rule_family<GMQ_OSCILLATORY>(precision, T, A, s);
+    case GMQ_PRODUCT_PEAK: return launch_rule_family<GMQ_PRODUCT_PEAK>(precision, T, A, s);
+    case GMQ_CORNER_PEAK: return launch_rule_family<GMQ_CORNER_PEAK>(precision, T, A, s);
+    case GMQ_GAUSSIAN: return launch_rule_family<GMQ_GAUSSIAN>(precision, T, A, s);
+    case GMQ_C0: return launch_rule_family<GMQ_C0>(precision, T, A, s);
+    case GMQ_DISCONTINUOUS: return launch_rule_family<GMQ_DISCONTINUOUS>(precision, T, A, s);
+    case GMQ_POLY_SUMSQ11: return launch_rule_family<GMQ_POLY_SUMSQ11>(precision, T, A, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+gmq_status cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return GMQ_ERR_OOM;
+  if (e == cudaErrorNotSupported) return GMQ_ERR_INVALID;
+  return GMQ_ERR_CUDA;
+}
+
+#define GMQ_CK(expr)                          \
+  do {                                        \
+    cudaError_t e_ = (expr);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+// Pool memory for an integration: the caller's pool or library memory that
+// grows on demand.
+gmq_status ensure_pool(gmq_context* ctx, size_t need, char** base) {
+  if (ctx->ext) {
+    if (ctx->ext_bytes < need) return GMQ_ERR_OOM;
+    *base = ctx->ext;
+    return GMQ_OK;
+  }
+  if (ctx->own_bytes < need) {
+    if (ctx->own) {
+      cudaFree(ctx->own);
+      ctx->own = nullptr;
+      ctx->own_bytes = 0;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      return GMQ_ERR_OOM;
+    }
+    ctx->own = (char*)p;
+    ctx->own_bytes = need;
+  }
+  *base = ctx->own;
+  return GMQ_OK;
+}
+
+// Kernel timing: events around each launch, collected after the stream wait.
+enum { kKRule = 0, kKSum = 1, kKClassify = 2, kKSplit = 3, kKPartition = 4 };
+
+inline void prof_begin(gmq_context* c, int k) {
+  if (c->prof_on) cudaEventRecord(c->ev[k][0], c->stream);
+}
+
+inline void prof_end(gmq_context* c, int k, int64_t regions) {
+  if (!c->prof_on) return;
+  cudaEventRecord(c->ev[k][1], c->stream);
+  c->pending[k] = true;
+  c->pend_regions[k] = regions;
+}
+
+void prof_collect(gmq_context* c) {
+  if (!c->prof_on) return;
+  for (int k = 0; k < 5; ++k) {
+    if (!c->pending[k]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[k][0], c->ev[k][1]) == cudaSuccess) {
+      c->stats[k].ms += ms;
+      c->stats[k].launches += 1;
+      c->stats[k].regions += c->pend_regions[k];
+    } else {
+      cudaGetLastError();
+    }
+    c->pending[k] = false;
+  }
+}
+
+// Scratch of the step-level calls: per-tile arrays for n regions, a flag
+// array, and a device status.
+struct Scratch {
+  int* cnt;
+  long long* off;
+  double* ba;
+  double* bb;
+  uint8_t* flags;
+  DevStatus* st;
+  double* out;
+};
+
+gmq_status ensure_scratch(gmq_context* ctx, int64_t n, Scratch* S) {
+  const int64_t nb = std::max<int64_t>(1, (n + kTile - 1) / kTile);
+  size_t p = 0;
+  const size_t o_cnt = p; p += align256(sizeof(int) * nb);
+  const size_t o_off = p; p += align256(sizeof(long long) * nb);
+  const size_t o_ba = p; p += align256(sizeof(double) * nb);
+  const size_t o_bb = p; p += align256(sizeof(double) * nb);
+  const size_t o_fl = p; p += align256((size_t)std::max<int64_t>(n, 1));
+  const size_t o_st = p; p += align256(sizeof(DevStatus));
+  const size_t o_out = p; p += 256;
+  if (ctx->scratch_bytes < p) {
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    void* q = nullptr;
+    if (cudaMalloc(&q, p) != cudaSuccess) {
+      cudaGetLastError();
+      return GMQ_ERR_OOM;
+    }
+    ctx->scratch = (char*)q;
+    ctx->scratch_bytes = p;
+  }
+  char* b = ctx->scratch;
+  S->cnt = (int*)(b + o_cnt);
+  S->off = (long long*)(b + o_off);
+  S->ba = (double*)(b + o_ba);
+  S->bb = (double*)(b + o_bb);
+  S->flags = (uint8_t*)(b + o_fl);
+  S->st = (DevStatus*)(b + o_st);
+  S->out = (double*)(b + o_out);
+  return GMQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gmq_status_string(gmq_status s) {
+  switch (s) {
+    case GMQ_OK: return "converged";
+    case GMQ_CAP_REACHED: return "region cap reached";
+    case GMQ_MAX_ITERS: return "iteration limit reached";
+    case GMQ_ROUNDOFF_LIMIT: return "all regions retired before the tolerance was met";
+    case GMQ_ERR_INVALID: return "invalid argument";
+    case GMQ_ERR_OOM: return "out of device memory";
+    case GMQ_ERR_CUDA: return "CUDA error";
+    case GMQ_ERR_NONFINITE: return "non-finite integrand value";
+    case GMQ_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+gmq_status gmq_create(gmq_context** out, int device, size_t pool_bytes_hint) {
+  if (!out) return GMQ_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return GMQ_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return GMQ_ERR_INVALID;
+  DeviceGuard g(device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  gmq_context* ctx = new (std::nothrow) gmq_context();
+  if (!ctx) return GMQ_ERR_OOM;
+  ctx->device = device;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete ctx;
+    return GMQ_ERR_CUDA;
+  }
+  ctx->sm_count = prop.multiProcessorCount;
+  if (cudaHostAlloc((void**)&ctx->h_status, sizeof(DevStatus), cudaHostAllocDefault) != cudaSuccess) {
+    delete ctx;
+    return GMQ_ERR_CUDA;
+  }
+  if (pool_bytes_hint > 0) {
+    char* base = nullptr;
+    gmq_status st = ensure_pool(ctx, pool_bytes_hint, &base);
+    if (st != GMQ_OK) {
+      cudaFreeHost(ctx->h_status);
+      delete ctx;
+      return st;
+    }
+  }
+  *out = ctx;
+  return GMQ_OK;
+}
+
+gmq_status gmq_destroy(gmq_context* ctx) {
+  if (!ctx) return GMQ_ERR_INVALID;
+  {
+    DeviceGuard g(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->own) cudaFree(ctx->own);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->ev_made)
+      for (int k = 0; k < 5; ++k)
+        for (int j = 0; j < 2; ++j) cudaEventDestroy(ctx->ev[k][j]);
+  }
+  delete ctx;
+  return GMQ_OK;
+}
+
+gmq_status gmq_set_stream(gmq_context* ctx, void* cuda_stream) {
+  if (!ctx) return GMQ_ERR_INVALID;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return GMQ_OK;
+}
+
+gmq_status gmq_set_pool(gmq_context* ctx, void* dev_ptr, size_t bytes) {
+  if (!ctx) return GMQ_ERR_INVALID;
+  if (dev_ptr && ((uintptr_t)dev_ptr & 255u)) return GMQ_ERR_INVALID;
+  ctx->ext = (char*)dev_ptr;
+  ctx->ext_bytes = dev_ptr ? bytes : 0;
+  return GMQ_OK;
+}
+
+gmq_status gmq_pool_bytes(int32_t dim, int64_t max_regions, size_t* bytes) {
+  if (!bytes || dim < 1 || dim > GMQ_MAX_DIM || max_regions < 1 || max_regions > kMaxRegions)
+    return GMQ_ERR_INVALID;
+  *bytes = pool_layout(dim, max_regions).total;
+  return GMQ_OK;
+}
+
+gmq_status gmq_default_options(gmq_options* opt) {
+  if (!opt) return GMQ_ERR_INVALID;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->rel_tol = 1e-6;
+  opt->abs_tol = 1e-16;
+  opt->max_regions = (int64_t)1 << 22;
+  opt->max_iters = 1000;
+  opt->precision = GMQ_FP64;
+  opt->classifier = GMQ_VOLUME_SHARE;
+  return GMQ_OK;
+}
+
+gmq_status gmq_launch_count(gmq_context* ctx, int64_t* count) {
+  if (!ctx || !count) return GMQ_ERR_INVALID;
+  *count = ctx->launches;
+  return GMQ_OK;
+}
+
+gmq_status gmq_last_trace(gmq_context* ctx, gmq_sweep* out, int32_t max, int32_t* count) {
+  if (!ctx || !count || max < 0 || (max > 0 && !out)) return GMQ_ERR_INVALID;
+  *count = (int32_t)ctx->trace.size();
+  const int32_t m = std::min<int32_t>(max, *count);
+  for (int32_t i = 0; i < m; ++i) out[i] = ctx->trace[i];
+  return GMQ_OK;
+}
+
+gmq_status gmq_seed_genz(uint64_t seed, int32_t family, int32_t dim, double target_sum,
+                         double* a_out, double* u_out) {
+  if (dim < 1 || dim > 255 || family < 0 || family > 255 || !a_out || !u_out) return GMQ_ERR_INVALID;
+  // SplitMix64 (Steele, Lea & Flood 2014)
+  uint64_t state = (seed << 16) ^ ((uint64_t)family << 8) ^ (uint64_t)dim;
+  auto next = [&state]() -> double {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  double tot = 0.0;
+  for (int j = 0; j < dim; ++j) {
+    a_out[j] = next();
+    tot = tot + a_out[j];
+  }
+  for (int j = 0; j < dim; ++j) u_out[j] = next();
+  const double scale = target_sum / tot;
+  for (int j = 0; j < dim; ++j) a_out[j] = a_out[j] * scale;
+  return GMQ_OK;
+}
+
+gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_options* opt,
+                         gmq_result* out) {
+  if (!ctx || !opt || !out) return GMQ_ERR_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  ctx->trace.clear();
+  gmq_status vs = validate_problem(prob);
+  if (vs != GMQ_OK) return out->status = vs, vs;
+  const int d = prob->dim;
+  const int64_t cap = opt->max_regions;
+  if (!(opt->rel_tol >= 0.0) || !(opt->abs_tol >= 0.0) || cap < 1 || cap > kMaxRegions ||
+      opt->init_splits < 0 || opt->max_iters < 0 || opt->reserved != 0 ||
+      (opt->precision != GMQ_FP64 && opt->precision != GMQ_MIXED) ||
+      (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL) ||
+      (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32))
+    return out->status = GMQ_ERR_INVALID, GMQ_ERR_INVALID;
+  const int s = opt->init_splits > 0 ? opt->init_splits : auto_splits(d, cap);
+  int64_t n = 1;
+  for (int k = 0; k < d; ++k) {
+    n *= s;
+    if (n > cap) return out->status = GMQ_ERR_INVALID, GMQ_ERR_INVALID;
+  }
+  const int max_iters = opt->max_iters > 0 ? opt->max_iters : 1000;
+
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return out->status = GMQ_ERR_CUDA, GMQ_ERR_CUDA;
+  const PoolLayout L = pool_layout(d, cap);
+  char* base = nullptr;
+  gmq_status ps = ensure_pool(ctx, L.total, &base);
+  if (ps != GMQ_OK) return out->status = ps, ps;
+
+  double* cA = (double*)(base + L.cA);
+  double* hA = (double*)(base + L.hA);
+  double* cB = (double*)(base + L.cB);
+  double* hB = (double*)(base + L.hB);
+  DevStatus* st = (DevStatus*)(base + L.st);
+  cudaStream_t strm = ctx->stream;
+
+  const FamParams P = fam_params(prob);
+  const RuleConst R = rule_const(d, prob->lo, prob->hi);
+
+  // initial uniform partition
+  PartArgs PA;
+  std::memset(&PA, 0, sizeof(PA));
+  PA.d = d;
+  PA.s = s;
+  PA.n = n;
+  for (int k = 0; k < d; ++k) {
+    const double lo = prob->lo ? prob->lo[k] : 0.0, hi = prob->hi ? prob->hi[k] : 1.0;
+    PA.lo[k] = lo;
+    PA.h[k] = (hi - lo) / (2.0 * (double)s);
+  }
+  PA.c_out = cA;
+  PA.h_out = hA;
+  PA.ld = L.ld;
+  GMQ_CK(cudaMemsetAsync(st, 0, sizeof(DevStatus), strm));
+  prof_begin(ctx, kKPartition);
+  GMQ_CK(launch_partition(PA, strm));
+  prof_end(ctx, kKPartition, n);
+  ctx->launches += 1;
+
+  gmq_status status = GMQ_OK;
+  int iters = 0;
+  for (;;) {
+    const int T = choose_lanes(opt->lanes, n, d, ctx->sm_count);
+    RuleArgs A;
+    A.c = cA;
+    A.h = hA;
+    A.ld = L.ld;
+    A.n = n;
+    A.i7 = (double*)(base + L.i7);
+    A.err = (double*)(base + L.err);
+    A.volfrac = (double*)(base + L.vf);
+    A.axis = (uint8_t*)(base + L.axis);
+    A.P = P;
+    A.R = R;
+    prof_begin(ctx, kKRule);
+    GMQ_CK(launch_rule(prob->family, opt->precision, T, A, strm));
+    prof_end(ctx, kKRule, n);
+
+    SweepArgs S;
+    std::memset(&S, 0, sizeof(S));
+    S.n = n;
+    S.d = d;
+    S.classifier = opt->classifier;
+    S.rel_tol = opt->rel_tol;
+    S.abs_tol = opt->abs_tol;
+    S.cap = cap;
+    S.c = cA;
+    S.h = hA;
+    S.ld = L.ld;
+    S.c_out = cB;
+    S.h_out = hB;
+    S.ld_out = L.ld;
+    S.i7 = A.i7;
+    S.err = A.err;
+    S.volfrac = A.volfrac;
+    S.axis = A.axis;
+    S.flags = (uint8_t*)(base + L.flags);
+    S.blk_count = (int*)(base + L.cnt);
+    S.blk_off = (long long*)(base + L.off);
+    S.blk_a = (double*)(base + L.ba);
+    S.blk_b = (double*)(base + L.bb);
+    S.budget_ptr = &st->budget;
+    S.st = st;
+    prof_begin(ctx, kKSum);
+    GMQ_CK(launch_sum_status(S, strm));
+    prof_end(ctx, kKSum, n);
+    prof_begin(ctx, kKClassify);
+    GMQ_CK(launch_classify(S, strm));
+    prof_end(ctx, kKClassify, n);
+    prof_begin(ctx, kKSplit);
+    GMQ_CK(launch_split(S, strm));
+    prof_end(ctx, kKSplit, n);
+    ctx->launches += 4;
+    GMQ_CK(cudaMemcpyAsync(ctx->h_status, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, strm));
+    GMQ_CK(cudaStreamSynchronize(strm));
+    prof_collect(ctx);
+    const DevStatus h = *ctx->h_status;
+
+    ++iters;
+    out->regions_evaluated += n;
+    out->function_evals += n * R.nodes;
+    out->final_active = n;
+    out->integral = h.I;
+    out->error = h.E;
+    gmq_sweep rec;
+    rec.n = n;
+    rec.I = h.I;
+    rec.E = h.E;
+    rec.budget = h.budget;
+    // the loop classifies only when it neither stopped nor hit the sweep
+    // limit; the classify kernel ran regardless, so an unclassified record
+    // carries the retired sums of the previous sweep
+    const bool classified = !(h.flags & (kConverged | kNonfinite)) && iters < max_iters;
+    rec.n_split = classified ? h.n_split : -1;
+    rec.I_ret = classified ? h.I_ret : (ctx->trace.empty() ? 0.0 : ctx->trace.back().I_ret);
+    rec.E_ret = classified ? h.E_ret : (ctx->trace.empty() ? 0.0 : ctx->trace.back().E_ret);
+    ctx->trace.push_back(rec);
+
+    if (h.flags & kNonfinite) {
+      status = GMQ_ERR_NONFINITE;
+      break;
+    }
+    if (h.flags & kConverged) {
+      status = GMQ_OK;
+      break;
+    }
+    if (iters >= max_iters) {
+      status = GMQ_MAX_ITERS;
+      break;
+    }
+    if (h.flags & kAllRetired) {
+      status = GMQ_ROUNDOFF_LIMIT;
+      break;
+    }
+    if (h.flags & kCapExceeded) {
+      status = GMQ_CAP_REACHED;
+      break;
+    }
+    n = 2 * h.n_split;
+    std::swap(cA, cB);
+    std::swap(hA, hB);
+  }
+  out->iterations = iters;
+  out->status = status;
+  return status;
+}
+
+gmq_status gmq_eval_rule(gmq_context* ctx, const gmq_problem* prob, int32_t precision,
+                         int32_t lanes, int64_t n, const double* d_center, const double* d_halfw,
+                         int64_t ld, double* d_integral, double* d_error, double* d_volfrac,
+                         uint8_t* d_axis) {
+  if (!ctx) return GMQ_ERR_INVALID;
+  gmq_status vs = validate_problem(prob);
+  if (vs != GMQ_OK) return vs;
+  if (n < 0 || ld < n || (n > 0 && (!d_center || !d_halfw || !d_integral || !d_error || !d_axis)))
+    return GMQ_ERR_INVALID;
+  if (precision != GMQ_FP64 && precision != GMQ_MIXED) return GMQ_ERR_INVALID;
+  if (lanes != 0 && lanes != 1 && lanes != 4 && lanes != 32) return GMQ_ERR_INVALID;
+  if (n == 0) return GMQ_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  RuleArgs A;
+  A.c = d_center;
+  A.h = d_halfw;
+  A.ld = ld;
+  A.n = n;
+  A.i7 = d_integral;
+  A.err = d_error;
+  A.volfrac = d_volfrac;
+  A.axis = d_axis;
+  A.P = fam_params(prob);
+  A.R = rule_const(prob->dim, prob->lo, prob->hi);
+  const int T = choose_lanes(lanes, n, prob->dim, ctx->sm_count);
+  prof_begin(ctx, kKRule);
+  GMQ_CK(launch_rule(prob->family, precision, T, A, ctx->stream));
+  prof_end(ctx, kKRule, n);
+  ctx->launches += 1;
+  GMQ_CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  return GMQ_OK;
+}
+
+gmq_status gmq_classify_split(gmq_context* ctx, int32_t dim, int64_t n, const double* d_center,
+                              const double* d_halfw, int64_t ld, const double* d_integral,
+                              const double* d_error, const double* d_volfrac,
+                              const uint8_t* d_axis, double budget, double rel_tol,
+                              int32_t classifier, double* d_center_out, double* d_halfw_out,
+                              int64_t ld_out, int64_t cap_out, uint8_t* d_flags,
+                              int64_t* n_split, double* retired_integral,
+                              double* retired_error) {
+  if (!ctx || !n_split || !retired_integral || !retired_error) return GMQ_ERR_INVALID;
+  if (dim < 1 || dim > GMQ_MAX_DIM || n < 0 || n > kMaxRegions || ld < n || cap_out < 0 ||
+      ld_out < cap_out)
+    return GMQ_ERR_INVALID;
+  if (classifier != GMQ_VOLUME_SHARE && classifier != GMQ_LOCAL_REL) return GMQ_ERR_INVALID;
+  if (n > 0 && (!d_center || !d_halfw || !d_integral || !d_error || !d_axis ||
+                (classifier == GMQ_VOLUME_SHARE && !d_volfrac)))
+    return GMQ_ERR_INVALID;
+  if (cap_out > 0 && (!d_center_out || !d_halfw_out)) return GMQ_ERR_INVALID;
+  *n_split = 0;
+  *retired_integral = 0.0;
+  *retired_error = 0.0;
+  if (n == 0) return GMQ_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  Scratch X;
+  gmq_status ss = ensure_scratch(ctx, n, &X);
+  if (ss != GMQ_OK) return ss;
+  SweepArgs S;
+  std::memset(&S, 0, sizeof(S));
+  S.n = n;
+  S.d = dim;
+  S.classifier = classifier;
+  S.rel_tol = rel_tol;
+  S.cap = cap_out;
+  S.c = d_center;
+  S.h = d_halfw;
+  S.ld = ld;
+  S.c_out = d_center_out;
+  S.h_out = d_halfw_out;
+  S.ld_out = ld_out;
+  S.i7 = d_integral;
+  S.err = d_error;
+  S.volfrac = d_volfrac;
+  S.axis = d_axis;
+  S.flags = d_flags ? d_flags : X.flags;
+  S.blk_count = X.cnt;
+  S.blk_off = X.off;
+  S.blk_a = X.ba;
+  S.blk_b = X.bb;
+  S.budget_ptr = nullptr;
+  S.budget_val = budget;
+  S.st = X.st;
+  cudaStream_t strm = ctx->stream;
+  GMQ_CK(cudaMemsetAsync(X.st, 0, sizeof(DevStatus), strm));
+  prof_begin(ctx, kKClassify);
+  GMQ_CK(launch_classify(S, strm));
+  prof_end(ctx, kKClassify, n);
+  prof_begin(ctx, kKSplit);
+  GMQ_CK(launch_split(S, strm));
+  prof_end(ctx, kKSplit, n);
+  ctx->launches += 2;
+  GMQ_CK(cudaMemcpyAsync(ctx->h_status, X.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, strm));
+  GMQ_CK(cudaStreamSynchronize(strm));
+  prof_collect(ctx);
+  const DevStatus h = *ctx->h_status;
+  *n_split = h.n_split;
+  *retired_integral = h.ret_i;
+  *retired_error = h.ret_e;
+  if (h.flags & kCapExceeded) return GMQ_CAP_REACHED;
+  return GMQ_OK;
+}
+
+gmq_status gmq_tree_sum(gmq_context* ctx, int64_t n, const double* d_v, double* sum) {
+  if (!ctx || !sum || n < 0 || n > kMaxRegions || (n > 0 && !d_v)) return GMQ_ERR_INVALID;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  Scratch X;
+  gmq_status ss = ensure_scratch(ctx, n, &X);
+  if (ss != GMQ_OK) return ss;
+  cudaStream_t strm = ctx->stream;
+  GMQ_CK(cudaMemsetAsync(X.st, 0, sizeof(DevStatus), strm));
+  prof_begin(ctx, kKSum);
+  GMQ_CK(launch_tree_sum(d_v, n, X.ba, X.st, X.out, strm));
+  prof_end(ctx, kKSum, n);
+  ctx->launches += 1;
+  GMQ_CK(cudaMemcpyAsync(&ctx->h_status->I, X.out, sizeof(double), cudaMemcpyDeviceToHost, strm));
+  GMQ_CK(cudaStreamSynchronize(strm));
+  prof_collect(ctx);
+  *sum = ctx->h_status->I;
+  return GMQ_OK;
+}
+
+gmq_status gmq_partition(gmq_context* ctx, int32_t dim, const double* lo, const double* hi,
+                         int32_t s, double* d_center, double* d_halfw, int64_t ld) {
+  if (!ctx || dim < 1 || dim > GMQ_MAX_DIM || s < 1 || !d_center || !d_halfw)
+    return GMQ_ERR_INVALID;
+  int64_t n = 1;
+  for (int k = 0; k < dim; ++k) {
+    n *= s;
+    if (n > kMaxRegions) return GMQ_ERR_INVALID;
+  }
+  if (ld < n) return GMQ_ERR_INVALID;
+  PartArgs PA;
+  std::memset(&PA, 0, sizeof(PA));
+  PA.d = dim;
+  PA.s = s;
+  PA.n = n;
+  for (int k = 0; k < dim; ++k) {
+    const double l = lo ? lo[k] : 0.0, h = hi ? hi[k] : 1.0;
+    if (!std::isfinite(l) || !std::isfinite(h) || !(h > l)) return GMQ_ERR_INVALID;
+    PA.lo[k] = l;
+    PA.h[k] = (h - l) / (2.0 * (double)s);
+  }
+  PA.c_out = d_center;
+  PA.h_out = d_halfw;
+  PA.ld = ld;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  prof_begin(ctx, kKPartition);
+  GMQ_CK(launch_partition(PA, ctx->stream));
+  prof_end(ctx, kKPartition, n);
+  ctx->launches += 1;
+  GMQ_CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  return GMQ_OK;
+}
+
+gmq_status gmq_profile_enable(gmq_context* ctx, int32_t on) {
+  if (!ctx) return GMQ_ERR_INVALID;
+  if (on && !ctx->ev_made) {
+    DeviceGuard g(ctx->device);
+    for (int k = 0; k < 5; ++k)
+      for (int j = 0; j < 2; ++j)
+        if (cudaEventCreate(&ctx->ev[k][j]) != cudaSuccess) return GMQ_ERR_CUDA;
+    ctx->ev_made = true;
+  }
+  ctx->prof_on = on != 0;
+  return GMQ_OK;
+}
+
+gmq_status gmq_profile_reset(gmq_context* ctx) {
+  if (!ctx) return GMQ_ERR_INVALID;
+  for (int k = 0; k < 5; ++k) {
+    ctx->stats[k] = gmq_kernel_stats{0, 0, 0.0};
+    ctx->pending[k] = false;
+  }
+  return GMQ_OK;
+}
+
+gmq_status gmq_profile_read(gmq_context* ctx, int32_t kernel, gmq_kernel_stats* out) {
+  if (!ctx || !out || kernel < 0 || kernel > 4) return GMQ_ERR_INVALID;
+  *out = ctx->stats[kernel];
+  return GMQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,27 @@
+// sweep_kernels.cuh -- launchers of the per-sweep kernels (sums, classify,
+// split, partition) defined in sweep_kernels.cu.
+#pragma once
+
+#include "gmq_common.cuh"
+
+namespace gmq {
+
+struct PartArgs {
+  int32_t d;
+  int32_t s;
+  int64_t n;  // s^d
+  double lo[GMQ_MAX_DIM];
+  double h[GMQ_MAX_DIM];  // (hi - lo) / (2 s), computed on the host
+  double* c_out;
+  double* h_out;
+  int64_t ld;
+};
+
+cudaError_t launch_sum_status(const SweepArgs& S, cudaStream_t s);
+cudaError_t launch_classify(const SweepArgs& S, cudaStream_t s);
+cudaError_t launch_split(const SweepArgs& S, cudaStream_t s);
+cudaError_t launch_partition(const PartArgs& P, cudaStream_t s);
+cudaError_t launch_tree_sum(const double* v, int64_t n, double* blk, DevStatus* st, double* out,
+                            cudaStream_t s);
+
+}  // namespace gmq

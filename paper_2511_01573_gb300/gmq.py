@@ -1,0 +1,328 @@
+"""Python binding of the C ABI in ``include/gmq.h`` (ctypes).
+
+Argument marshalling only: every step of the quadrature runs in the CUDA
+library.  PyTorch supplies device memory (tensors) and the current stream.
+The names follow the C calls without the ``gmq_`` prefix.  If the library
+has not been built the import fails loudly; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libgmq.so")
+
+MAX_DIM = 16
+
+OK, CAP_REACHED, MAX_ITERS, ROUNDOFF_LIMIT = 0, 1, 2, 3
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5
+
+(OSCILLATORY, PRODUCT_PEAK, CORNER_PEAK, GAUSSIAN, C0, DISCONTINUOUS,
+ POLY_SUMSQ11) = range(7)
+FP64, MIXED = 0, 1
+VOLUME_SHARE, LOCAL_REL = 0, 1
+
+_dp = C.POINTER(C.c_double)
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("family", C.c_int32), ("lo", _dp), ("hi", _dp),
+                ("a", _dp), ("u", _dp)]
+
+
+class Options(C.Structure):
+    _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_regions", C.c_int64),
+                ("init_splits", C.c_int32), ("max_iters", C.c_int32), ("precision", C.c_int32),
+                ("classifier", C.c_int32), ("lanes", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("integral", C.c_double), ("error", C.c_double),
+                ("regions_evaluated", C.c_int64), ("function_evals", C.c_int64),
+                ("final_active", C.c_int64), ("iterations", C.c_int32), ("status", C.c_int32)]
+
+
+class KernelStats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("regions", C.c_int64), ("ms", C.c_double)]
+
+
+KERNELS = ("rule", "sum", "classify", "split", "partition")
+
+
+class Sweep(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_split", C.c_int64), ("I", C.c_double), ("E", C.c_double),
+                ("I_ret", C.c_double), ("E_ret", C.c_double), ("budget", C.c_double)]
+
+
+EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_pool_bytes",
+           "gmq_default_options", "gmq_integrate", "gmq_last_trace", "gmq_seed_genz",
+           "gmq_status_string", "gmq_launch_count", "gmq_eval_rule", "gmq_classify_split",
+           "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
+           "gmq_profile_read")
+
+
+class GmqError(RuntimeError):
+    def __init__(self, call, code):
+        self.code = code
+        super().__init__(f"{call} failed: {status_string(code)} ({code})")
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (ctypes); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                          "(run __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "gmq_create": [C.POINTER(vp), C.c_int, C.c_size_t],
+        "gmq_destroy": [vp],
+        "gmq_set_stream": [vp, vp],
+        "gmq_set_pool": [vp, vp, C.c_size_t],
+        "gmq_pool_bytes": [i32, i64, C.POINTER(C.c_size_t)],
+        "gmq_default_options": [C.POINTER(Options)],
+        "gmq_integrate": [vp, C.POINTER(Problem), C.POINTER(Options), C.POINTER(Result)],
+        "gmq_last_trace": [vp, C.POINTER(Sweep), i32, C.POINTER(i32)],
+        "gmq_seed_genz": [C.c_uint64, i32, i32, dbl, _dp, _dp],
+        "gmq_launch_count": [vp, C.POINTER(i64)],
+        "gmq_eval_rule": [vp, C.POINTER(Problem), i32, i32, i64, vp, vp, i64, vp, vp, vp, vp],
+        "gmq_classify_split": [vp, i32, i64, vp, vp, i64, vp, vp, vp, vp, dbl, dbl, i32, vp, vp,
+                               i64, i64, vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)],
+        "gmq_tree_sum": [vp, i64, vp, C.POINTER(dbl)],
+        "gmq_partition": [vp, i32, _dp, _dp, i32, vp, vp, i64],
+        "gmq_profile_enable": [vp, i32],
+        "gmq_profile_reset": [vp],
+        "gmq_profile_read": [vp, i32, C.POINTER(KernelStats)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.gmq_status_string.argtypes = [C.c_int]
+    L.gmq_status_string.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().gmq_status_string(int(code)).decode()
+
+
+def _check(call, code, ok=(OK,)):
+    if code not in ok:
+        raise GmqError(call, code)
+    return code
+
+
+def _f64(x, d=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if d is not None and a.shape != (d,):
+        raise ValueError(f"expected {d} values, got shape {a.shape}")
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def pool_bytes(dim: int, max_regions: int) -> int:
+    out = C.c_size_t()
+    _check("gmq_pool_bytes", lib().gmq_pool_bytes(dim, max_regions, C.byref(out)))
+    return int(out.value)
+
+
+def default_options() -> Options:
+    o = Options()
+    _check("gmq_default_options", lib().gmq_default_options(C.byref(o)))
+    return o
+
+
+def seed_genz(seed: int, family: int, dim: int, target_sum: float):
+    a = np.zeros(dim)
+    u = np.zeros(dim)
+    _check("gmq_seed_genz", lib().gmq_seed_genz(seed, family, dim, target_sum, _ptr(a), _ptr(u)))
+    return a, u
+
+
+@dataclass
+class IntegrateResult:
+    integral: float
+    error: float
+    regions_evaluated: int
+    function_evals: int
+    final_active: int
+    iterations: int
+    status: int
+
+    @property
+    def status_str(self) -> str:
+        return status_string(self.status)
+
+
+class _ProblemHandle:
+    def __init__(self, family, a, u, lo, hi, dim=None):
+        d = dim if dim is not None else len(np.atleast_1d(a))
+        self.a = _f64(np.zeros(d) if a is None else a, d)
+        self.u = _f64(np.zeros(d) if u is None else u, d)
+        self.lo = _f64(np.zeros(d) if lo is None else lo, d)
+        self.hi = _f64(np.ones(d) if hi is None else hi, d)
+        self.s = Problem(d, int(family), _ptr(self.lo), _ptr(self.hi), _ptr(self.a), _ptr(self.u))
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One library context on one CUDA device; runs on torch's current stream
+    of that device unless ``set_stream`` says otherwise."""
+
+    def __init__(self, device: int = 0, pool_bytes_hint: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = device
+        h = C.c_void_p()
+        _check("gmq_create", lib().gmq_create(C.byref(h), device, pool_bytes_hint))
+        self.h = h
+        self.set_stream(stream if stream is not None else torch.cuda.current_stream(device))
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check("gmq_set_stream", lib().gmq_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def set_pool(self, tensor):
+        """Use a caller-owned uint8 CUDA tensor as the region pool (None to undo)."""
+        self._pool = tensor
+        if tensor is None:
+            _check("gmq_set_pool", lib().gmq_set_pool(self.h, None, 0))
+        else:
+            _check("gmq_set_pool", lib().gmq_set_pool(self.h, _dptr(tensor), tensor.numel()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gmq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, on: bool = True):
+        """Time every kernel launch with CUDA events on the context stream."""
+        _check("gmq_profile_enable", lib().gmq_profile_enable(self.h, 1 if on else 0))
+
+    def profile_reset(self):
+        _check("gmq_profile_reset", lib().gmq_profile_reset(self.h))
+
+    def profile_read(self):
+        out = {}
+        for k, name in enumerate(KERNELS):
+            s = KernelStats()
+            _check("gmq_profile_read", lib().gmq_profile_read(self.h, k, C.byref(s)))
+            out[name] = {"launches": int(s.launches), "regions": int(s.regions), "ms": s.ms}
+        return out
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        _check("gmq_launch_count", lib().gmq_launch_count(self.h, C.byref(n)))
+        return int(n.value)
+
+    def integrate(self, family, a=None, u=None, rel_tol=1e-6, lo=None, hi=None, abs_tol=1e-16,
+                  max_regions=1 << 22, init_splits=0, max_iters=0, precision=FP64,
+                  classifier=VOLUME_SHARE, lanes=0, dim=None, check=True) -> IntegrateResult:
+        p = _ProblemHandle(family, a, u, lo, hi, dim)
+        o = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, precision, classifier,
+                    lanes, 0)
+        r = Result()
+        code = lib().gmq_integrate(self.h, C.byref(p.s), C.byref(o), C.byref(r))
+        if check:
+            _check("gmq_integrate", code, ok=(OK, CAP_REACHED, MAX_ITERS, ROUNDOFF_LIMIT))
+        return IntegrateResult(r.integral, r.error, r.regions_evaluated, r.function_evals,
+                               r.final_active, r.iterations, code)
+
+    def last_trace(self):
+        cnt = C.c_int32()
+        lib().gmq_last_trace(self.h, None, 0, C.byref(cnt))
+        arr = (Sweep * max(1, cnt.value))()
+        _check("gmq_last_trace", lib().gmq_last_trace(self.h, arr, cnt.value, C.byref(cnt)))
+        return [dict(n=s.n, n_split=s.n_split, I=s.I, E=s.E, I_ret=s.I_ret, E_ret=s.E_ret,
+                     budget=s.budget) for s in arr[:cnt.value]]
+
+    # ---- step-level calls on torch CUDA tensors -------------------------
+
+    def _dev(self, t, dtype):
+        torch = self.torch
+        if not (t.is_cuda and t.dtype == dtype):
+            raise ValueError(f"expected a CUDA {dtype} tensor")
+        return t
+
+    def eval_rule(self, family, a, u, center, halfw, lo=None, hi=None, precision=FP64, lanes=0):
+        """center, halfw: CUDA float64 tensors [dim, n] with unit stride along
+        regions.  Returns (I7, err, volfrac, axis) tensors of length n."""
+        torch = self.torch
+        center = self._dev(center, torch.float64)
+        halfw = self._dev(halfw, torch.float64)
+        d, n = center.shape
+        if halfw.shape != center.shape or center.stride(1) != 1 or halfw.stride(0) != center.stride(0):
+            raise ValueError("center/halfw must share shape [dim, n] and row stride")
+        p = _ProblemHandle(family, a, u, lo, hi, d)
+        dev = center.device
+        i7 = torch.empty(n, dtype=torch.float64, device=dev)
+        err = torch.empty(n, dtype=torch.float64, device=dev)
+        vf = torch.empty(n, dtype=torch.float64, device=dev)
+        ax = torch.empty(n, dtype=torch.uint8, device=dev)
+        _check("gmq_eval_rule", lib().gmq_eval_rule(
+            self.h, C.byref(p.s), precision, lanes, n, _dptr(center), _dptr(halfw),
+            center.stride(0), _dptr(i7), _dptr(err), _dptr(vf), _dptr(ax)))
+        return i7, err, vf, ax
+
+    def classify_split(self, center, halfw, i7, err, volfrac, axis, budget, rel_tol=0.0,
+                       classifier=VOLUME_SHARE, cap_out=None):
+        torch = self.torch
+        d, n = center.shape
+        cap = 2 * n if cap_out is None else cap_out
+        dev = center.device
+        co = torch.zeros((d, max(cap, 1)), dtype=torch.float64, device=dev)
+        ho = torch.zeros((d, max(cap, 1)), dtype=torch.float64, device=dev)
+        flags = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+        ns = C.c_int64()
+        ri = C.c_double()
+        re_ = C.c_double()
+        code = lib().gmq_classify_split(
+            self.h, d, n, _dptr(center), _dptr(halfw), center.stride(0), _dptr(i7), _dptr(err),
+            _dptr(volfrac) if volfrac is not None else None, _dptr(axis), budget, rel_tol,
+            classifier, _dptr(co), _dptr(ho), co.stride(0), cap, _dptr(flags), C.byref(ns),
+            C.byref(ri), C.byref(re_))
+        _check("gmq_classify_split", code, ok=(OK, CAP_REACHED))
+        k = int(ns.value)
+        return dict(status=code, n_split=k, ret_i=ri.value, ret_e=re_.value, flags=flags[:n],
+                    center=co[:, :2 * k], halfw=ho[:, :2 * k])
+
+    def tree_sum(self, v) -> float:
+        v = self._dev(v, self.torch.float64).contiguous()
+        out = C.c_double()
+        _check("gmq_tree_sum", lib().gmq_tree_sum(self.h, v.numel(), _dptr(v), C.byref(out)))
+        return out.value
+
+    def partition(self, dim, s, lo=None, hi=None):
+        torch = self.torch
+        lo = _f64(np.zeros(dim) if lo is None else lo, dim)
+        hi = _f64(np.ones(dim) if hi is None else hi, dim)
+        n = s ** dim
+        c = torch.empty((dim, n), dtype=torch.float64, device=f"cuda:{self.device}")
+        h = torch.empty_like(c)
+        _check("gmq_partition", lib().gmq_partition(self.h, dim, _ptr(lo), _ptr(hi), s, _dptr(c),
+                                                     _dptr(h), n))
+        return c, h

@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances (FP64 path):
+* per region: |dI7| and |d eps| <= 1e-12 * scale_r, where scale_r =
+  vol_r * sum_c |w_c| sum_{nodes in c} |f| is the magnitude of the terms the
+  rule adds (|I7_r| itself can cancel, e.g. for the oscillatory family);
+* volume fractions, split axes (outside the oracle's near-tie flag), the
+  round-off guard bit, classification flags, split counts, child coordinates
+  and pairwise-tree sums of identical inputs: bit-exact;
+* end to end: the same sweeps, region counts and statuses when the oracle
+  reports no near-tie decision, and the integral within 1e-12 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_01573_gb300 import genz_inputs as G
+from tests import closed_forms as CF
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _soa(x):
+    return torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device="cuda")
+
+
+def _params(fam, d, seed=3):
+    if fam == G.PRODUCT_PEAK:
+        return G.seed_genz(seed, fam, d, 5.0 * d)
+    if fam == G.DISCONTINUOUS:
+        a, u = G.seed_genz(seed, fam, d, 2.0)
+        return a, 0.3 + 0.6 * u
+    if fam == G.POLY_SUMSQ11:
+        return np.zeros(d), np.zeros(d)
+    return G.seed_genz(seed, fam, d, G.GENZ_TARGET_SUM.get(fam, 2.0))
+
+
+def _region_count(d):
+    return {1: 2500, 2: 2100, 3: 1100, 4: 700, 5: 400, 6: 300, 8: 150, 10: 40, 12: 12,
+            16: 1}.get(d, 100)
+
+
+def _compare_rule(oracle, gpu_ctx, fam, d, lanes, n=None, seed=3, boxes=None):
+    a, u = _params(fam, d, seed)
+    if boxes is None:
+        n = n or _region_count(d)
+        c, h = G.random_boxes(seed + 10 * d, n, d)
+    else:
+        c, h = boxes
+        n = len(c)
+    o = oracle.rule_regions(fam, a, u, c, h)
+    i7, err, vf, ax = gpu_ctx.eval_rule(fam, a, u, _soa(c), _soa(h), lanes=lanes)
+    i7 = i7.cpu().numpy()
+    err = err.cpu().numpy()
+    vf = vf.cpu().numpy()
+    ax = ax.cpu().numpy().astype(np.int32)
+    scale = o["i7abs"]
+    assert np.all(np.abs(i7 - o["i7"]) <= 1e-12 * scale), (fam, d, lanes)
+    assert np.all(np.abs(err - o["err"]) <= 1e-12 * scale), (fam, d, lanes)
+    assert np.array_equal(vf, o["vol"] / 1.0)
+    tie = o["axis_tie"].astype(bool)
+    assert np.array_equal((ax & 0x7F)[~tie], o["axis"][~tie]), (fam, d, lanes)
+    assert np.array_equal((ax >> 7)[~tie], o["split_bad"][~tie])
+    return o, (i7, err, vf, ax)
+
+
+@pytest.mark.parametrize("fam", range(7))
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+def test_rule_per_region(oracle, gpu_ctx, fam, d, lanes):
+    _compare_rule(oracle, gpu_ctx, fam, d, lanes)
+
+
+@pytest.mark.parametrize("fam", [G.OSCILLATORY, G.GAUSSIAN, G.CORNER_PEAK, G.C0])
+@pytest.mark.parametrize("lanes", [1, 32])
+def test_rule_d12(oracle, gpu_ctx, fam, lanes):
+    _compare_rule(oracle, gpu_ctx, fam, 12, lanes)
+
+
+def test_rule_max_dim(oracle, gpu_ctx):
+    # GMQ_MAX_DIM = 16: 66081 nodes per region, one region per lane mapping
+    for lanes in (1, 32):
+        _compare_rule(oracle, gpu_ctx, G.GAUSSIAN, 16, lanes, n=1)
+
+
+def test_rule_auto_lanes_and_ragged(oracle, gpu_ctx):
+    # tile edges: n = 1, RB - 1, RB + 1 for every lane count; automatic choice
+    for n in (1, 3, 4, 5, 31, 33, 127, 129):
+        for lanes in (0, 1, 4, 32):
+            _compare_rule(oracle, gpu_ctx, G.C0, 4, lanes, n=n, seed=n)
+
+
+def test_rule_on_partition_boxes_exact_axis_ties(oracle, gpu_ctx):
+    # symmetric boxes of a symmetric integrand: exact axis ties must resolve
+    # to the lowest index on both sides
+    c, h = oracle.partition(np.zeros(3), np.ones(3), 4)
+    a, u = np.full(3, 2.0), np.full(3, 0.5)
+    o = oracle.rule_regions(G.GAUSSIAN, a, u, c, h)
+    i7, err, vf, ax = gpu_ctx.eval_rule(G.GAUSSIAN, a, u, _soa(c), _soa(h))
+    assert np.array_equal(ax.cpu().numpy() & 0x7F, o["axis"])
+
+
+def test_tree_sum_bit_exact(oracle, gpu_ctx):
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 5, 1023, 1024, 1025, 4097, 100003, 3_000_001):
+        v = rng.standard_normal(n) * np.exp(rng.uniform(-30, 30, n))
+        got = gpu_ctx.tree_sum(torch.tensor(v, device="cuda"))
+        assert got == oracle.pairwise_sum(v), n
+
+
+def test_partition_bit_exact(oracle, gpu_ctx):
+    for d, s, lo, hi in ((3, 16, [0, 0, 0], [1, 1, 1]), (2, 7, [-1.5, 0.1], [2.0, 0.3]),
+                         (8, 2, [0] * 8, [1] * 8), (1, 4096, [0.0], [3.0])):
+        c, h = gpu_ctx.partition(d, s, lo, hi)
+        oc, oh = oracle.partition(lo, hi, s)
+        assert np.array_equal(c.cpu().numpy().T, oc) and np.array_equal(h.cpu().numpy().T, oh)
+
+
+@pytest.mark.parametrize("fam,d,n", [(G.C0, 3, 5000), (G.GAUSSIAN, 5, 3000),
+                                     (G.OSCILLATORY, 2, 70000), (G.DISCONTINUOUS, 4, 2000)])
+def test_classify_split_decisions_bit_exact(oracle, gpu_ctx, fam, d, n):
+    """Feed the GPU classify/split the oracle's per-region outputs: flags,
+    counts, retired sums and children must equal the oracle's bit for bit."""
+    a, u = _params(fam, d)
+    c, h = G.random_boxes(77 + d, n, d)
+    o = oracle.rule_regions(fam, a, u, c, h)
+    vol_omega = 1.0
+    vf = o["vol"] / vol_omega
+    axis_byte = (o["axis"] | (o["split_bad"] << 7)).astype(np.uint8)
+    I = oracle.pairwise_sum(o["i7"])
+    for tol in (1e-3, 1e-5, 1e-7):
+        budget = max(1e-16, tol * abs(I))
+        for classifier in (0, 1):
+            ref = oracle.classify(o["i7"], o["err"], o["vol"], o["split_bad"], vol_omega,
+                                  budget, rel_tol=tol, classifier=classifier)
+            got = gpu_ctx.classify_split(
+                _soa(c), _soa(h), torch.tensor(o["i7"], device="cuda"),
+                torch.tensor(o["err"], device="cuda"), torch.tensor(vf, device="cuda"),
+                torch.tensor(axis_byte, device="cuda"), budget, rel_tol=tol,
+                classifier=classifier)
+            assert got["n_split"] == ref["n_split"]
+            assert np.array_equal(got["flags"].cpu().numpy(), ref["flags"])
+            assert got["ret_i"] == ref["ret_i"] and got["ret_e"] == ref["ret_e"]
+            co, ho = oracle.bisect(c, h, o["axis"], ref["flags"])
+            assert np.array_equal(got["center"].cpu().numpy().T, co)
+            assert np.array_equal(got["halfw"].cpu().numpy().T, ho)
+
+
+def test_classify_split_cap_and_empty(oracle, gpu_ctx):
+    d, n = 3, 3000
+    a, u = _params(G.C0, d)
+    c, h = G.random_boxes(5, n, d)
+    i7, err, vf, ax = gpu_ctx.eval_rule(G.C0, a, u, _soa(c), _soa(h))
+    # tiny budget: everything splits; a cap below 2 n_split refuses to write
+    got = gpu_ctx.classify_split(_soa(c), _soa(h), i7, err, vf, ax, 0.0, cap_out=100)
+    assert got["status"] == 1 and got["n_split"] == n
+    # huge budget: everything retires
+    got = gpu_ctx.classify_split(_soa(c), _soa(h), i7, err, vf, ax, 1e300)
+    assert got["n_split"] == 0
+    ref = oracle.pairwise_sum(i7.cpu().numpy())
+    assert got["ret_i"] == ref
+
+
+def _e2e(oracle, gpu_ctx, fam, a, u, tol, cap=1 << 20, lanes=0, **kw):
+    o = oracle.integrate(fam, a, u, tol, max_regions=cap, **kw)
+    g = gpu_ctx.integrate(fam, a, u, tol, max_regions=cap, lanes=lanes, **kw)
+    tr = gpu_ctx.last_trace()
+    if o.near_ties == 0:
+        assert g.status == o.status
+        assert g.iterations == o.iterations
+        assert g.regions_evaluated == o.regions_evaluated
+        assert [t["n"] for t in tr] == [t["n"] for t in o.trace]
+        assert [t["n_split"] for t in tr] == [t["n_split"] for t in o.trace]
+        assert abs(g.integral - o.integral) <= 1e-12 * abs(o.integral) + 1e-300
+        assert abs(g.error - o.error) <= 1e-12 * abs(o.integral) + 1e-300
+    return o, g
+
+
+def test_e2e_product_peak_d3(oracle, gpu_ctx):
+    p = G.product_peak_d3()
+    o, g = _e2e(oracle, gpu_ctx, p.family, p.a, p.u, p.rel_tol, cap=100000)
+    assert g.status == 0
+    ex = (10 * math.atan(2.5)) ** 3
+    assert abs(g.integral - ex) <= 1e-6 * ex
+
+
+@pytest.mark.parametrize("fam", range(7))
+@pytest.mark.parametrize("d,tol", [(2, 1e-9), (3, 1e-7), (5, 1e-5)])
+def test_e2e_families(oracle, gpu_ctx, fam, d, tol):
+    a, u = _params(fam, d, seed=5)
+    o, g = _e2e(oracle, gpu_ctx, fam, a, u, tol)
+    if g.status == 0 and fam != G.GAUSSIAN:
+        ex = CF.exact(fam, a, u) if fam != G.DISCONTINUOUS else CF.discontinuous(a, u)
+        assert abs(g.integral - ex) <= tol * abs(ex) * 1.0001
+
+
+@pytest.mark.parametrize("fam", G.GENZ_D8_FAMILIES)
+@pytest.mark.parametrize("tol", [1e-3, 1e-4])
+def test_e2e_genz_d8(oracle, gpu_ctx, fam, tol):
+    a, u = G.seed_genz(1, fam, 8, G.GENZ_TARGET_SUM[fam])
+    _e2e(oracle, gpu_ctx, fam, a, u, tol, cap=1 << 24)
+
+
+def test_e2e_paper_integrands(oracle, gpu_ctx):
+    for idx in range(1, 8):
+        p = G.paper_integrand(idx, 3)
+        _e2e(oracle, gpu_ctx, p.family, p.a, p.u, 1e-5, cap=1 << 22)
+
+
+def test_e2e_lane_choices_agree(gpu_ctx):
+    a, u = G.seed_genz(2, G.C0, 4, 2.0)
+    rs = [gpu_ctx.integrate(G.C0, a, u, 1e-6, lanes=t) for t in (1, 4, 32, 0)]
+    for r in rs[1:]:
+        assert r.iterations == rs[0].iterations
+        assert r.regions_evaluated == rs[0].regions_evaluated
+        assert abs(r.integral - rs[0].integral) <= 1e-13 * abs(rs[0].integral)
+
+
+def test_e2e_status_paths(oracle, gpu_ctx):
+    f6 = G.paper_integrand(6, 3)
+    o, g = _e2e(oracle, gpu_ctx, f6.family, f6.a, f6.u, 1e-12, cap=1000)
+    assert g.status == 1 == o.status
+    a, u = G.seed_genz(1, G.C0, 3, 2.0)
+    g = gpu_ctx.integrate(G.C0, a, u, 1e-9, max_iters=3)
+    assert g.status == 2 and g.iterations == 3
+    g = gpu_ctx.integrate(G.CORNER_PEAK, [-2.0], [0.0], 1e-6, init_splits=1)
+    assert g.status == -4
+    from paper_2511_01573_gb300 import gmq
+    with pytest.raises(gmq.GmqError):
+        gpu_ctx.integrate(G.C0, a, u, 1e-6, lo=[0, 0, 0], hi=[1, 0, 1])
+    with pytest.raises(gmq.GmqError):
+        gpu_ctx.integrate(G.C0, a, u, -1.0)
+    with pytest.raises(gmq.GmqError):
+        gpu_ctx.integrate(G.C0, a, u, 1e-6, lanes=3)
+
+
+def test_e2e_caller_pool(gpu_ctx):
+    from paper_2511_01573_gb300 import gmq
+    a, u = G.seed_genz(3, G.GAUSSIAN, 6, 3.5)
+    ref = gpu_ctx.integrate(G.GAUSSIAN, a, u, 1e-7, max_regions=1 << 18)
+    need = gmq.pool_bytes(6, 1 << 18)
+    pool = torch.empty(need, dtype=torch.uint8, device="cuda")
+    gpu_ctx.set_pool(pool)
+    try:
+        got = gpu_ctx.integrate(G.GAUSSIAN, a, u, 1e-7, max_regions=1 << 18)
+        assert got.integral == ref.integral and got.regions_evaluated == ref.regions_evaluated
+        with pytest.raises(gmq.GmqError):
+            gpu_ctx.integrate(G.GAUSSIAN, a, u, 1e-7, max_regions=1 << 19)
+    finally:
+        gpu_ctx.set_pool(None)
