@@ -13,14 +13,19 @@
 //      decoded from the bits of i (centre; 4d axis nodes; 4 sign patterns
 //      per axis pair; the 2^d sign patterns of the last class are the bits
 //      of i itself), and its coordinates are read from the table, so the
-//      only FP64 work per node is the integrand and one accumulation;
+//      only floating-point work per node is the integrand and one
+//      accumulation;
 //   3. reduces the five class sums over the T lanes with warp shuffles,
 //      finds the split axis (argmax of the fourth differences) with a
 //      shuffle argmax, and writes I7, |I7 - I5|, vol / vol(Omega) and the
 //      axis byte.
-// With T = 1 the class sums are accumulated in the same node order as the
-// plain definition (centre; per axis +l2, -l2, +l3, -l3; pairs j < k with
-// sign patterns ++, +-, -+, --; sign patterns m = 0 .. 2^d - 1).
+// Real = double: every step in FP64.  Real = float (mixed form): node
+// coordinates are formed in FP64 and rounded to FP32, the integrand runs in
+// FP32 and the class sums are FP32 with TwoSum compensation; class sums,
+// fourth differences, axis choice, rule values and error estimate are FP64.
+// With T = 1 and Real = double the class sums are accumulated in the same
+// node order as the plain definition (centre; per axis +l2, -l2, +l3, -l3;
+// pairs j < k with sign patterns ++, +-, -+, --; patterns m = 0 .. 2^d-1).
 #pragma once
 
 #include "gmq_common.cuh"
@@ -28,24 +33,32 @@
 
 namespace gmq {
 
-// Shared-memory bytes of the rule kernel for dimension d and T lanes.
-inline size_t rule_smem_bytes(int d, int T) {
+// Node-coordinate rows of the shared-memory table (lambda4 == lambda3, so
+// pair nodes reuse rows P3/M3).
+enum XRow { kXC = 0, kXP2 = 1, kXM2 = 2, kXP3 = 3, kXM3 = 4, kXP5 = 5, kXM5 = 6, kXRows = 7 };
+
+// Shared-memory bytes of the rule kernel for dimension d, T lanes and an
+// integrand type of `real_bytes` bytes.
+inline size_t rule_smem_bytes(int d, int T, int real_bytes) {
   const int RB = kRuleBlock / T;
-  size_t dbl = (size_t)kRows * d * RB;
-  if (T > 1) dbl += (size_t)4 * d * RB + RB;
-  size_t bytes = dbl * sizeof(double) + sizeof(SmemParams) + sizeof(unsigned short) * 128;
+  size_t bytes = sizeof(double) * (size_t)2 * d * RB;          // centres, half-widths
+  if (T > 1) bytes += sizeof(double) * ((size_t)4 * d * RB + RB);  // axis-node values, f(c)
+  bytes += (size_t)real_bytes * kXRows * d * RB;                 // node coordinates
+  bytes += sizeof(SmemParams<double>) + sizeof(unsigned short) * 128;
   return (bytes + 15) & ~(size_t)15;
 }
 
-template <int FAM, int T>
-__global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
+template <int FAM, int T, class Real>
+__global__ void __launch_bounds__(kRuleBlock) k_rule(const RuleArgs A) {
   constexpr int RB = kRuleBlock / T;
   extern __shared__ __align__(16) double smem[];
   const int d = A.P.d;
-  double* tab = smem;  // [kRows][d][RB]
-  double* fv = tab + kRows * d * RB;            // [4][d][RB]   (T > 1)
-  double* f0s = fv + (T > 1 ? 4 * d * RB : 0);  // [RB]         (T > 1)
-  SmemParams* P = reinterpret_cast<SmemParams*>(f0s + (T > 1 ? RB : 0));
+  double* cd = smem;                              // [d][RB] centres
+  double* hd = cd + d * RB;                       // [d][RB] half-widths
+  double* fv = hd + d * RB;                       // [4][d][RB] axis-node values (T > 1)
+  double* f0s = fv + (T > 1 ? 4 * d * RB : 0);    // [RB] f(c)                   (T > 1)
+  Real* xt = reinterpret_cast<Real*>(f0s + (T > 1 ? RB : 0));  // [kXRows][d][RB]
+  SmemParams<Real>* P = reinterpret_cast<SmemParams<Real>*>(xt + kXRows * d * RB);
   unsigned short* pairs = reinterpret_cast<unsigned short*>(P + 1);
 
   const int tid = threadIdx.x;
@@ -53,11 +66,11 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
 
   // integrand parameters and the (j, k) pair table, j < k lexicographic
   for (int j = tid; j < d; j += kRuleBlock) {
-    P->a[j] = A.P.a[j];
-    P->u[j] = A.P.u[j];
-    P->b[j] = A.P.b[j];
+    P->a[j] = (Real)A.P.a[j];
+    P->u[j] = (Real)A.P.u[j];
+    P->b[j] = (Real)A.P.b[j];
   }
-  if (tid == 0) P->c0 = A.P.c0;
+  if (tid == 0) P->c0 = (Real)A.P.c0;
   const int npairs = d * (d - 1) / 2;
   for (int p = tid; p < npairs; p += kRuleBlock) {
     int j = 0, rem = p;
@@ -78,14 +91,15 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
       cv = A.c[(int64_t)k * A.ld + r];
       hv = A.h[(int64_t)k * A.ld + r];
     }
-    tab[(kC * d + k) * RB + q] = cv;
-    tab[(kH * d + k) * RB + q] = hv;
-    tab[(kP2 * d + k) * RB + q] = fma(l2, hv, cv);
-    tab[(kM2 * d + k) * RB + q] = fma(-l2, hv, cv);
-    tab[(kP3 * d + k) * RB + q] = fma(l3, hv, cv);
-    tab[(kM3 * d + k) * RB + q] = fma(-l3, hv, cv);
-    tab[(kP5 * d + k) * RB + q] = fma(l5, hv, cv);
-    tab[(kM5 * d + k) * RB + q] = fma(-l5, hv, cv);
+    cd[k * RB + q] = cv;
+    hd[k * RB + q] = hv;
+    xt[(kXC * d + k) * RB + q] = (Real)cv;
+    xt[(kXP2 * d + k) * RB + q] = (Real)fma(l2, hv, cv);
+    xt[(kXM2 * d + k) * RB + q] = (Real)fma(-l2, hv, cv);
+    xt[(kXP3 * d + k) * RB + q] = (Real)fma(l3, hv, cv);
+    xt[(kXM3 * d + k) * RB + q] = (Real)fma(-l3, hv, cv);
+    xt[(kXP5 * d + k) * RB + q] = (Real)fma(l5, hv, cv);
+    xt[(kXM5 * d + k) * RB + q] = (Real)fma(-l5, hv, cv);
   }
   __syncthreads();
 
@@ -94,17 +108,17 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
   const int64_t r = r0 + g;
   const bool active = r < A.n;
   const int N = (int)A.R.nodes;
-  const int b4 = 1 + 4 * d;               // first pair node
-  const int b5 = b4 + 2 * d * (d - 1);    // first sign-class node
+  const int b4 = 1 + 4 * d;             // first pair node
+  const int b5 = b4 + 2 * d * (d - 1);  // first sign-class node
   const double ratio = A.R.ratio;
 
-  double S1 = 0.0, S2 = 0.0, S3 = 0.0, S4 = 0.0, S5 = 0.0;
+  Acc<Real> S1, S2, S3, S4, S5;
   double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
   int kbest = 0;
 
   if (active) {
     for (int i = lane; i < N; i += T) {
-      int kind, k1 = -1, r1 = kC, k2 = -1, r2 = kC, w = 0;
+      int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
       unsigned m = 0u;
       if (i == 0) {
         kind = 1;
@@ -112,53 +126,54 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
         const int q = i - 1;
         k1 = q >> 2;
         w = q & 3;
-        r1 = kP2 + w;
+        r1 = kXP2 + w;
         kind = (w < 2) ? 2 : 3;
       } else if (i < b5) {
         const int q = i - b4;
         const unsigned pr = pairs[q >> 2];
         k1 = (int)(pr >> 8);
         k2 = (int)(pr & 255u);
-        r1 = (q & 2) ? kM3 : kP3;
-        r2 = (q & 1) ? kM3 : kP3;
+        r1 = (q & 2) ? kXM3 : kXP3;
+        r2 = (q & 1) ? kXM3 : kXP3;
         kind = 4;
       } else {
         m = (unsigned)(i - b5);
         kind = 5;
       }
-      auto X = [&](int j) -> double {
+      auto X = [&](int j) -> Real {
         int row;
         if (kind == 5)
-          row = ((m >> j) & 1u) ? kM5 : kP5;
+          row = ((m >> j) & 1u) ? kXM5 : kXP5;
         else
-          row = (j == k1) ? r1 : ((j == k2) ? r2 : kC);
-        return tab[(row * d + j) * RB + g];
+          row = (j == k1) ? r1 : ((j == k2) ? r2 : kXC);
+        return xt[(row * d + j) * RB + g];
       };
-      const double v = Family<FAM>::eval(*P, d, X);
+      const Real v = Family<FAM>::template eval<Real>(*P, d, X);
       if (kind == 5) {
-        S5 += v;
+        S5.add(v);
       } else if (kind == 4) {
-        S4 += v;
+        S4.add(v);
       } else if (kind == 1) {
-        S1 += v;
-        f0 = v;
-        if (T > 1) f0s[g] = v;
+        S1.add(v);
+        f0 = (double)v;
+        if (T > 1) f0s[g] = (double)v;
       } else {
         if (kind == 2)
-          S2 += v;
+          S2.add(v);
         else
-          S3 += v;
+          S3.add(v);
+        const double vd = (double)v;
         if (T == 1) {
           if (w == 0) {
-            q0 = v;
+            q0 = vd;
           } else if (w == 1) {
-            q1 = v;
+            q1 = vd;
           } else if (w == 2) {
-            q2 = v;
+            q2 = vd;
           } else {
             const double two_f0 = __dmul_rn(2.0, f0);
             const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
-            const double t2 = __dsub_rn(__dadd_rn(q2, v), two_f0);
+            const double t2 = __dsub_rn(__dadd_rn(q2, vd), two_f0);
             const double D = fabs(__dsub_rn(t1, __dmul_rn(ratio, t2)));
             if (D > dbest) {
               dbest = D;
@@ -166,21 +181,22 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
             }
           }
         } else {
-          fv[(w * d + k1) * RB + g] = v;
+          fv[(w * d + k1) * RB + g] = vd;
         }
       }
     }
   }
 
+  double s1 = S1.value(), s2 = S2.value(), s3 = S3.value(), s4 = S4.value(), s5 = S5.value();
   if (T > 1) {
     // class sums over the group's lanes
 #pragma unroll
     for (int off = T / 2; off > 0; off >>= 1) {
-      S1 += __shfl_xor_sync(0xffffffffu, S1, off, T);
-      S2 += __shfl_xor_sync(0xffffffffu, S2, off, T);
-      S3 += __shfl_xor_sync(0xffffffffu, S3, off, T);
-      S4 += __shfl_xor_sync(0xffffffffu, S4, off, T);
-      S5 += __shfl_xor_sync(0xffffffffu, S5, off, T);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, off, T);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, off, T);
+      s3 += __shfl_xor_sync(0xffffffffu, s3, off, T);
+      s4 += __shfl_xor_sync(0xffffffffu, s4, off, T);
+      s5 += __shfl_xor_sync(0xffffffffu, s5, off, T);
     }
     __syncwarp();
     if (active) {
@@ -211,28 +227,28 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
   if (active && lane == 0) {
     // volume, rule values and error estimate
     double vol = 1.0;
-    for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, tab[(kH * d + k) * RB + g]));
+    for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, hd[k * RB + g]));
     const double* w7 = A.R.w7;
     const double* w5 = A.R.w5;
-    double s7 = __dmul_rn(w7[0], S1);
-    s7 = __dadd_rn(s7, __dmul_rn(w7[1], S2));
-    s7 = __dadd_rn(s7, __dmul_rn(w7[2], S3));
-    s7 = __dadd_rn(s7, __dmul_rn(w7[3], S4));
-    s7 = __dadd_rn(s7, __dmul_rn(w7[4], S5));
-    double s5 = __dmul_rn(w5[0], S1);
-    s5 = __dadd_rn(s5, __dmul_rn(w5[1], S2));
-    s5 = __dadd_rn(s5, __dmul_rn(w5[2], S3));
-    s5 = __dadd_rn(s5, __dmul_rn(w5[3], S4));
-    const double i7 = __dmul_rn(vol, s7);
-    const double i5 = __dmul_rn(vol, s5);
+    double t7 = __dmul_rn(w7[0], s1);
+    t7 = __dadd_rn(t7, __dmul_rn(w7[1], s2));
+    t7 = __dadd_rn(t7, __dmul_rn(w7[2], s3));
+    t7 = __dadd_rn(t7, __dmul_rn(w7[3], s4));
+    t7 = __dadd_rn(t7, __dmul_rn(w7[4], s5));
+    double t5 = __dmul_rn(w5[0], s1);
+    t5 = __dadd_rn(t5, __dmul_rn(w5[1], s2));
+    t5 = __dadd_rn(t5, __dmul_rn(w5[2], s3));
+    t5 = __dadd_rn(t5, __dmul_rn(w5[3], s4));
+    const double i7 = __dmul_rn(vol, t7);
+    const double i5 = __dmul_rn(vol, t5);
     // split axis: flat differences -> widest axis (lowest index on ties)
     const double flat_thr = __dadd_rn(__dmul_rn(1e-14, fabs(f0)), 1e-300);
     int ax = kbest;
     if (!(dbest > flat_thr)) {
       ax = 0;
-      double hb = tab[(kH * d + 0) * RB + g];
+      double hb = hd[0 * RB + g];
       for (int k = 1; k < d; ++k) {
-        const double hk = tab[(kH * d + k) * RB + g];
+        const double hk = hd[k * RB + g];
         if (hk > hb) {
           hb = hk;
           ax = k;
@@ -240,8 +256,8 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
       }
     }
     // round-off guard: bisection along ax must move the centre
-    const double cs = tab[(kC * d + ax) * RB + g];
-    const double hh = __dmul_rn(0.5, tab[(kH * d + ax) * RB + g]);
+    const double cs = cd[ax * RB + g];
+    const double hh = __dmul_rn(0.5, hd[ax * RB + g]);
     const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
     A.i7[r] = i7;
     A.err[r] = fabs(__dsub_rn(i7, i5));
@@ -254,32 +270,38 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_f64(const RuleArgs A) {
 template <int FAM>
 cudaError_t launch_rule_family(int precision, int T, const RuleArgs& A, cudaStream_t s);
 
-template <int FAM, int T>
+template <int FAM, int T, class Real>
 cudaError_t launch_rule_t(const RuleArgs& A, cudaStream_t s) {
   const int RB = kRuleBlock / T;
-  const size_t smem = rule_smem_bytes(A.P.d, T);
+  const size_t smem = rule_smem_bytes(A.P.d, T, (int)sizeof(Real));
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_rule_f64<FAM, T>,
+    cudaError_t e = cudaFuncSetAttribute(k_rule<FAM, T, Real>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const int64_t blocks = (A.n + RB - 1) / RB;
   if (blocks == 0) return cudaSuccess;
-  k_rule_f64<FAM, T><<<(unsigned)blocks, kRuleBlock, smem, s>>>(A);
+  k_rule<FAM, T, Real><<<(unsigned)blocks, kRuleBlock, smem, s>>>(A);
   return cudaGetLastError();
+}
+
+template <int FAM, class Real>
+cudaError_t launch_rule_real(int T, const RuleArgs& A, cudaStream_t s) {
+  switch (T) {
+    case 1: return launch_rule_t<FAM, 1, Real>(A, s);
+    case 4: return launch_rule_t<FAM, 4, Real>(A, s);
+    case 32: return launch_rule_t<FAM, 32, Real>(A, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 #define GMQ_DEFINE_RULE_FAMILY(FAMV)                                                   \
   template <>                                                                          \
   cudaError_t launch_rule_family<FAMV>(int precision, int T, const RuleArgs& A,         \
                                        cudaStream_t s) {                                \
-    if (precision != GMQ_FP64) return cudaErrorNotSupported;                          \
-    switch (T) {                                                                       \
-      case 1: return launch_rule_t<FAMV, 1>(A, s);                                     \
-      case 4: return launch_rule_t<FAMV, 4>(A, s);                                     \
-      case 32: return launch_rule_t<FAMV, 32>(A, s);                                   \
-      default: return cudaErrorInvalidValue;                                           \
-    }                                                                                  \
+    if (precision == GMQ_FP64) return launch_rule_real<FAMV, double>(T, A, s);         \
+    if (precision == GMQ_MIXED) return launch_rule_real<FAMV, float>(T, A, s);         \
+    return cudaErrorInvalidValue;                                                      \
   }
 
 }  // namespace gmq

@@ -53,6 +53,13 @@ namespace {
 
 constexpr int64_t kMaxRegions = (int64_t)1 << 30;
 
+// Round-off guard (paper Sec. 3): a region whose error estimate is below
+// g u |I7_r| is at the rounding level of its own rule value and is retired.
+// FP64: g = 50, u = 2^-53.  Mixed form (FP32 node values): g = 4, u = 2^-24,
+// about twice the spread that FP32 node values leave in |I7 - I5|.
+constexpr double kGuardFp64 = 50.0 * 0x1p-53;
+constexpr double kGuardMixed = 4.0 * 0x1p-24;
+
 struct DeviceGuard {
   int prev = -1;
   bool ok = true;
@@ -563,6 +570,7 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
     S.blk_a = (double*)(base + L.ba);
     S.blk_b = (double*)(base + L.bb);
     S.budget_ptr = &st->budget;
+    S.guard = opt->precision == GMQ_MIXED ? kGuardMixed : kGuardFp64;
     S.st = st;
     prof_begin(ctx, kKSum);
     GMQ_CK(launch_sum_status(S, strm));
@@ -713,6 +721,7 @@ gmq_status gmq_classify_split(gmq_context* ctx, int32_t dim, int64_t n, const do
   S.blk_b = X.bb;
   S.budget_ptr = nullptr;
   S.budget_val = budget;
+  S.guard = kGuardFp64;
   S.st = X.st;
   cudaStream_t strm = ctx->stream;
   GMQ_CK(cudaMemsetAsync(X.st, 0, sizeof(DevStatus), strm));

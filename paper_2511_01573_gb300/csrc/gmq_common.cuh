@@ -17,11 +17,6 @@ constexpr int kTile = 1024;
 // Threads per block of the rule kernel.
 constexpr int kRuleBlock = 128;
 
-// Rows of the per-region coordinate table staged in shared memory by the
-// rule kernel: centre, half-width, and the node coordinates c_k +- lambda h_k
-// of every generator (lambda4 == lambda3, so pair nodes reuse rows P3/M3).
-enum Row { kC = 0, kH = 1, kP2 = 2, kM2 = 3, kP3 = 4, kM3 = 5, kP5 = 6, kM5 = 7, kRows = 8 };
-
 // Family parameters as the device functors use them.  Filled on the host
 // from gmq_problem: a, u as given; b is a per-axis constant of the family
 // (a^-2 for the product peak, a^2 for the Gaussian); c0 a scalar
@@ -96,6 +91,7 @@ struct SweepArgs {
   double* blk_b;
   const double* budget_ptr;  // device budget (integrate path) or null
   double budget_val;         // host budget (step-level path)
+  double guard;              // round-off guard factor g*u: retire if err <= guard |I7|
   DevStatus* st;
 };
 

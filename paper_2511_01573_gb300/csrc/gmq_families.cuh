@@ -3,6 +3,7 @@
 // whose coordinates it reads through an accessor x(j), j = 0..d-1, so the
 // rule kernel never materialises the node vector.  Per-family constants
 // (a_j^2, a_j^-2, 2 pi u_1) are precomputed once per problem on the host.
+// Real = double is the FP64 path; Real = float the mixed path's integrand.
 #pragma once
 
 #include "gmq_common.cuh"
@@ -10,26 +11,23 @@
 namespace gmq {
 
 // Parameters staged in shared memory by the rule kernel.
+template <class Real>
 struct SmemParams {
-  double a[GMQ_MAX_DIM];
-  double u[GMQ_MAX_DIM];
-  double b[GMQ_MAX_DIM];
-  double c0;
+  Real a[GMQ_MAX_DIM];
+  Real u[GMQ_MAX_DIM];
+  Real b[GMQ_MAX_DIM];
+  Real c0;
 };
 
-// x^e for a positive integer exponent by binary powering.
-__device__ __forceinline__ double ipow(double x, int e) {
-  double r = 1.0;
-  while (e) {
-    if (e & 1) r *= x;
-    x *= x;
-    e >>= 1;
-  }
-  return r;
-}
+__device__ __forceinline__ double gexp(double x) { return exp(x); }
+__device__ __forceinline__ float gexp(float x) { return expf(x); }
+__device__ __forceinline__ double gcos(double x) { return cos(x); }
+__device__ __forceinline__ float gcos(float x) { return cosf(x); }
 
-__device__ __forceinline__ float ipowf(float x, int e) {
-  float r = 1.0f;
+// x^e for a positive integer exponent by binary powering.
+template <class Real>
+__device__ __forceinline__ Real ipow(Real x, int e) {
+  Real r = Real(1);
   while (e) {
     if (e & 1) r *= x;
     x *= x;
@@ -44,11 +42,11 @@ struct Family;
 // cos(2 pi u_1 + sum a_j x_j)
 template <>
 struct Family<GMQ_OSCILLATORY> {
-  template <class X>
-  __device__ __forceinline__ static double eval(const SmemParams& P, int d, X x) {
-    double s = P.c0;
+  template <class Real, class X>
+  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+    Real s = P.c0;
     for (int j = 0; j < d; ++j) s = fma(P.a[j], x(j), s);
-    return cos(s);
+    return gcos(s);
   }
 };
 
@@ -56,82 +54,107 @@ struct Family<GMQ_OSCILLATORY> {
 // product of the denominators (b_j = a_j^-2)
 template <>
 struct Family<GMQ_PRODUCT_PEAK> {
-  template <class X>
-  __device__ __forceinline__ static double eval(const SmemParams& P, int d, X x) {
-    double den = 1.0;
+  template <class Real, class X>
+  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+    Real den = Real(1);
     for (int j = 0; j < d; ++j) {
-      double t = x(j) - P.u[j];
+      Real t = x(j) - P.u[j];
       den *= fma(t, t, P.b[j]);
     }
-    return 1.0 / den;
+    return Real(1) / den;
   }
 };
 
 // (1 + sum a_j x_j)^-(d+1)
 template <>
 struct Family<GMQ_CORNER_PEAK> {
-  template <class X>
-  __device__ __forceinline__ static double eval(const SmemParams& P, int d, X x) {
-    double s = 1.0;
+  template <class Real, class X>
+  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+    Real s = Real(1);
     for (int j = 0; j < d; ++j) s = fma(P.a[j], x(j), s);
-    return 1.0 / ipow(s, d + 1);
+    return Real(1) / ipow(s, d + 1);
   }
 };
 
 // exp(-sum a_j^2 (x_j - u_j)^2)  (b_j = a_j^2)
 template <>
 struct Family<GMQ_GAUSSIAN> {
-  template <class X>
-  __device__ __forceinline__ static double eval(const SmemParams& P, int d, X x) {
-    double s = 0.0;
+  template <class Real, class X>
+  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+    Real s = Real(0);
     for (int j = 0; j < d; ++j) {
-      double t = x(j) - P.u[j];
+      Real t = x(j) - P.u[j];
       s = fma(P.b[j], t * t, s);
     }
-    return exp(-s);
+    return gexp(-s);
   }
 };
 
 // exp(-sum a_j |x_j - u_j|)
 template <>
 struct Family<GMQ_C0> {
-  template <class X>
-  __device__ __forceinline__ static double eval(const SmemParams& P, int d, X x) {
-    double s = 0.0;
+  template <class Real, class X>
+  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+    Real s = Real(0);
     for (int j = 0; j < d; ++j) s = fma(P.a[j], fabs(x(j) - P.u[j]), s);
-    return exp(-s);
+    return gexp(-s);
   }
 };
 
 // 0 if any x_j > u_j, else exp(sum a_j x_j)
 template <>
 struct Family<GMQ_DISCONTINUOUS> {
-  template <class X>
-  __device__ __forceinline__ static double eval(const SmemParams& P, int d, X x) {
-    double s = 0.0;
+  template <class Real, class X>
+  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+    Real s = Real(0);
     bool zero = false;
     for (int j = 0; j < d; ++j) {
-      double xj = x(j);
+      Real xj = x(j);
       zero = zero || (xj > P.u[j]);
       s = fma(P.a[j], xj, s);
     }
-    return zero ? 0.0 : exp(s);
+    return zero ? Real(0) : gexp(s);
   }
 };
 
 // (sum x_j^2)^11
 template <>
 struct Family<GMQ_POLY_SUMSQ11> {
-  template <class X>
-  __device__ __forceinline__ static double eval(const SmemParams& P, int d, X x) {
-    double s = 0.0;
+  template <class Real, class X>
+  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+    Real s = Real(0);
     for (int j = 0; j < d; ++j) {
-      double xj = x(j);
+      Real xj = x(j);
       s = fma(xj, xj, s);
     }
-    double s2 = s * s, s4 = s2 * s2, s8 = s4 * s4;
+    Real s2 = s * s, s4 = s2 * s2, s8 = s4 * s4;
     return s8 * s2 * s;
   }
+};
+
+// Class-sum accumulators: plain FP64 sums, or FP32 sums compensated with
+// Knuth's TwoSum (the rounding error of every addition is carried in c).
+template <class Real>
+struct Acc;
+
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float ap = __fsub_rn(t, bp);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, ap), __fsub_rn(v, bp)));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
 }  // namespace gmq

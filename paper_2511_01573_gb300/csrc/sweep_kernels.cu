@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kTile) k_classify(const SweepArgs S) {
     const uint8_t ax = S.axis[r];
     const double thr = (S.classifier == GMQ_LOCAL_REL) ? __dmul_rn(S.rel_tol, fabs(i7))
                                                        : __dmul_rn(budget, S.volfrac[r]);
-    const double guard = __dmul_rn(50.0 * 0x1p-53, fabs(i7));
+    const double guard = __dmul_rn(S.guard, fabs(i7));
     const bool retire = (e <= thr) || (e <= guard) || (ax & 0x80);
     split = retire ? 0 : 1;
     if (retire) {

@@ -262,6 +262,22 @@ class Context:
 
     # ---- step-level calls on torch CUDA tensors -------------------------
 
+    @staticmethod
+    def _ld(center, halfw):
+        """Leading dimension of a [dim, n] pair with unit stride along regions
+        (the stride of a size-1 dimension is not meaningful)."""
+        d, n = center.shape
+        if halfw.shape != center.shape:
+            raise ValueError("center and halfw must have the same shape [dim, n]")
+        for t in (center, halfw):
+            if n > 1 and t.stride(1) != 1:
+                raise ValueError("regions must be contiguous along the last dimension")
+        if d == 1:
+            return max(n, 1)
+        if halfw.stride(0) != center.stride(0) or center.stride(0) < n:
+            raise ValueError("center and halfw must share a row stride >= n")
+        return center.stride(0)
+
     def _dev(self, t, dtype):
         torch = self.torch
         if not (t.is_cuda and t.dtype == dtype):
@@ -275,8 +291,7 @@ class Context:
         center = self._dev(center, torch.float64)
         halfw = self._dev(halfw, torch.float64)
         d, n = center.shape
-        if halfw.shape != center.shape or center.stride(1) != 1 or halfw.stride(0) != center.stride(0):
-            raise ValueError("center/halfw must share shape [dim, n] and row stride")
+        ld = self._ld(center, halfw)
         p = _ProblemHandle(family, a, u, lo, hi, d)
         dev = center.device
         i7 = torch.empty(n, dtype=torch.float64, device=dev)
@@ -285,13 +300,14 @@ class Context:
         ax = torch.empty(n, dtype=torch.uint8, device=dev)
         _check("gmq_eval_rule", lib().gmq_eval_rule(
             self.h, C.byref(p.s), precision, lanes, n, _dptr(center), _dptr(halfw),
-            center.stride(0), _dptr(i7), _dptr(err), _dptr(vf), _dptr(ax)))
+            ld, _dptr(i7), _dptr(err), _dptr(vf), _dptr(ax)))
         return i7, err, vf, ax
 
     def classify_split(self, center, halfw, i7, err, volfrac, axis, budget, rel_tol=0.0,
                        classifier=VOLUME_SHARE, cap_out=None):
         torch = self.torch
         d, n = center.shape
+        ld = self._ld(center, halfw)
         cap = 2 * n if cap_out is None else cap_out
         dev = center.device
         co = torch.zeros((d, max(cap, 1)), dtype=torch.float64, device=dev)
@@ -301,9 +317,9 @@ class Context:
         ri = C.c_double()
         re_ = C.c_double()
         code = lib().gmq_classify_split(
-            self.h, d, n, _dptr(center), _dptr(halfw), center.stride(0), _dptr(i7), _dptr(err),
+            self.h, d, n, _dptr(center), _dptr(halfw), ld, _dptr(i7), _dptr(err),
             _dptr(volfrac) if volfrac is not None else None, _dptr(axis), budget, rel_tol,
-            classifier, _dptr(co), _dptr(ho), co.stride(0), cap, _dptr(flags), C.byref(ns),
+            classifier, _dptr(co), _dptr(ho), max(cap, 1), cap, _dptr(flags), C.byref(ns),
             C.byref(ri), C.byref(re_))
         _check("gmq_classify_split", code, ok=(OK, CAP_REACHED))
         k = int(ns.value)

@@ -155,9 +155,13 @@ def test_classify_split_cap_and_empty(oracle, gpu_ctx):
     a, u = _params(G.C0, d)
     c, h = G.random_boxes(5, n, d)
     i7, err, vf, ax = gpu_ctx.eval_rule(G.C0, a, u, _soa(c), _soa(h))
-    # tiny budget: everything splits; a cap below 2 n_split refuses to write
+    # zero budget: only the round-off guards retire; a cap below 2 n_split
+    # refuses to write but still reports the count
+    axn = ax.cpu().numpy()
+    ref = oracle.classify(i7.cpu().numpy(), err.cpu().numpy(), vf.cpu().numpy(), axn >> 7, 1.0,
+                          0.0)
     got = gpu_ctx.classify_split(_soa(c), _soa(h), i7, err, vf, ax, 0.0, cap_out=100)
-    assert got["status"] == 1 and got["n_split"] == n
+    assert got["status"] == 1 and got["n_split"] == ref["n_split"] > n // 2
     # huge budget: everything retires
     got = gpu_ctx.classify_split(_soa(c), _soa(h), i7, err, vf, ax, 1e300)
     assert got["n_split"] == 0
