@@ -39,6 +39,12 @@ def parse():
     ap.add_argument("--tols", default="1e-3,1e-4,1e-5,1e-6,1e-7,1e-8")
     ap.add_argument("--seeds", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-tol", action="store_true")
+    ap.add_argument("--probe-rule", default=None,
+                    help="profiling probe: family codes (e.g. 0,1,2,3,4); runs the rule "
+                         "kernel 3 times per family on 2^20 random d=8 regions and exits")
+    ap.add_argument("--lanes", type=int, default=1)
+    ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -50,6 +56,49 @@ def workload(args):
 
 
 CAP = 1 << 24
+
+# FP64 work of the rule kernel per region at d = 8 (401 nodes), per family:
+# FP64 thread-instructions (sm__thread_inst_executed_pipe_fp64_pred_on) and
+# flops (FMA = 2), from the ncu counters of a launch over 2^20 regions
+# (profiles/rule_fp64_d8.md).  The counts are fixed by the integrand and d:
+# the four families take no data-dependent branch.  Family codes: 0
+# oscillatory, 1 product peak, 2 corner peak, 3 Gaussian, 4 C0.
+RULE_FP64_INST_D8 = {0: 11032.0, 1: 12235.0, 2: 9027.0, 3: 16646.0, 4: 13438.0}
+RULE_FP64_FLOPS_D8 = {0: 17090.0, 1: 17491.0, 2: 14283.0, 3: 25511.0, 4: 22303.0}
+# DRAM bytes per region of the rule kernel in the same capture (128 B read,
+# ~13 B written of 25 B of outputs); traffic per launch scales with regions.
+RULE_DRAM_BYTES_PER_REGION_D8 = 141.7
+
+
+def time_to_tol(ctx, stream, tol):
+    """Wall time (CUDA events) for the 40 d = 8 problems at one tolerance,
+    FP64 against the mixed form, and the mixed results' largest relative
+    difference from the FP64 results."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    probs = G.genz_d8_problems(tols=(tol,))
+    out = {"tol": tol, "problems": len(probs)}
+    vals = {}
+    for name, prec in (("fp64", gmq.FP64), ("mixed", gmq.MIXED)):
+        for p in probs[:4]:
+            ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=CAP, precision=prec)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=CAP, precision=prec)
+               for p in probs]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        vals[name] = res
+        out[f"{name}_s"] = e0.elapsed_time(e1) / 1000.0
+        out[f"{name}_regions"] = sum(r.regions_evaluated for r in res)
+        out[f"{name}_converged"] = sum(1 for r in res if r.status == 0)
+    out["speedup_mixed_over_fp64"] = out["fp64_s"] / out["mixed_s"]
+    out["mixed_max_rel_diff_vs_fp64"] = max(
+        abs(m.integral - f.integral) / abs(f.integral) for m, f in zip(vals["mixed"], vals["fp64"]))
+    return out
 
 
 class ClockSampler:
@@ -164,8 +213,37 @@ def cpu_baseline(args, seconds):
                       f"({dt:.1f} s, pool 2^20)"}
 
 
+def probe_rule(args):
+    """The rule kernel alone on 2^20 random sub-boxes of [0,1]^8 (about
+    150 MB of inputs and outputs, more than L2), three launches per family,
+    for ncu captures; prints the event-timed rate."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    n, d = 1 << 20, 8
+    g = torch.Generator(device="cuda").manual_seed(1)
+    lo = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.9
+    w = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.05 + 1e-3
+    c = (lo + 0.5 * w).contiguous()
+    h = (0.5 * w).contiguous()
+    ctx = gmq.Context(0)
+    ctx.profile(True)
+    for fam in (int(x) for x in args.probe_rule.split(",")):
+        a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM.get(fam, 2.0))
+        ctx.profile_reset()
+        for _ in range(3):
+            ctx.eval_rule(fam, a, u, c, h, lanes=args.lanes, precision=args.precision)
+        p = ctx.profile_read()["rule"]
+        print(f"family {fam} lanes {args.lanes} precision {args.precision}: {p['launches']} "
+              f"launches, {p['ms'] / p['launches']:.3f} ms/launch, "
+              f"{n * p['launches'] / p['ms'] * 1e3:.4g} regions/s", flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.probe_rule:
+        return probe_rule(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -182,6 +260,8 @@ def main():
     ctx.profile(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    fam_regions = {}
+
     def step():
         regions = 0
         sweeps = 0
@@ -189,6 +269,7 @@ def main():
             r = ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=CAP)
             regions += r.regions_evaluated
             sweeps += r.iterations
+            fam_regions[p.family] = fam_regions.get(p.family, 0) + r.regions_evaluated
         return regions, sweeps
 
     def barrier():
@@ -200,6 +281,7 @@ def main():
         step()
     torch.cuda.synchronize()
     ctx.profile_reset()
+    fam_regions.clear()
     total_ms = 0.0
     regions = sweeps = 0
     launches0 = ctx.launch_count()
@@ -221,16 +303,13 @@ def main():
             sweeps += sw
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read()
-    # e2e: host wall clock through the public call
+    timed_fam_regions = dict(fam_regions)
+    # e2e: host wall clock through the public call (one step)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_regions = 0
-    e2e_sweeps = 0
-    for _ in range(args.steps):
-        rg, sw = step()
-        e2e_regions += rg
-        e2e_sweeps += sw
+    e2e_regions, e2e_sweeps = step()
     e2e_s = time.perf_counter() - t0
+    tt = time_to_tol(ctx, stream, 1e-6) if not args.no_time_to_tol else None
 
     ms_step = total_ms / args.steps
     my_time = total_ms / 1000.0
@@ -247,18 +326,30 @@ def main():
     if rank != 0:
         return
     rule = prof["rule"]
-    # FP64 roofline of the rule kernel: executed FP64 flops per region of the
-    # workload's mix (measured once with ncu, see profiles/) over the rule
-    # kernel's event-timed launches
-    flops_per_region = float(os.environ.get("GMQ_RULE_FLOPS_PER_REGION", "0")) or None
-    peak_fp64 = 2 * 2 * 152 * 2070e6 / 1e9  # GFLOP/s: 2 FP64 FMA lanes/clk/SM
+    # FP64 roofline of the rule kernel: FP64 flops per region of each family
+    # at d = 8 (a fixed count: the integrand at 401 nodes plus one
+    # accumulation each and the per-region epilogue) times the regions of
+    # that family in the timed steps, over the rule kernel's event-timed
+    # launches.  Peak: 2 FP64 FMA lanes per clock per SM (1.25 TFLOP/s
+    # nominal / 2 / 152 SMs / 2.07 GHz) at the measured median SM clock.
     roof = None
-    if rule["launches"] and flops_per_region:
-        avg_s = rule["ms"] / 1000.0 / rule["launches"]
-        per_launch = flops_per_region * rule["regions"] / rule["launches"]
-        ach = per_launch / avg_s / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": peak_fp64, "unit": "GFLOP/s",
-                "frac": ach / peak_fp64, "traffic": None}
+    clocks = clk.summary()
+    if rule["launches"] and all(f in RULE_FP64_INST_D8 for f in timed_fam_regions):
+        n_launch = rule["launches"]
+        avg_s = rule["ms"] / 1000.0 / n_launch
+        inst = sum(RULE_FP64_INST_D8[f] * n for f, n in timed_fam_regions.items()) / n_launch
+        flops = sum(RULE_FP64_FLOPS_D8[f] * n for f, n in timed_fam_regions.items()) / n_launch
+        mhz = clocks.get("sm_mhz") or 2070.0
+        peak_inst = 2 * 152 * mhz * 1e6 / 1e9  # G FP64 lane-inst/s
+        ach = inst / avg_s / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_inst,
+                "unit": "G FP64 lane-inst/s", "frac": ach / peak_inst,
+                "traffic": RULE_DRAM_BYTES_PER_REGION_D8 * rule["regions"] / n_launch,
+                "kernel": "k_rule (FP64 rule evaluation)",
+                "peak_basis": (f"2 FP64 lanes/clk/SM (1.25 TFLOP/s nominal) x 152 SMs "
+                               f"x median {mhz:.0f} MHz"),
+                "flops_view": {"achieved_gflops": flops / avg_s / 1e9,
+                               "peak_gflops": 2 * peak_inst}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -272,8 +363,9 @@ def main():
         "roofline": roof,
         "e2e": {"value": e2e_regions / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": len(probs) * 4 * 8 * 8,
-                "d2h_bytes_per_step": (e2e_sweeps // args.steps) * 80},
-        "clocks": clk.summary(),
+                "d2h_bytes_per_step": e2e_sweeps * 80},
+        "clocks": clocks,
+        "time_to_1e-6": tt,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, args.cpu_seconds)

@@ -3,7 +3,9 @@ differences, axis choice and global sums) against the FP64 oracle.
 
 The mixed form is not expected to match the oracle to 1e-12: node values
 carry FP32 rounding (about 6e-8 relative each), so the per-region rule value
-is compared with a 2e-6 bound relative to the magnitude of its terms and
+is compared with a 5e-6 bound relative to the magnitude of its terms (the
+oscillatory family's FP32 argument, up to 2 pi + sum a_j, carries an absolute
+rounding of about 1e-6) and
 the end-to-end integral with max(tol, 2e-6) relative.  The errors measured
 here are the ones reported for the mixed form.
 """
@@ -33,7 +35,7 @@ def test_mixed_rule_per_region(oracle, gpu_ctx, fam, d, lanes):
     i7, err, vf, ax = gpu_ctx.eval_rule(fam, a, u, _soa(c), _soa(h), precision=MIXED, lanes=lanes)
     i7 = i7.cpu().numpy()
     rel = np.abs(i7 - o["i7"]) / o["i7abs"]
-    assert rel.max() <= 2e-6, rel.max()
+    assert rel.max() <= 5e-6, rel.max()
     assert np.array_equal(vf.cpu().numpy(), o["vol"])
 
 
