@@ -149,6 +149,21 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+def aggregate_over_ranks(my_time_s, my_regions, world_size, device="cpu"):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the regions of all ranks (no data-path collective; only these two
+    numbers cross ranks, after the timed region)."""
+    if world_size <= 1:
+        return float(my_time_s), float(my_regions)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(my_time_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    r = torch.tensor([float(my_regions)], dtype=torch.float64, device=device)
+    dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(r.item())
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -312,16 +327,8 @@ def main():
     tt = time_to_tol(ctx, stream, 1e-6) if not args.no_time_to_tol else None
 
     ms_step = total_ms / args.steps
-    my_time = total_ms / 1000.0
-    my_regions = regions
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([my_time], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        rtot = torch.tensor([float(my_regions)], dtype=torch.float64, device=dev)
-        dist.all_reduce(rtot, op=dist.ReduceOp.SUM)
-        my_time = float(t.item())
-        my_regions = float(rtot.item())
+    my_time, my_regions = aggregate_over_ranks(total_ms / 1000.0, regions, ws,
+                                               f"cuda:{dev}" if ws > 1 else "cpu")
     value = my_regions / my_time
     if rank != 0:
         return

@@ -197,8 +197,12 @@ def test_e2e_product_peak_d3(oracle, gpu_ctx):
 def test_e2e_families(oracle, gpu_ctx, fam, d, tol):
     a, u = _params(fam, d, seed=5)
     o, g = _e2e(oracle, gpu_ctx, fam, a, u, tol)
-    if g.status == 0 and fam != G.GAUSSIAN:
-        ex = CF.exact(fam, a, u) if fam != G.DISCONTINUOUS else CF.discontinuous(a, u)
+    # closed-form accuracy is a property of the method, not of the port: the
+    # embedded-rule estimate cannot see a discontinuity that no node
+    # straddles, so the discontinuous family (random thresholds) may stop
+    # early with an optimistic estimate -- in the oracle exactly as on the GPU
+    if g.status == 0 and fam not in (G.GAUSSIAN, G.DISCONTINUOUS):
+        ex = CF.exact(fam, a, u)
         assert abs(g.integral - ex) <= tol * abs(ex) * 1.0001
 
 
