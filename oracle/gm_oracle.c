@@ -445,9 +445,36 @@ int64_t or_bisect(int d, int64_t n, const double *c, const double *h,
 /* The adaptive loop (paper Sec. 3, Fig. 1a; stopping rule paper Sec. 4).   */
 /* ------------------------------------------------------------------------ */
 
-int32_t or_integrate(const or_family *fam, const double *lo, const double *hi,
-                     const or_options *opt, or_result *res, or_trace *trace,
-                     int32_t max_trace) {
+/* Append regions r with (flags == NULL or flags[r] == 0) to the leaf list;
+ * sets *n_leaves = -1 once the list overflows. */
+static void append_leaves(int d, int64_t n, const double *c, const double *h,
+                          const uint8_t *flags, double *c_out, double *h_out,
+                          int64_t max_leaves, int64_t *n_leaves) {
+  int64_t r;
+  int k;
+  if (!c_out || *n_leaves < 0) return;
+  for (r = 0; r < n; ++r) {
+    if (flags && flags[r]) continue;
+    if (*n_leaves >= max_leaves) {
+      *n_leaves = -1;
+      return;
+    }
+    for (k = 0; k < d; ++k) {
+      c_out[*n_leaves * d + k] = c[r * d + k];
+      h_out[*n_leaves * d + k] = h[r * d + k];
+    }
+    *n_leaves += 1;
+  }
+}
+
+/* The loop.  When c_out is given, the final partition is recorded: the
+ * regions retired in each sweep (in list order), then every region of the
+ * last evaluated sweep. */
+static int32_t integrate_impl(const or_family *fam, const double *lo,
+                              const double *hi, const or_options *opt,
+                              or_result *res, or_trace *trace,
+                              int32_t max_trace, double *c_out, double *h_out,
+                              int64_t max_leaves, int64_t *n_leaves) {
   const int d = fam->d;
   int64_t cap = opt->max_regions;
   int32_t s, iters = 0, max_iters = opt->max_iters > 0 ? opt->max_iters : 1000;
@@ -459,6 +486,9 @@ int32_t or_integrate(const or_family *fam, const double *lo, const double *hi,
   int32_t status = 0;
   int k;
 
+  int64_t leaves_dummy = 0;
+  if (!n_leaves) n_leaves = &leaves_dummy;
+  *n_leaves = 0;
   memset(res, 0, sizeof(*res));
   if (d < 1 || d > 20 || cap < 1 || !(opt->rel_tol >= 0.0) ||
       !(opt->abs_tol >= 0.0)) {
@@ -562,7 +592,8 @@ int32_t or_integrate(const or_family *fam, const double *lo, const double *hi,
       status = 1;
       break;
     }
-    /* bisect the survivors */
+    /* record the retired regions, bisect the survivors */
+    append_leaves(d, n, c, h, flags, c_out, h_out, max_leaves, n_leaves);
     or_bisect(d, n, c, h, axis, flags, c2, h2);
     n = 2 * nsplit;
     {
@@ -571,6 +602,11 @@ int32_t or_integrate(const or_family *fam, const double *lo, const double *hi,
       t = h; h = h2; h2 = t;
     }
   }
+
+  if (status == -4)
+    *n_leaves = -1;
+  else
+    append_leaves(d, n, c, h, NULL, c_out, h_out, max_leaves, n_leaves);
 
 done:
   res->iterations = iters;
@@ -589,4 +625,92 @@ done:
   free(atie);
   free(flags);
   return status;
+}
+
+int32_t or_integrate(const or_family *fam, const double *lo, const double *hi,
+                     const or_options *opt, or_result *res, or_trace *trace,
+                     int32_t max_trace) {
+  return integrate_impl(fam, lo, hi, opt, res, trace, max_trace, NULL, NULL, 0,
+                        NULL);
+}
+
+int32_t or_integrate_partition(const or_family *fam, const double *lo,
+                               const double *hi, const or_options *opt,
+                               or_result *res, double *c_out, double *h_out,
+                               int64_t max_leaves, int64_t *n_leaves) {
+  return integrate_impl(fam, lo, hi, opt, res, NULL, 0, c_out, h_out,
+                        max_leaves, n_leaves);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the frozen-partition quadrature (no counterpart in the paper; */
+/* the adjoint extension differentiates the rule sum with respect to the     */
+/* integrand parameters with the partition held fixed).                      */
+/* ------------------------------------------------------------------------ */
+
+/* df/dtheta_k of the built-in families, written from their formulas. */
+double or_family_deriv(const double *x, int d, const void *ctx) {
+  const or_deriv_ctx *D = (const or_deriv_ctx *)ctx;
+  const or_family *F = D->fam;
+  const double *a = F->a, *u = F->u;
+  const int k = D->k % d;
+  const int wrt_u = D->k >= d;
+  const double f = or_family_eval(x, d, F);
+  double s, t;
+  int j;
+  switch (F->family) {
+  case OR_OSCILLATORY: /* f = cos(s), s = 2 pi u_1 + sum a_j x_j */
+    s = 2.0 * M_PI * u[0];
+    for (j = 0; j < d; ++j) s = s + a[j] * x[j];
+    if (wrt_u) return k == 0 ? -sin(s) * (2.0 * M_PI) : 0.0;
+    return -sin(s) * x[k];
+  case OR_PRODUCT_PEAK: /* factor g_k = 1/(a_k^-2 + t_k^2) */
+    t = x[k] - u[k];
+    s = 1.0 / (a[k] * a[k]) + t * t;
+    if (wrt_u) return f * (2.0 * t / s);
+    return f * (2.0 / (a[k] * a[k] * a[k]) / s);
+  case OR_CORNER_PEAK: /* f = (1 + sum a_j x_j)^-(d+1) */
+    if (wrt_u) return 0.0;
+    s = 1.0;
+    for (j = 0; j < d; ++j) s = s + a[j] * x[j];
+    return -(double)(d + 1) * x[k] * pow(s, -(double)(d + 2));
+  case OR_GAUSSIAN: /* f = exp(-sum a_j^2 (x_j - u_j)^2) */
+    t = x[k] - u[k];
+    if (wrt_u) return 2.0 * a[k] * a[k] * t * f;
+    return -2.0 * a[k] * t * t * f;
+  case OR_C0: /* f = exp(-sum a_j |x_j - u_j|) */
+    t = x[k] - u[k];
+    if (wrt_u) return a[k] * (t > 0.0 ? 1.0 : (t < 0.0 ? -1.0 : 0.0)) * f;
+    return -fabs(t) * f;
+  case OR_DISCONTINUOUS: /* a.e.: moving the threshold moves a jump */
+    if (wrt_u) return 0.0;
+    return x[k] * f;
+  default:
+    return 0.0;
+  }
+}
+
+void or_rule_grad(const or_family *fam, int64_t n, const double *c,
+                  const double *h, double *grad, double *integral) {
+  const int d = fam->d;
+  double *v = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  int64_t r;
+  int k;
+  or_rule_out o;
+  for (r = 0; r < n; ++r) {
+    or_rule(d, c + r * d, h + r * d, or_family_eval, fam, NULL, &o);
+    v[r] = o.i7;
+  }
+  *integral = or_pairwise_sum(v, n);
+  for (k = 0; k < 2 * d; ++k) {
+    or_deriv_ctx dc;
+    dc.fam = fam;
+    dc.k = k;
+    for (r = 0; r < n; ++r) {
+      or_rule(d, c + r * d, h + r * d, or_family_deriv, &dc, NULL, &o);
+      v[r] = o.i7;
+    }
+    grad[k] = or_pairwise_sum(v, n);
+  }
+  free(v);
 }

@@ -119,6 +119,28 @@ int64_t or_bisect(int d, int64_t n, const double *c, const double *h,
                   const int32_t *axis, const uint8_t *flags, double *c_out,
                   double *h_out);
 
+/* Derivative of a built-in integrand with respect to parameter k
+ * (k < d: a_k, k >= d: u_{k-d}); ctx is an or_deriv_ctx*. */
+typedef struct {
+  const or_family *fam;
+  int32_t k;
+} or_deriv_ctx;
+double or_family_deriv(const double *x, int d, const void *ctx);
+
+/* Frozen-partition quadrature Q = sum_r I7_r and its gradient: the same rule
+ * applied to each derivative integrand, summed over the regions with the
+ * pairwise tree.  grad has 2d entries (a_1..a_d, u_1..u_d). */
+void or_rule_grad(const or_family *fam, int64_t n, const double *c,
+                  const double *h, double *grad, double *integral);
+
+/* Like or_integrate, and also returns the final partition (every retired region followed by the regions of
+ * the last evaluated sweep) in c_out/h_out (capacity max_leaves regions);
+ * *n_leaves receives its size, or -1 if it did not fit. */
+int32_t or_integrate_partition(const or_family *fam, const double *lo,
+                               const double *hi, const or_options *opt,
+                               or_result *res, double *c_out, double *h_out,
+                               int64_t max_leaves, int64_t *n_leaves);
+
 /* The whole adaptive loop.  trace (may be NULL) receives up to max_trace
  * records.  Status codes: 0 converged, 1 region cap reached, 2 iteration
  * limit, 3 every region retired before the tolerance was met,

@@ -271,3 +271,50 @@ def integrate(family: int, a, u, rel_tol: float, lo=None, hi=None, abs_tol: floa
                   E_ret=t.E_ret, budget=t.budget) for t in tr[:min(res.iterations, max_trace)]]
     return IntegrateResult(res.integral, res.error, res.regions_evaluated, res.function_evals,
                            res.final_active, res.iterations, res.status, res.near_ties, trace)
+
+
+def _lib_grad():
+    L = lib()
+    if not getattr(L, "_grad_sig", False):
+        L.or_rule_grad.argtypes = [C.POINTER(Family), C.c_int64, _dp, _dp, _dp, _dp]
+        L.or_integrate_partition.restype = C.c_int32
+        L.or_integrate_partition.argtypes = [C.POINTER(Family), _dp, _dp, C.POINTER(Options),
+                                             C.POINTER(Result), _dp, _dp, C.c_int64,
+                                             C.POINTER(C.c_int64)]
+        L._grad_sig = True
+    return L
+
+
+def rule_grad(family: int, a, u, c, h):
+    """Frozen-partition quadrature Q and dQ/d(a, u) (2d values)."""
+    c, h = _f64(c), _f64(h)
+    n, d = c.shape
+    fh = _FamilyHandle(family, a, u)
+    g = np.zeros(2 * d)
+    q = C.c_double()
+    _lib_grad().or_rule_grad(C.byref(fh.s), n, _p(c), _p(h), _p(g), C.byref(q))
+    return g, q.value
+
+
+def integrate_partition(family: int, a, u, rel_tol: float, lo=None, hi=None,
+                        abs_tol: float = 1e-16, max_regions: int = 100000, max_leaves=None,
+                        init_splits: int = 0, max_iters: int = 0, classifier: int = 0):
+    """or_integrate plus the final partition (leaves as n x d arrays)."""
+    fh = _FamilyHandle(family, a, u)
+    d = len(fh.a)
+    lo = _f64(np.zeros(d) if lo is None else lo)
+    hi = _f64(np.ones(d) if hi is None else hi)
+    ml = max_leaves or max_regions
+    co = np.zeros((ml, d))
+    ho = np.zeros((ml, d))
+    nl = C.c_int64()
+    opt = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier)
+    res = Result()
+    _lib_grad().or_integrate_partition(C.byref(fh.s), _p(lo), _p(hi), C.byref(opt), C.byref(res),
+                                       _p(co), _p(ho), ml, C.byref(nl))
+    k = int(nl.value)
+    r = IntegrateResult(res.integral, res.error, res.regions_evaluated, res.function_evals,
+                        res.final_active, res.iterations, res.status, res.near_ties, [])
+    if k < 0:
+        return r, None, None
+    return r, co[:k].copy(), ho[:k].copy()
