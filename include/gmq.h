@@ -54,7 +54,8 @@ typedef enum gmq_status {
   GMQ_ERR_OOM = -2,        /* device memory (or the caller's pool) too small  */
   GMQ_ERR_CUDA = -3,       /* a CUDA call failed                              */
   GMQ_ERR_NONFINITE = -4,  /* the integrand produced a NaN or an infinity     */
-  GMQ_ERR_TIMEOUT = -5     /* a bounded device wait gave up                   */
+  GMQ_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                   */
+  GMQ_ERR_TOO_LARGE = -6   /* input longer than a fixed-size scratch allows   */
 } gmq_status;
 
 /* Built-in integrands (paper Sec. 4 test functions; Genz families).
@@ -242,6 +243,41 @@ gmq_status gmq_tree_sum(gmq_context *ctx, int64_t n, const double *d_v,
 gmq_status gmq_partition(gmq_context *ctx, int32_t dim, const double *lo,
                          const double *hi, int32_t s, double *d_center,
                          double *d_halfw, int64_t ld);
+
+/* ---- allocation-free variant ------------------------------------------ */
+
+/* Longest input of gmq_tree_sum_noalloc: 2^23 values (8192 tiles). */
+#define GMQ_NOALLOC_MAX_N ((int64_t)1 << 23)
+
+/* The pairwise-tree sum of gmq_tree_sum (same order, same result) without
+ * any device allocation.  The paper has no counterpart: this call exists for
+ * callers that cannot allocate device memory at the point where they need
+ * the sum -- code whose device memory is wholly owned by its own allocator
+ * or a fixed budget reserved at start-up, and code that cannot afford the
+ * device-wide synchronisation that cudaMalloc and cudaFree may cause in the
+ * middle of its work.  It needs no gmq_context (creating one allocates).
+ *
+ * Arguments: device is the CUDA device of d_v, d_sum and the stream; d_v
+ * holds n doubles (device memory, read only); d_sum receives the sum (one
+ * double of device memory); cuda_stream is the cudaStream_t to run on (NULL
+ * = the legacy default stream).  The call only enqueues work on that
+ * stream: the sum is in *d_sum once the stream reaches that point.
+ *
+ * Working memory: a file-scope static device array of about 64 KiB (the
+ * last-block ticket and one partial sum per 1024-value tile), which every
+ * device that loads the library keeps until the process exits.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture.  All calls
+ * share the one array, and each call clears the ticket it needs on its own
+ * stream, so calls whose work overlaps on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller.
+ *
+ * Errors: GMQ_ERR_TOO_LARGE if n > GMQ_NOALLOC_MAX_N (nothing is enqueued);
+ * GMQ_ERR_INVALID for a negative n, a NULL pointer or a bad device;
+ * GMQ_ERR_CUDA if the address lookup, the memset or the launch fails.  The
+ * call makes no cudaMalloc, cudaFree or other allocating call. */
+gmq_status gmq_tree_sum_noalloc(int32_t device, int64_t n, const double *d_v,
+                                double *d_sum, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -339,6 +339,7 @@ const char* gmq_status_string(gmq_status s) {
     case GMQ_ERR_CUDA: return "CUDA error";
     case GMQ_ERR_NONFINITE: return "non-finite integrand value";
     case GMQ_ERR_TIMEOUT: return "device wait timed out";
+    case GMQ_ERR_TOO_LARGE: return "input longer than the fixed scratch allows";
   }
   return "unknown status";
 }

@@ -62,7 +62,10 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_default_options", "gmq_integrate", "gmq_last_trace", "gmq_seed_genz",
            "gmq_status_string", "gmq_launch_count", "gmq_eval_rule", "gmq_classify_split",
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
-           "gmq_profile_read")
+           "gmq_profile_read", "gmq_tree_sum_noalloc")
+
+ERR_TOO_LARGE = -6
+NOALLOC_MAX_N = 1 << 23
 
 
 class GmqError(RuntimeError):
@@ -103,6 +106,7 @@ def lib():
         "gmq_profile_enable": [vp, i32],
         "gmq_profile_reset": [vp],
         "gmq_profile_read": [vp, i32, C.POINTER(KernelStats)],
+        "gmq_tree_sum_noalloc": [i32, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -152,6 +156,23 @@ def seed_genz(seed: int, family: int, dim: int, target_sum: float):
     u = np.zeros(dim)
     _check("gmq_seed_genz", lib().gmq_seed_genz(seed, family, dim, target_sum, _ptr(a), _ptr(u)))
     return a, u
+
+
+def tree_sum_noalloc(v, out, stream=None) -> int:
+    """Enqueue the allocation-free pairwise sum of the CUDA float64 tensor v
+    into the one-element CUDA float64 tensor out, on `stream` (default: the
+    current torch stream of v's device).  Returns the status code; the
+    value is in `out` once the stream gets there.  Calls whose GPU work
+    overlaps share one scratch array and race."""
+    import torch
+    if not (v.is_cuda and v.dtype == torch.float64 and out.is_cuda and out.dtype == torch.float64):
+        raise ValueError("expected CUDA float64 tensors")
+    if v.numel() > 1 and not v.is_contiguous():
+        raise ValueError("v must be contiguous")
+    dev = v.device.index
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    return lib().gmq_tree_sum_noalloc(dev, v.numel(), C.c_void_p(v.data_ptr()),
+                                      C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream))
 
 
 @dataclass
