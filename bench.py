@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--probe-rule", default=None,
                     help="profiling probe: family codes (e.g. 0,1,2,3,4); runs the rule "
                          "kernel 3 times per family on 2^20 random d=8 regions and exits")
+    ap.add_argument("--probe-split", action="store_true",
+                    help="profiling probe: classify + split on 2^22 random d=8 regions")
     ap.add_argument("--lanes", type=int, default=1)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -255,10 +257,42 @@ def probe_rule(args):
     ctx.close()
 
 
+def probe_split(args):
+    """Classify + split alone on 2^22 random d = 8 regions (three calls):
+    HBM-bound kernels.  The budget is the median per-region threshold, so
+    about half the regions split."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    n, d = 1 << 22, 8
+    g = torch.Generator(device="cuda").manual_seed(2)
+    lo = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.9
+    w = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.05 + 1e-3
+    c = (lo + 0.5 * w).contiguous()
+    h = (0.5 * w).contiguous()
+    ctx = gmq.Context(0)
+    a, u = G.seed_genz(1, G.GAUSSIAN, d, 3.5)
+    i7, err, vf, ax = ctx.eval_rule(G.GAUSSIAN, a, u, c, h, precision=gmq.MIXED)
+    budget = float(torch.median(err / vf).item())
+    ctx.profile(True)
+    for _ in range(3):
+        out = ctx.classify_split(c, h, i7, err, vf, ax, budget)
+    p = ctx.profile_read()
+    ns = out["n_split"]
+    for k in ("classify", "split"):
+        ms = p[k]["ms"] / p[k]["launches"]
+        alg = 26.0 * n if k == "classify" else (1.0 * n + ns * (16 * d + 32 * d))
+        print(f"{k}: {ms:.3f} ms/launch, n={n}, n_split={ns}, algorithmic {alg / 1e6:.1f} MB, "
+              f"{alg / ms / 1e6:.1f} GB/s", flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.probe_rule:
         return probe_rule(args)
+    if args.probe_split:
+        return probe_split(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch

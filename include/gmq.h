@@ -102,8 +102,15 @@ typedef struct gmq_options {
   int32_t classifier;  /* gmq_classifier                                    */
   int32_t lanes;       /* threads per region in the rule kernel: 0 = chosen
                           per sweep by the library, else 1, 4 or 32          */
-  int32_t reserved;    /* must be 0                                         */
+  int32_t flags;       /* 0, or GMQ_KEEP_PARTITION                           */
 } gmq_options;
+
+/* gmq_options.flags: record the final partition of the run (every region
+ * retired in any sweep, then the regions of the last evaluated sweep), for
+ * gmq_partition_copy / gmq_rule_grad.  The list holds up to max_regions
+ * regions and adds two region lists to the pool; if it fills up, the run
+ * stops with GMQ_CAP_REACHED and no partition is kept. */
+#define GMQ_KEEP_PARTITION 1
 
 typedef struct gmq_result {
   double integral;           /* I: retired sums + active regions' I7_r     */
@@ -146,8 +153,10 @@ gmq_status gmq_set_stream(gmq_context *ctx, void *cuda_stream);
  * (see gmq_pool_bytes).  Passing NULL returns to library-owned memory. */
 gmq_status gmq_set_pool(gmq_context *ctx, void *dev_ptr, size_t bytes);
 
-/* Device bytes the region pool needs for dimension dim and max_regions. */
-gmq_status gmq_pool_bytes(int32_t dim, int64_t max_regions, size_t *bytes);
+/* Device bytes the region pool needs for dimension dim, max_regions and
+ * gmq_options.flags (GMQ_KEEP_PARTITION adds the final-partition list). */
+gmq_status gmq_pool_bytes(int32_t dim, int64_t max_regions, int32_t flags,
+                          size_t *bytes);
 
 /* Fill opt with defaults: rel_tol 1e-6, abs_tol 1e-16, max_regions 2^22,
  * automatic partition, 1000 sweeps, FP64, volume-share classifier, lanes 0. */
@@ -162,6 +171,29 @@ gmq_status gmq_integrate(gmq_context *ctx, const gmq_problem *prob,
  * *count receives the number of records available. */
 gmq_status gmq_last_trace(gmq_context *ctx, gmq_sweep *out, int32_t max,
                           int32_t *count);
+
+/* Final partition of the last gmq_integrate call made with
+ * GMQ_KEEP_PARTITION: *count receives its number of regions (-1 if none was
+ * kept); up to max regions are copied into the caller's device arrays
+ * (layout as for gmq_eval_rule, leading dimension ld >= min(count, max)).
+ * The regions tile Omega; their order is the order they left the loop.
+ * The list lives in the context's pool until the next gmq_integrate. */
+gmq_status gmq_partition_copy(gmq_context *ctx, double *d_center,
+                              double *d_halfw, int64_t ld, int64_t max,
+                              int64_t *count);
+
+/* Adjoint over a frozen partition (no counterpart in the paper; the
+ * differentiation extension).  For the n regions given (typically the
+ * final partition of an integration), Q = sum_r vol_r sum_i w_i f(x_i) with
+ * the degree-7 Genz-Malik weights, and its exact gradient with respect to
+ * the family parameters, dQ/dtheta = sum_r vol_r sum_i w_i df/dtheta(x_i).
+ * *integral receives Q; grad (host, 2*dim doubles) receives dQ/da_1..a_dim
+ * followed by dQ/du_1..u_dim, each summed over the regions with the
+ * pairwise tree.  The discontinuous family's u-derivatives are reported as
+ * 0 (its thresholds move a jump, which a fixed partition does not see). */
+gmq_status gmq_rule_grad(gmq_context *ctx, const gmq_problem *prob, int64_t n,
+                         const double *d_center, const double *d_halfw,
+                         int64_t ld, double *integral, double *grad);
 
 /* Seeded Genz parameters (no counterpart in the paper; the paper's
  * integrands use fixed parameters).  SplitMix64 stream with initial state

@@ -1,6 +1,8 @@
-// gm_rule_inst.cu -- instantiates the rule kernel for one integrand family.
-// The build compiles this file once per family with -DGMQ_FAM=<code>, so the
-// instantiations compile in parallel.
+// gm_rule_inst.cu -- instantiates the rule kernel (FP64 and mixed) and the
+// adjoint kernel for one integrand family.  The build compiles this file
+// once per family with -DGMQ_FAM=<code>, so the instantiations compile in
+// parallel.
+#include "gm_adjoint.cuh"
 #include "gm_rule.cuh"
 
 #ifndef GMQ_FAM
@@ -9,4 +11,5 @@
 
 namespace gmq {
 GMQ_DEFINE_RULE_FAMILY(GMQ_FAM)
+GMQ_DEFINE_GRAD_FAMILY(GMQ_FAM)
 }  // namespace gmq

@@ -16,6 +16,7 @@
 #include <new>
 #include <vector>
 
+#include "gm_adjoint.cuh"
 #include "gm_rule.cuh"
 #include "gmq_common.cuh"
 #include "sweep_kernels.cuh"
@@ -25,6 +26,13 @@ using namespace gmq;
 namespace gmq {
 template <int FAM>
 cudaError_t launch_rule_family(int precision, int T, const RuleArgs& A, cudaStream_t s);
+extern template cudaError_t launch_rule_grad_family<GMQ_OSCILLATORY>(const GradArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_grad_family<GMQ_PRODUCT_PEAK>(const GradArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_grad_family<GMQ_CORNER_PEAK>(const GradArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_grad_family<GMQ_GAUSSIAN>(const GradArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_grad_family<GMQ_C0>(const GradArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_grad_family<GMQ_DISCONTINUOUS>(const GradArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_grad_family<GMQ_POLY_SUMSQ11>(const GradArgs&, cudaStream_t);
 }
 
 struct gmq_context {
@@ -40,6 +48,15 @@ struct gmq_context {
   DevStatus* h_status = nullptr;  // pinned
   std::vector<gmq_sweep> trace;
   int64_t launches = 0;
+  // final partition of the last integration (GMQ_KEEP_PARTITION)
+  int64_t part_count = -1;
+  int part_d = 0;
+  int64_t part_ld = 0;
+  const double* part_c = nullptr;
+  const double* part_h = nullptr;
+  // working memory of gmq_rule_grad
+  char* gscratch = nullptr;
+  size_t gscratch_bytes = 0;
   // kernel timing (gmq_profile_*)
   bool prof_on = false;
   bool ev_made = false;
@@ -78,14 +95,15 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int64_t num_nodes(int d) { return ((int64_t)1 << d) + 2 * (int64_t)d * d + 2 * (int64_t)d + 1; }
 
 // Region pool of one integration: two region lists (ping-pong), the rule
-// outputs, the decision bytes, per-tile arrays and the device status.
+// outputs, the decision bytes, per-tile arrays, the device status and, with
+// GMQ_KEEP_PARTITION, the final-partition list.
 struct PoolLayout {
   int64_t ld = 0, nb = 0;
   size_t cA = 0, hA = 0, cB = 0, hB = 0, i7 = 0, err = 0, vf = 0, axis = 0, flags = 0;
-  size_t cnt = 0, off = 0, ba = 0, bb = 0, st = 0, total = 0;
+  size_t cnt = 0, off = 0, ba = 0, bb = 0, st = 0, cL = 0, hL = 0, total = 0;
 };
 
-PoolLayout pool_layout(int d, int64_t cap) {
+PoolLayout pool_layout(int d, int64_t cap, int flags) {
   PoolLayout L;
   L.ld = (cap + 31) / 32 * 32;
   L.nb = (cap + kTile - 1) / kTile;
@@ -107,6 +125,10 @@ PoolLayout pool_layout(int d, int64_t cap) {
   L.ba = p; p += align256(sizeof(double) * (size_t)L.nb);
   L.bb = p; p += align256(sizeof(double) * (size_t)L.nb);
   L.st = p; p += align256(sizeof(DevStatus));
+  if (flags & GMQ_KEEP_PARTITION) {
+    L.cL = p; p += list;
+    L.hL = p; p += list;
+  }
   L.total = p;
   return L;
 }
@@ -388,6 +410,7 @@ gmq_status gmq_destroy(gmq_context* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->own) cudaFree(ctx->own);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->gscratch) cudaFree(ctx->gscratch);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->ev_made)
       for (int k = 0; k < 5; ++k)
@@ -411,10 +434,11 @@ gmq_status gmq_set_pool(gmq_context* ctx, void* dev_ptr, size_t bytes) {
   return GMQ_OK;
 }
 
-gmq_status gmq_pool_bytes(int32_t dim, int64_t max_regions, size_t* bytes) {
-  if (!bytes || dim < 1 || dim > GMQ_MAX_DIM || max_regions < 1 || max_regions > kMaxRegions)
+gmq_status gmq_pool_bytes(int32_t dim, int64_t max_regions, int32_t flags, size_t* bytes) {
+  if (!bytes || dim < 1 || dim > GMQ_MAX_DIM || max_regions < 1 || max_regions > kMaxRegions ||
+      (flags & ~GMQ_KEEP_PARTITION))
     return GMQ_ERR_INVALID;
-  *bytes = pool_layout(dim, max_regions).total;
+  *bytes = pool_layout(dim, max_regions, flags).total;
   return GMQ_OK;
 }
 
@@ -478,7 +502,7 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
   const int d = prob->dim;
   const int64_t cap = opt->max_regions;
   if (!(opt->rel_tol >= 0.0) || !(opt->abs_tol >= 0.0) || cap < 1 || cap > kMaxRegions ||
-      opt->init_splits < 0 || opt->max_iters < 0 || opt->reserved != 0 ||
+      opt->init_splits < 0 || opt->max_iters < 0 || (opt->flags & ~GMQ_KEEP_PARTITION) ||
       (opt->precision != GMQ_FP64 && opt->precision != GMQ_MIXED) ||
       (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL) ||
       (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32))
@@ -493,7 +517,9 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
 
   DeviceGuard g(ctx->device);
   if (!g.ok) return out->status = GMQ_ERR_CUDA, GMQ_ERR_CUDA;
-  const PoolLayout L = pool_layout(d, cap);
+  const bool keep = (opt->flags & GMQ_KEEP_PARTITION) != 0;
+  ctx->part_count = -1;
+  const PoolLayout L = pool_layout(d, cap, opt->flags);
   char* base = nullptr;
   gmq_status ps = ensure_pool(ctx, L.total, &base);
   if (ps != GMQ_OK) return out->status = ps, ps;
@@ -572,6 +598,12 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
     S.blk_b = (double*)(base + L.bb);
     S.budget_ptr = &st->budget;
     S.guard = opt->precision == GMQ_MIXED ? kGuardMixed : kGuardFp64;
+    S.last_sweep = (iters + 1 >= max_iters) ? 1 : 0;
+    S.keep = keep ? 1 : 0;
+    S.c_leaf = keep ? (double*)(base + L.cL) : nullptr;
+    S.h_leaf = keep ? (double*)(base + L.hL) : nullptr;
+    S.ld_leaf = L.ld;
+    S.leaf_cap = cap;
     S.st = st;
     prof_begin(ctx, kKSum);
     GMQ_CK(launch_sum_status(S, strm));
@@ -624,7 +656,7 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
       status = GMQ_ROUNDOFF_LIMIT;
       break;
     }
-    if (h.flags & kCapExceeded) {
+    if (h.flags & (kCapExceeded | kLeafOverflow)) {
       status = GMQ_CAP_REACHED;
       break;
     }
@@ -634,6 +666,25 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
   }
   out->iterations = iters;
   out->status = status;
+  // final partition: the leaves recorded so far plus the last sweep's list
+  if (keep && status != GMQ_ERR_NONFINITE && !(ctx->h_status->flags & kLeafOverflow)) {
+    const long long base_leaves = ctx->h_status->n_leaves;
+    if (base_leaves + n <= cap) {
+      double* cL = (double*)(base + L.cL);
+      double* hL = (double*)(base + L.hL);
+      const size_t pitch = sizeof(double) * (size_t)L.ld;
+      GMQ_CK(cudaMemcpy2DAsync(cL + base_leaves, pitch, cA, pitch, sizeof(double) * (size_t)n, d,
+                               cudaMemcpyDeviceToDevice, strm));
+      GMQ_CK(cudaMemcpy2DAsync(hL + base_leaves, pitch, hA, pitch, sizeof(double) * (size_t)n, d,
+                               cudaMemcpyDeviceToDevice, strm));
+      GMQ_CK(cudaStreamSynchronize(strm));
+      ctx->part_count = base_leaves + n;
+      ctx->part_d = d;
+      ctx->part_ld = L.ld;
+      ctx->part_c = cL;
+      ctx->part_h = hL;
+    }
+  }
   return status;
 }
 
@@ -824,6 +875,97 @@ gmq_status gmq_profile_reset(gmq_context* ctx) {
 gmq_status gmq_profile_read(gmq_context* ctx, int32_t kernel, gmq_kernel_stats* out) {
   if (!ctx || !out || kernel < 0 || kernel > 4) return GMQ_ERR_INVALID;
   *out = ctx->stats[kernel];
+  return GMQ_OK;
+}
+
+
+gmq_status gmq_partition_copy(gmq_context* ctx, double* d_center, double* d_halfw, int64_t ld,
+                              int64_t max, int64_t* count) {
+  if (!ctx || !count || max < 0) return GMQ_ERR_INVALID;
+  *count = ctx->part_count;
+  if (ctx->part_count < 0) return GMQ_OK;
+  const int64_t m = std::min<int64_t>(max, ctx->part_count);
+  if (m == 0) return GMQ_OK;
+  if (!d_center || !d_halfw || ld < m) return GMQ_ERR_INVALID;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  const size_t spitch = sizeof(double) * (size_t)ctx->part_ld, dpitch = sizeof(double) * (size_t)ld;
+  GMQ_CK(cudaMemcpy2DAsync(d_center, dpitch, ctx->part_c, spitch, sizeof(double) * (size_t)m,
+                           ctx->part_d, cudaMemcpyDeviceToDevice, ctx->stream));
+  GMQ_CK(cudaMemcpy2DAsync(d_halfw, dpitch, ctx->part_h, spitch, sizeof(double) * (size_t)m,
+                           ctx->part_d, cudaMemcpyDeviceToDevice, ctx->stream));
+  GMQ_CK(cudaStreamSynchronize(ctx->stream));
+  return GMQ_OK;
+}
+
+gmq_status gmq_rule_grad(gmq_context* ctx, const gmq_problem* prob, int64_t n,
+                         const double* d_center, const double* d_halfw, int64_t ld,
+                         double* integral, double* grad) {
+  if (!ctx || !integral || !grad) return GMQ_ERR_INVALID;
+  gmq_status vs = validate_problem(prob);
+  if (vs != GMQ_OK) return vs;
+  const int d = prob->dim;
+  if (n < 0 || n > kMaxRegions || ld < n || (n > 0 && (!d_center || !d_halfw)))
+    return GMQ_ERR_INVALID;
+  *integral = 0.0;
+  for (int k = 0; k < 2 * d; ++k) grad[k] = 0.0;
+  if (n == 0) return GMQ_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  // working memory: per-region contributions [2d+1][ldo], per-row tile
+  // partials, row tickets and row sums
+  const int rows = 2 * d + 1;
+  const int64_t ldo = (n + 31) / 32 * 32;
+  const int64_t nb = (n + kTile - 1) / kTile;
+  const size_t o_out = 0;
+  const size_t o_blk = o_out + align256(sizeof(double) * (size_t)rows * (size_t)ldo);
+  const size_t o_tk = o_blk + align256(sizeof(double) * (size_t)rows * (size_t)nb);
+  const size_t o_sum = o_tk + align256(sizeof(unsigned) * (size_t)rows);
+  const size_t need = o_sum + align256(sizeof(double) * (size_t)rows);
+  if (ctx->gscratch_bytes < need) {
+    if (ctx->gscratch) cudaFree(ctx->gscratch);
+    ctx->gscratch = nullptr;
+    ctx->gscratch_bytes = 0;
+    void* q = nullptr;
+    if (cudaMalloc(&q, need) != cudaSuccess) {
+      cudaGetLastError();
+      return GMQ_ERR_OOM;
+    }
+    ctx->gscratch = (char*)q;
+    ctx->gscratch_bytes = need;
+  }
+  char* b = ctx->gscratch;
+  GradArgs A;
+  A.c = d_center;
+  A.h = d_halfw;
+  A.ld = ld;
+  A.n = n;
+  A.out = (double*)(b + o_out);
+  A.ldo = ldo;
+  A.P = fam_params(prob);
+  A.R = rule_const(d, prob->lo, prob->hi);
+  cudaStream_t strm = ctx->stream;
+  cudaError_t e;
+  switch (prob->family) {
+    case GMQ_OSCILLATORY: e = launch_rule_grad_family<GMQ_OSCILLATORY>(A, strm); break;
+    case GMQ_PRODUCT_PEAK: e = launch_rule_grad_family<GMQ_PRODUCT_PEAK>(A, strm); break;
+    case GMQ_CORNER_PEAK: e = launch_rule_grad_family<GMQ_CORNER_PEAK>(A, strm); break;
+    case GMQ_GAUSSIAN: e = launch_rule_grad_family<GMQ_GAUSSIAN>(A, strm); break;
+    case GMQ_C0: e = launch_rule_grad_family<GMQ_C0>(A, strm); break;
+    case GMQ_DISCONTINUOUS: e = launch_rule_grad_family<GMQ_DISCONTINUOUS>(A, strm); break;
+    default: e = launch_rule_grad_family<GMQ_POLY_SUMSQ11>(A, strm); break;
+  }
+  GMQ_CK(e);
+  GMQ_CK(cudaMemsetAsync(b + o_tk, 0, sizeof(unsigned) * (size_t)rows, strm));
+  GMQ_CK(launch_rows_tree_sum(A.out, ldo, n, rows, (double*)(b + o_blk), (unsigned*)(b + o_tk),
+                              (double*)(b + o_sum), strm));
+  ctx->launches += 2;
+  std::vector<double> sums((size_t)rows);
+  GMQ_CK(cudaMemcpyAsync(sums.data(), b + o_sum, sizeof(double) * (size_t)rows,
+                         cudaMemcpyDeviceToHost, strm));
+  GMQ_CK(cudaStreamSynchronize(strm));
+  for (int k = 0; k < 2 * d; ++k) grad[k] = sums[(size_t)k];
+  *integral = sums[(size_t)(2 * d)];
   return GMQ_OK;
 }
 

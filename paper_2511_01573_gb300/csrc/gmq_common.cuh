@@ -60,12 +60,22 @@ struct DevStatus {
   double I, E, budget;   // this sweep's global estimates
   double ret_i, ret_e;   // this sweep's retired sums
   long long n_split;     // regions split in this sweep
-  int flags;             // kConverged | kNonfinite | kCap | kDone
+  long long n_leaves;    // regions recorded in the final-partition list
+  long long leaf_base;   // n_leaves before this sweep's retired regions
+  int flags;             // kConverged | kNonfinite | kCap | kDone ...
   unsigned ticket_sum;   // last-block counters (reset by the last block)
   unsigned ticket_cls;
   int pad;
 };
-enum { kConverged = 1, kNonfinite = 2, kCapExceeded = 4, kAllRetired = 8, kDone = 16 };
+enum {
+  kConverged = 1,
+  kNonfinite = 2,
+  kCapExceeded = 4,
+  kAllRetired = 8,
+  kDone = 16,
+  kLastSweep = 32,    // the sweep limit is reached: stop after the sums
+  kLeafOverflow = 64  // the final-partition list is full
+};
 
 // Parameters of the sum / classify / split kernels of one sweep.
 struct SweepArgs {
@@ -92,6 +102,12 @@ struct SweepArgs {
   const double* budget_ptr;  // device budget (integrate path) or null
   double budget_val;         // host budget (step-level path)
   double guard;              // round-off guard factor g*u: retire if err <= guard |I7|
+  int last_sweep;            // 1: this is the last sweep the loop may run
+  int keep;                  // 1: record retired regions in the leaf list
+  double* c_leaf;            // final-partition list (keep == 1)
+  double* h_leaf;
+  int64_t ld_leaf;
+  int64_t leaf_cap;
   DevStatus* st;
 };
 

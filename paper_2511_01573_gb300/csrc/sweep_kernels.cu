@@ -114,6 +114,8 @@ __global__ void __launch_bounds__(kTile) k_sum_status(const SweepArgs S) {
       f |= kNonfinite | kDone;
     else if (E <= budget)
       f |= kConverged | kDone;
+    else if (S.last_sweep)
+      f |= kLastSweep | kDone;
     st->flags = f;
   }
 }
@@ -169,10 +171,20 @@ __global__ void __launch_bounds__(kTile) k_classify(const SweepArgs S) {
     st->E_ret = __dadd_rn(st->E_ret, B);
     st->n_split = total;
     int f = st->flags;
-    if (total == 0)
+    if (total == 0) {
       f |= kAllRetired | kDone;
-    else if (2 * total > S.cap)
+    } else if (2 * total > S.cap) {
       f |= kCapExceeded | kDone;
+    } else if (S.keep) {
+      // the split kernel appends this sweep's retired regions to the leaves
+      const long long nl = st->n_leaves + (S.n - total);
+      if (nl > S.leaf_cap) {
+        f |= kLeafOverflow | kDone;
+      } else {
+        st->leaf_base = st->n_leaves;
+        st->n_leaves = nl;
+      }
+    }
     st->flags = f;
   }
 }
@@ -188,8 +200,21 @@ __global__ void __launch_bounds__(kTile) k_split(const SweepArgs S) {
   __syncthreads();
   int wpre = 0;
   for (int w = 0; w < warp; ++w) wpre += wcount[w];
-  if (!f) return;
+  if (r >= S.n) return;
+  // split regions before r in the whole list
   const long long pos = S.blk_off[blockIdx.x] + wpre + __popc(bal & ((1u << lane) - 1u));
+  if (!f) {
+    if (S.keep) {
+      // retired: append to the final-partition list after the earlier
+      // retired regions of this sweep (r - pos of them)
+      const long long leaf = S.st->leaf_base + (r - pos);
+      for (int k = 0; k < S.d; ++k) {
+        S.c_leaf[(int64_t)k * S.ld_leaf + leaf] = S.c[(int64_t)k * S.ld + r];
+        S.h_leaf[(int64_t)k * S.ld_leaf + leaf] = S.h[(int64_t)k * S.ld + r];
+      }
+    }
+    return;
+  }
   const long long ns = S.st->n_split;
   const int ax = S.axis[r] & 0x7f;
   for (int k = 0; k < S.d; ++k) {
@@ -243,6 +268,43 @@ __global__ void __launch_bounds__(kTile) k_tree_sum(const double* v, int64_t n, 
     st->ticket_sum = 0u;
     *out = s;
   }
+}
+
+// Pairwise-tree sum of every row of v ([rows][ldv], n values per row):
+// blockIdx.y is the row; the last tile of a row to finish writes out[row].
+__global__ void __launch_bounds__(kTile) k_rows_tree_sum(const double* v, int64_t ldv, int64_t n,
+                                                         double* blk, unsigned* tickets,
+                                                         double* out) {
+  __shared__ double scratch[33];
+  __shared__ double tile_sums[kTile];
+  __shared__ int is_last;
+  const int row = blockIdx.y;
+  const int64_t r = (int64_t)blockIdx.x * kTile + threadIdx.x;
+  const double t = block_tree_sum(r < n ? v[(int64_t)row * ldv + r] : 0.0, scratch);
+  double* rb = blk + (int64_t)row * gridDim.x;
+  if (threadIdx.x == 0) {
+    rb[blockIdx.x] = t;
+    __threadfence();
+    const unsigned k = atomicAdd(&tickets[row], 1u);
+    is_last = (k == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const double s = tree_sum_global(rb, gridDim.x, scratch, tile_sums);
+  if (threadIdx.x == 0) {
+    tickets[row] = 0u;
+    out[row] = s;
+  }
+}
+
+cudaError_t launch_rows_tree_sum(const double* v, int64_t ldv, int64_t n, int rows, double* blk,
+                                 unsigned* tickets, double* out, cudaStream_t s) {
+  int64_t blocks = (n + kTile - 1) / kTile;
+  if (blocks == 0) blocks = 1;
+  k_rows_tree_sum<<<dim3((unsigned)blocks, (unsigned)rows), kTile, 0, s>>>(v, ldv, n, blk, tickets,
+                                                                          out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sum_status(const SweepArgs& S, cudaStream_t s) {

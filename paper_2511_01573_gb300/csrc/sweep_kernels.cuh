@@ -23,5 +23,8 @@ cudaError_t launch_split(const SweepArgs& S, cudaStream_t s);
 cudaError_t launch_partition(const PartArgs& P, cudaStream_t s);
 cudaError_t launch_tree_sum(const double* v, int64_t n, double* blk, DevStatus* st, double* out,
                             cudaStream_t s);
+// blk: rows * ceil(n / kTile) doubles; tickets: rows zeroed counters.
+cudaError_t launch_rows_tree_sum(const double* v, int64_t ldv, int64_t n, int rows, double* blk,
+                                 unsigned* tickets, double* out, cudaStream_t s);
 
 }  // namespace gmq

@@ -37,7 +37,7 @@ class Problem(C.Structure):
 class Options(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_regions", C.c_int64),
                 ("init_splits", C.c_int32), ("max_iters", C.c_int32), ("precision", C.c_int32),
-                ("classifier", C.c_int32), ("lanes", C.c_int32), ("reserved", C.c_int32)]
+                ("classifier", C.c_int32), ("lanes", C.c_int32), ("flags", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -62,7 +62,9 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_default_options", "gmq_integrate", "gmq_last_trace", "gmq_seed_genz",
            "gmq_status_string", "gmq_launch_count", "gmq_eval_rule", "gmq_classify_split",
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
-           "gmq_profile_read", "gmq_tree_sum_noalloc")
+           "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad")
+
+KEEP_PARTITION = 1
 
 ERR_TOO_LARGE = -6
 NOALLOC_MAX_N = 1 << 23
@@ -92,7 +94,7 @@ def lib():
         "gmq_destroy": [vp],
         "gmq_set_stream": [vp, vp],
         "gmq_set_pool": [vp, vp, C.c_size_t],
-        "gmq_pool_bytes": [i32, i64, C.POINTER(C.c_size_t)],
+        "gmq_pool_bytes": [i32, i64, i32, C.POINTER(C.c_size_t)],
         "gmq_default_options": [C.POINTER(Options)],
         "gmq_integrate": [vp, C.POINTER(Problem), C.POINTER(Options), C.POINTER(Result)],
         "gmq_last_trace": [vp, C.POINTER(Sweep), i32, C.POINTER(i32)],
@@ -107,6 +109,8 @@ def lib():
         "gmq_profile_reset": [vp],
         "gmq_profile_read": [vp, i32, C.POINTER(KernelStats)],
         "gmq_tree_sum_noalloc": [i32, i64, vp, vp, vp],
+        "gmq_partition_copy": [vp, vp, vp, i64, i64, C.POINTER(i64)],
+        "gmq_rule_grad": [vp, C.POINTER(Problem), i64, vp, vp, i64, C.POINTER(dbl), _dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -139,9 +143,9 @@ def _ptr(a):
     return a.ctypes.data_as(_dp)
 
 
-def pool_bytes(dim: int, max_regions: int) -> int:
+def pool_bytes(dim: int, max_regions: int, flags: int = 0) -> int:
     out = C.c_size_t()
-    _check("gmq_pool_bytes", lib().gmq_pool_bytes(dim, max_regions, C.byref(out)))
+    _check("gmq_pool_bytes", lib().gmq_pool_bytes(dim, max_regions, flags, C.byref(out)))
     return int(out.value)
 
 
@@ -262,16 +266,53 @@ class Context:
 
     def integrate(self, family, a=None, u=None, rel_tol=1e-6, lo=None, hi=None, abs_tol=1e-16,
                   max_regions=1 << 22, init_splits=0, max_iters=0, precision=FP64,
-                  classifier=VOLUME_SHARE, lanes=0, dim=None, check=True) -> IntegrateResult:
+                  classifier=VOLUME_SHARE, lanes=0, dim=None, check=True,
+                  keep_partition=False) -> IntegrateResult:
         p = _ProblemHandle(family, a, u, lo, hi, dim)
         o = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, precision, classifier,
-                    lanes, 0)
+                    lanes, KEEP_PARTITION if keep_partition else 0)
         r = Result()
+        self._last_dim = p.s.dim
         code = lib().gmq_integrate(self.h, C.byref(p.s), C.byref(o), C.byref(r))
         if check:
             _check("gmq_integrate", code, ok=(OK, CAP_REACHED, MAX_ITERS, ROUNDOFF_LIMIT))
         return IntegrateResult(r.integral, r.error, r.regions_evaluated, r.function_evals,
                                r.final_active, r.iterations, code)
+
+    def partition_copy(self):
+        """The final partition of the last integrate(keep_partition=True) call
+        as CUDA float64 tensors (center, halfw) of shape [dim, count]."""
+        torch = self.torch
+        cnt = C.c_int64()
+        _check("gmq_partition_copy", lib().gmq_partition_copy(self.h, None, None, 0, 0,
+                                                              C.byref(cnt)))
+        n = int(cnt.value)
+        if n < 0:
+            raise RuntimeError("no partition was kept by the last integration")
+        return self._copy_partition(n)
+
+    def _copy_partition(self, n):
+        torch = self.torch
+        # the dimension is that of the last problem; recover it from the pool copy
+        d = self._last_dim
+        c = torch.empty((d, max(n, 1)), dtype=torch.float64, device=f"cuda:{self.device}")
+        h = torch.empty_like(c)
+        cnt = C.c_int64()
+        _check("gmq_partition_copy", lib().gmq_partition_copy(self.h, _dptr(c), _dptr(h),
+                                                              max(n, 1), n, C.byref(cnt)))
+        return c[:, :n], h[:, :n]
+
+    def rule_grad(self, family, a, u, center, halfw, lo=None, hi=None):
+        """Frozen-partition quadrature Q and dQ/d(a_1..a_d, u_1..u_d) over the
+        regions (center, halfw: CUDA float64 [dim, n]).  Returns (grad, Q)."""
+        d, n = center.shape
+        ld = self._ld(center, halfw) if n > 0 else 1
+        p = _ProblemHandle(family, a, u, lo, hi, d)
+        g = np.zeros(2 * d)
+        q = C.c_double()
+        _check("gmq_rule_grad", lib().gmq_rule_grad(self.h, C.byref(p.s), n, _dptr(center),
+                                                    _dptr(halfw), ld, C.byref(q), _ptr(g)))
+        return g, q.value
 
     def last_trace(self):
         cnt = C.c_int32()
