@@ -45,6 +45,10 @@ def parse():
                          "kernel 3 times per family on 2^20 random d=8 regions and exits")
     ap.add_argument("--probe-split", action="store_true",
                     help="profiling probe: classify + split on 2^22 random d=8 regions")
+    ap.add_argument("--all-configs", action="store_true",
+                    help="report the other workloads (d=3, d=12 mixed, batch, gradients)")
+    ap.add_argument("--seeds-d12", type=int, default=3)
+    ap.add_argument("--grad-sets", type=int, default=32)
     ap.add_argument("--lanes", type=int, default=1)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -100,6 +104,21 @@ def time_to_tol(ctx, stream, tol):
     out["speedup_mixed_over_fp64"] = out["fp64_s"] / out["mixed_s"]
     out["mixed_max_rel_diff_vs_fp64"] = max(
         abs(m.integral - f.integral) / abs(f.integral) for m, f in zip(vals["mixed"], vals["fp64"]))
+    # batched form (FP64, one graph launch for all 40 problems)
+    ctx.integrate_batch(probs[:4], max_regions=CAP)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = ctx.integrate_batch(probs, max_regions=CAP, pool_regions=1 << 26)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["batched_s"] = e0.elapsed_time(e1) / 1000.0
+    out["batched_regions"] = sum(r.regions_evaluated for r in res)
+    out["batched_converged"] = sum(1 for r in res if r.status == 0)
+    out["speedup_batched_over_fp64"] = out["fp64_s"] / out["batched_s"]
+    out["batched_max_rel_diff_vs_fp64"] = max(
+        abs(b.integral - f.integral) / abs(f.integral) for b, f in zip(res, vals["fp64"]))
     return out
 
 
@@ -287,8 +306,104 @@ def probe_split(args):
     ctx.close()
 
 
+def _closed_gauss(a, u):
+    import math
+    g = [math.sqrt(math.pi) / (2 * ai) * (math.erf(ai * (1 - ui)) + math.erf(ai * ui))
+         for ai, ui in zip(a, u)]
+    dga = [-gi / ai + ((1 - ui) * math.exp(-(ai * (1 - ui)) ** 2)
+                       + ui * math.exp(-(ai * ui) ** 2)) / ai for gi, ai, ui in zip(g, a, u)]
+    dgu = [math.exp(-(ai * ui) ** 2) - math.exp(-(ai * (1 - ui)) ** 2) for ai, ui in zip(a, u)]
+    I = math.prod(g)
+    return I, [I / gi * x for gi, x in zip(g, dga)] + [I / gi * x for gi, x in zip(g, dgu)]
+
+
+def all_configs(args):
+    """The five workloads beside the benchmark's own: d = 3 product peak,
+    d = 12 FP64 against mixed, the 4096-integral batch, and the d = 6
+    Gaussian gradients.  Prints one JSON object (a report, not the metric)."""
+    import math
+    import torch
+    from paper_2511_01573_gb300 import autograd as AG
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    stream = torch.cuda.Stream(device=0)
+    ctx = gmq.Context(0, stream=stream)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1000.0
+
+    rep = {}
+    # product peak on [0,1]^3, a = 5, u = 1/2, tol 1e-6, cap 1e5
+    p = G.product_peak_d3()
+    r, t = timed(lambda: ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=100000))
+    ex = (10 * math.atan(2.5)) ** 3
+    rep["product_peak_d3"] = {"s": t, "regions": r.regions_evaluated, "sweeps": r.iterations,
+                              "status": r.status, "rel_err_vs_closed_form": abs(r.integral - ex) / ex,
+                              "error_estimate": r.error}
+    # d = 12 corner peak and Gaussian: FP64 against the mixed form
+    rows = []
+    for tol in (1e-4, 1e-5, 1e-6, 1e-7):
+        for fam in (G.CORNER_PEAK, G.GAUSSIAN):
+            for s in range(1, args.seeds_d12 + 1):
+                a, u = G.seed_genz(s, fam, 12, G.GENZ_TARGET_SUM[fam])
+                r64, t64 = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=1 << 22))
+                rmx, tmx = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=1 << 22,
+                                                       precision=gmq.MIXED))
+                rows.append({"family": G.FAMILY_NAMES[fam], "seed": s, "tol": tol,
+                             "fp64_s": t64, "mixed_s": tmx, "fp64_regions": r64.regions_evaluated,
+                             "mixed_regions": rmx.regions_evaluated, "fp64_status": r64.status,
+                             "mixed_status": rmx.status,
+                             "mixed_rel_diff_vs_fp64": abs(rmx.integral - r64.integral)
+                             / abs(r64.integral)})
+    rep["d12_fp64_vs_mixed"] = rows
+    # 4096 integrals in one batch against one-by-one calls on a sample
+    probs = G.batched_problems(count=4096)
+    bcap = 1 << 22  # per problem
+    res, tb = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27))
+    info = ctx.last_batch_info()
+    sample = probs[::64]
+    seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
+                                           lanes=1) for q in sample])
+    same = sum(1 for q, sr in zip(range(0, 4096, 64), seq)
+               if sr.integral == res[q].integral and sr.regions_evaluated == res[q].regions_evaluated)
+    st = {}
+    for x in res:
+        st[str(x.status)] = st.get(str(x.status), 0) + 1
+    rep["batch_4096"] = {"s": tb, "regions": sum(x.regions_evaluated for x in res),
+                         "statuses": st, "info": info, "sample_sequential_s": ts,
+                         "sample_size": len(sample),
+                         "sequential_estimate_s": ts * len(probs) / len(sample),
+                         "sample_identical_to_single_runs": same}
+    # gradients of the d = 6 Gaussian over frozen partitions
+    sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
+    errs, tf, tg = [], 0.0, 0.0
+    for a, u in sets:
+        at = torch.tensor(a, requires_grad=True)
+        ut = torch.tensor(u, requires_grad=True)
+        I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx, max_regions=1 << 24))
+        _, t2 = timed(lambda: I.backward())
+        tf += t1
+        tg += t2
+        Iex, gex = _closed_gauss(a, u)
+        g = list(at.grad.numpy()) + list(ut.grad.numpy())
+        errs.append(max(abs(x - y) for x, y in zip(g, gex)) / max(abs(y) for y in gex))
+    rep["gaussian_d6_gradients"] = {"sets": len(sets), "forward_s": tf, "adjoint_s": tg,
+                                    "max_rel_grad_err_vs_closed_form": max(errs)}
+    print(json.dumps(rep), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.all_configs:
+        return all_configs(args)
     if args.probe_rule:
         return probe_rule(args)
     if args.probe_split:

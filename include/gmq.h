@@ -182,6 +182,57 @@ gmq_status gmq_partition_copy(gmq_context *ctx, double *d_center,
                               double *d_halfw, int64_t ld, int64_t max,
                               int64_t *count);
 
+/* ---- batched form ------------------------------------------------------ */
+
+/* gmq_options.flags for gmq_integrate_batch: drive the sweeps from the host
+ * (one launch sequence per sweep, status read every few sweeps) instead of
+ * one CUDA-graph launch whose while-node runs every sweep on the device. */
+#define GMQ_BATCH_HOST_LOOP 2
+
+/* How the last gmq_integrate_batch call ran. */
+typedef struct gmq_batch_info {
+  int32_t rule_block;   /* threads per block of the rule kernel (autotuned)  */
+  int32_t rule_grid;    /* blocks of its persistent grid                    */
+  int32_t sweeps;       /* sweeps of the device loop                        */
+  int32_t used_graph;   /* 1: ran as one CUDA graph with a while node       */
+  int32_t autotuned;    /* 1: this call timed the candidate launch shapes   */
+  int32_t pauses;       /* problem-sweeps deferred because the pool was full */
+  int32_t evictions;    /* problems evicted and restarted to make room      */
+  int32_t reserved;
+  double tune_ms[4];    /* rule-kernel time of each candidate (-1 if unused) */
+} gmq_batch_info;
+
+/* Many independent integrals in one device-resident loop (no counterpart in
+ * the paper, which integrates one problem at a time).  Every problem runs
+ * the paper's loop (Sec. 3) with the same decisions, sums and child order
+ * as gmq_integrate gives it alone with one thread per region; all of them
+ * advance one sweep per iteration, their active regions sharing one region
+ * pool of pool_regions regions (0: max(opt->max_regions, 4 x the initial
+ * partitions)); opt->max_regions is each problem's own cap.  probs[i] and
+ * rel_tols[i] (rel_tols may be NULL: opt->rel_tol for all) describe
+ * problem i; results[i] receives its result and status.  When the next
+ * sweep of all running problems does not fit in the pool, the problems
+ * whose region lists grow are served in index order while they fit; the
+ * others are paused for a sweep (their regions are carried over unchanged
+ * and evaluated again, which leaves their results unchanged); if nothing
+ * can split, the paused problem of highest index is evicted and later
+ * restarts from its initial partition (same result again), and a problem
+ * that cannot grow even alone stops with GMQ_CAP_REACHED.  The device loop
+ * is bounded by 4 x max_iters sweeps.  Device memory: about
+ * pool_regions x (32 dmax + 30) bytes, dmax the largest dimension.  FP64 only
+ * (opt->precision must be GMQ_FP64); opt->lanes is ignored: the rule
+ * kernel's block size and persistent grid are chosen by timing the
+ * candidates on the first call for each largest dimension (cached in the
+ * context).  Returns GMQ_OK when the batch ran (see the per-problem
+ * statuses), or an error. */
+gmq_status gmq_integrate_batch(gmq_context *ctx, int32_t count,
+                               const gmq_problem *probs, const double *rel_tols,
+                               const gmq_options *opt, int64_t pool_regions,
+                               gmq_result *results);
+
+/* Launch shape, sweep count and autotuning record of the last batch. */
+gmq_status gmq_last_batch_info(gmq_context *ctx, gmq_batch_info *info);
+
 /* Adjoint over a frozen partition (no counterpart in the paper; the
  * differentiation extension).  For the n regions given (typically the
  * final partition of an integration), Q = sum_r vol_r sum_i w_i f(x_i) with
@@ -205,6 +256,10 @@ gmq_status gmq_seed_genz(uint64_t seed, int32_t family, int32_t dim,
 
 /* Human-readable name of a status code (static string). */
 const char *gmq_status_string(gmq_status s);
+
+/* Name of the CUDA error behind the calling thread's last GMQ_ERR_CUDA or
+ * GMQ_ERR_OOM (static string, e.g. "cudaErrorInvalidValue"). */
+const char *gmq_last_cuda_error(void);
 
 /* Number of kernels the context has launched since creation. */
 gmq_status gmq_launch_count(gmq_context *ctx, int64_t *count);

@@ -1,0 +1,682 @@
+// gm_batch.cu -- many independent integrals in one device-resident loop
+// (gmq_integrate_batch).  No counterpart in the paper, which integrates one
+// problem at a time; every integral follows the paper's loop (Sec. 3, Fig.
+// 1a) exactly as gmq_integrate runs it, but all of them advance together,
+// one sweep per iteration, inside one CUDA graph.
+//
+// Layout: one region pool holds every integral's active regions; integral i
+// owns the contiguous segment [off_i, off_i + n_i) of the current list (SoA,
+// dmax rows, plus an int32 owner id per region).  Per sweep:
+//   k_batch_rule      all regions of all integrals, one thread per region,
+//                     persistent grid; family and dimension per region
+//   k_batch_sums      one block per integral: pairwise-tree sums over its
+//                     segment, convergence / sweep-limit test
+//   k_batch_classify  one block per integral: flags, split count, retired
+//                     pairwise-tree sums, round-off guard, per-integral cap
+//   k_batch_scan      one block: new segment offsets (exclusive scan of
+//                     2 n_split over the integrals still running), pool check
+//   k_batch_split     one block per integral: left children then right
+//                     children of its split regions into its new segment
+//   k_batch_advance   one thread: swap the lists, count the sweep, and set
+//                     the graph's loop condition (bounded by max_iters)
+// Per-integral sums use the same pairwise tree over the segment as the
+// single-integral path, and the same child order, so every integral's
+// result is the result gmq_integrate gives for it alone.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gm_batch.cuh"
+#include "gm_rule.cuh"
+
+namespace gmq {
+
+namespace {
+
+constexpr int kSegBlock = 1024;  // threads of the per-integral kernels
+constexpr int kSegTile = 4 * kSegBlock;  // regions per tile (4 per thread)
+
+// Pairwise-tree sum of a tile of 4 * blockDim values, 4 consecutive values
+// per thread: ((v0 + v1) + (v2 + v3)) is the first two levels of the tree.
+__device__ __forceinline__ double tile_tree(double v0, double v1, double v2, double v3,
+                                            double* scratch) {
+  return block_tree_sum((v0 + v1) + (v2 + v3), scratch);
+}
+
+// Pairwise-tree sum over the segment values get(i), i in [0, count), by one
+// block: tiles of kSegTile are complete subtrees; tile sums (at most
+// kSegBlock per group) are summed with the same tree, and groups of
+// kSegBlock tiles once more.
+template <class Get>
+__device__ double seg_tree_sum(Get get, long long count, double* scratch, double* tsum,
+                               double* gsum) {
+  const int tid = threadIdx.x;
+  const long long ntiles = (count + kSegTile - 1) / kSegTile;
+  const long long ngroups = (ntiles + kSegBlock - 1) / kSegBlock;
+  for (long long gi = 0; gi < ngroups; ++gi) {
+    const long long t0 = gi * kSegBlock;
+    const long long t1 = t0 + kSegBlock < ntiles ? t0 + kSegBlock : ntiles;
+    for (long long t = t0; t < t1; ++t) {
+      const long long i = t * kSegTile + 4LL * tid;
+      const double s = tile_tree(i < count ? get(i) : 0.0, i + 1 < count ? get(i + 1) : 0.0,
+                                 i + 2 < count ? get(i + 2) : 0.0, i + 3 < count ? get(i + 3) : 0.0,
+                                 scratch);
+      if (tid == 0) tsum[t - t0] = s;
+    }
+    __syncthreads();
+    const double g = block_tree_sum(tid < t1 - t0 ? tsum[tid] : 0.0, scratch);
+    if (tid == 0) gsum[gi] = g;
+    __syncthreads();
+  }
+  // at most kSegBlock groups (segments up to 2^32 regions)
+  return block_tree_sum(tid < ngroups ? gsum[tid] : 0.0, scratch);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+__global__ void k_batch_partition(const BatchArgs B) {
+  const int id = blockIdx.x;
+  const BatchItem& it = B.items[id];
+  const int d = it.P.d;
+  double* c = B.c[0];
+  double* h = B.h[0];
+  for (long long q = threadIdx.x; q < it.n; q += blockDim.x) {
+    long long rem = q;
+    const long long r = it.off + q;
+    for (int k = 0; k < d; ++k) {
+      const long long i = rem % it.s;
+      rem /= it.s;
+      c[(int64_t)k * B.ld + r] = __dadd_rn(it.lo[k], __dmul_rn((double)(2 * i + 1), it.h0[k]));
+      h[(int64_t)k * B.ld + r] = it.h0[k];
+    }
+    B.rid[0][r] = id;
+  }
+}
+
+template <int RB>
+__global__ void __launch_bounds__(RB) k_batch_rule(const BatchArgs B) {
+  extern __shared__ __align__(16) double smem[];
+  const BatchState* bs = B.bs;
+  const long long n_total = bs->n_total;
+  const int cur = bs->parity;
+  const double* C = B.c[cur];
+  const double* H = B.h[cur];
+  const int32_t* rid = B.rid[cur];
+  const int dm = B.dmax;
+  const int tid = threadIdx.x;
+  // this thread's column of the coordinate table: rows kXC..kXM5 and h
+  double* col = smem + tid;  // element (row, k) at col[(row * dm + k) * RB]
+  auto T = [&](int row, int k) -> double& { return col[(row * dm + k) * RB]; };
+  for (long long tile = blockIdx.x; tile * RB < n_total; tile += gridDim.x) {
+    const long long r = tile * RB + tid;
+    if (r >= n_total) continue;
+    const BatchItem& it = B.items[rid[r]];
+    const int d = it.P.d;
+    const int fam = it.P.family;
+    for (int k = 0; k < d; ++k) {
+      const double cv = C[(int64_t)k * B.ld + r], hv = H[(int64_t)k * B.ld + r];
+      T(kXC, k) = cv;
+      T(kXP2, k) = fma(B.lam2, hv, cv);
+      T(kXM2, k) = fma(-B.lam2, hv, cv);
+      T(kXP3, k) = fma(B.lam3, hv, cv);
+      T(kXM3, k) = fma(-B.lam3, hv, cv);
+      T(kXP5, k) = fma(B.lam5, hv, cv);
+      T(kXM5, k) = fma(-B.lam5, hv, cv);
+      T(kXRows, k) = hv;
+    }
+    const int N = it.nodes;
+    const int b4 = 1 + 4 * d, b5 = b4 + 2 * d * (d - 1);
+    double S1 = 0.0, S2 = 0.0, S3 = 0.0, S4 = 0.0, S5 = 0.0;
+    double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
+    int kbest = 0, pj = 0, pk = 1, pc = 0;
+    for (int i = 0; i < N; ++i) {
+      int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
+      unsigned m = 0u;
+      if (i == 0) {
+        kind = 1;
+      } else if (i < b4) {
+        const int q = i - 1;
+        k1 = q >> 2;
+        w = q & 3;
+        r1 = kXP2 + w;
+        kind = (w < 2) ? 2 : 3;
+      } else if (i < b5) {
+        const int q = i - b4;
+        k1 = pj;
+        k2 = pk;
+        r1 = (q & 2) ? kXM3 : kXP3;
+        r2 = (q & 1) ? kXM3 : kXP3;
+        kind = 4;
+        if (++pc == 4) {
+          pc = 0;
+          if (++pk == d) {
+            ++pj;
+            pk = pj + 1;
+          }
+        }
+      } else {
+        m = (unsigned)(i - b5);
+        kind = 5;
+      }
+      auto X = [&](int j) -> double {
+        int row;
+        if (kind == 5)
+          row = ((m >> j) & 1u) ? kXM5 : kXP5;
+        else
+          row = (j == k1) ? r1 : ((j == k2) ? r2 : kXC);
+        return T(row, j);
+      };
+      double v;
+      switch (fam) {
+        case GMQ_OSCILLATORY: v = Family<GMQ_OSCILLATORY>::template eval<double>(it.P, d, X); break;
+        case GMQ_PRODUCT_PEAK: v = Family<GMQ_PRODUCT_PEAK>::template eval<double>(it.P, d, X); break;
+        case GMQ_CORNER_PEAK: v = Family<GMQ_CORNER_PEAK>::template eval<double>(it.P, d, X); break;
+        case GMQ_GAUSSIAN: v = Family<GMQ_GAUSSIAN>::template eval<double>(it.P, d, X); break;
+        case GMQ_C0: v = Family<GMQ_C0>::template eval<double>(it.P, d, X); break;
+        case GMQ_DISCONTINUOUS: v = Family<GMQ_DISCONTINUOUS>::template eval<double>(it.P, d, X); break;
+        default: v = Family<GMQ_POLY_SUMSQ11>::template eval<double>(it.P, d, X); break;
+      }
+      if (kind == 5) {
+        S5 += v;
+      } else if (kind == 4) {
+        S4 += v;
+      } else if (kind == 1) {
+        S1 += v;
+        f0 = v;
+      } else {
+        if (kind == 2)
+          S2 += v;
+        else
+          S3 += v;
+        if (w == 0) {
+          q0 = v;
+        } else if (w == 1) {
+          q1 = v;
+        } else if (w == 2) {
+          q2 = v;
+        } else {
+          const double two_f0 = __dmul_rn(2.0, f0);
+          const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
+          const double t2 = __dsub_rn(__dadd_rn(q2, v), two_f0);
+          const double D = fabs(__dsub_rn(t1, __dmul_rn(B.ratio, t2)));
+          if (D > dbest) {
+            dbest = D;
+            kbest = k1;
+          }
+        }
+      }
+    }
+    double vol = 1.0;
+    for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, T(kXRows, k)));
+    double t7 = __dmul_rn(it.w7[0], S1);
+    t7 = __dadd_rn(t7, __dmul_rn(it.w7[1], S2));
+    t7 = __dadd_rn(t7, __dmul_rn(it.w7[2], S3));
+    t7 = __dadd_rn(t7, __dmul_rn(it.w7[3], S4));
+    t7 = __dadd_rn(t7, __dmul_rn(it.w7[4], S5));
+    double t5 = __dmul_rn(it.w5[0], S1);
+    t5 = __dadd_rn(t5, __dmul_rn(it.w5[1], S2));
+    t5 = __dadd_rn(t5, __dmul_rn(it.w5[2], S3));
+    t5 = __dadd_rn(t5, __dmul_rn(it.w5[3], S4));
+    const double i7 = __dmul_rn(vol, t7);
+    const double i5 = __dmul_rn(vol, t5);
+    const double flat_thr = __dadd_rn(__dmul_rn(1e-14, fabs(f0)), 1e-300);
+    int ax = kbest;
+    if (!(dbest > flat_thr)) {
+      ax = 0;
+      double hb = T(kXRows, 0);
+      for (int k = 1; k < d; ++k)
+        if (T(kXRows, k) > hb) {
+          hb = T(kXRows, k);
+          ax = k;
+        }
+    }
+    const double cs = T(kXC, ax);
+    const double hh = __dmul_rn(0.5, T(kXRows, ax));
+    const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
+    B.i7[r] = i7;
+    B.err[r] = fabs(__dsub_rn(i7, i5));
+    B.vf[r] = __ddiv_rn(vol, it.vol_omega);
+    B.axis[r] = (uint8_t)(ax | (bad ? 0x80 : 0));
+  }
+}
+
+__global__ void __launch_bounds__(kSegBlock) k_batch_sums(const BatchArgs B) {
+  __shared__ double scratch[33];
+  __shared__ double tsum[kSegBlock];
+  __shared__ double gsum[kSegBlock];
+  BatchItem& it = B.items[blockIdx.x];
+  if ((it.flags & kDone) || it.deferred) return;
+  const long long off = it.off;
+  const double A = seg_tree_sum([&](long long i) { return B.i7[off + i]; }, it.n, scratch, tsum,
+                                gsum);
+  const double E2 = seg_tree_sum([&](long long i) { return B.err[off + i]; }, it.n, scratch, tsum,
+                                 gsum);
+  if (threadIdx.x == 0) {
+    const double I = __dadd_rn(it.I_ret, A);
+    const double E = __dadd_rn(it.E_ret, E2);
+    const double budget = fmax(it.abs_tol, __dmul_rn(it.rel_tol, fabs(I)));
+    it.I = I;
+    it.E = E;
+    it.budget = budget;
+    it.iters += 1;
+    it.regions += it.n;
+    int f = it.flags;
+    if (!isfinite(I) || !isfinite(E))
+      f |= kNonfinite | kDone;
+    else if (E <= budget)
+      f |= kConverged | kDone;
+    else if (it.iters >= B.bs->max_iters)
+      f |= kLastSweep | kDone;
+    it.flags = f;
+  }
+}
+
+__global__ void __launch_bounds__(kSegBlock) k_batch_classify(const BatchArgs B) {
+  __shared__ double scratch[33];
+  __shared__ double tsum[kSegBlock];
+  __shared__ double gsum[kSegBlock];
+  __shared__ long long cnt;
+  BatchItem& it = B.items[blockIdx.x];
+  if ((it.flags & kDone) || it.deferred) return;
+  const long long off = it.off, n = it.n;
+  const double budget = it.budget;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  // flags and split count
+  for (long long base = 0; base < n; base += kSegBlock) {
+    const long long i = base + threadIdx.x;
+    int split = 0;
+    if (i < n) {
+      const long long r = off + i;
+      const double i7 = B.i7[r], e = B.err[r];
+      const double thr = (B.classifier == GMQ_LOCAL_REL) ? __dmul_rn(it.rel_tol, fabs(i7))
+                                                         : __dmul_rn(budget, B.vf[r]);
+      const bool retire = (e <= thr) || (e <= __dmul_rn(B.guard, fabs(i7))) || (B.axis[r] & 0x80);
+      split = retire ? 0 : 1;
+      B.flags[r] = (uint8_t)split;
+    }
+    const int c = __syncthreads_count(split);
+    if (threadIdx.x == 0) cnt += c;
+  }
+  __syncthreads();
+  // retired sums over the segment (split regions contribute zero)
+  const double ri = seg_tree_sum(
+      [&](long long i) { return B.flags[off + i] ? 0.0 : B.i7[off + i]; }, n, scratch, tsum, gsum);
+  const double re = seg_tree_sum(
+      [&](long long i) { return B.flags[off + i] ? 0.0 : B.err[off + i]; }, n, scratch, tsum, gsum);
+  if (threadIdx.x == 0) {
+    const long long total = cnt;
+    it.n_split = total;
+    int f = it.flags;
+    if (total == 0 || 2 * total > it.cap) {
+      // the integral stops this sweep either way: commit now
+      it.I_ret = __dadd_rn(it.I_ret, ri);
+      it.E_ret = __dadd_rn(it.E_ret, re);
+      f |= (total == 0 ? kAllRetired : kCapExceeded) | kDone;
+    } else {
+      // committed by the scan if the split fits in the pool this sweep
+      it.ret_i = ri;
+      it.ret_e = re;
+    }
+    it.flags = f;
+  }
+}
+
+// Inclusive scan of one value per thread over a block of kSegBlock threads;
+// *tot receives the block total.
+__device__ long long block_incl_scan(long long v, long long* wsum, long long* tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  const long long incl = x + (warp > 0 ? wsum[warp - 1] : 0);
+  *tot = wsum[31];
+  __syncthreads();
+  return incl;
+}
+
+// Pool allocation of the next list.  Every running integral first keeps
+// room for its current regions (their total fits: they are in the pool
+// now); integrals whose list shrinks always split; the growing ones split
+// while the running sum of their growth, in index order, fits in the rest
+// of the pool.  A growing integral that does not fit is paused: it keeps
+// this sweep's regions unchanged, its retired sums are not committed and
+// its counters are rolled back, so next sweep it re-evaluates the same
+// regions and takes the same decisions (its result is unchanged, only
+// later).  If nothing can split while some integral is paused, the paused
+// integral with the highest index is evicted: its regions and state are
+// dropped and it waits, holding nothing, until the pool has room for its
+// initial partition, when it starts over (deterministically, so again with
+// its single-run result).  Evicted integrals restart in index order.  An
+// integral that cannot grow even with the pool to itself stops (cap).
+__global__ void __launch_bounds__(kSegBlock) k_batch_scan(const BatchArgs B) {
+  __shared__ long long wsum[32];
+  __shared__ int active_s, admitted_s, paused_hi, paused_lo, running_s, stop_first;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    active_s = 0;
+    admitted_s = 0;
+    paused_hi = -1;
+    paused_lo = 0x7fffffff;
+    running_s = 0;
+    stop_first = 0;
+  }
+  __syncthreads();
+  auto running = [&](int i) {
+    return i < B.count && !(B.items[i].flags & kDone) && !B.items[i].deferred;
+  };
+  long long tot = 0, R = 0;
+  for (int base = 0; base < B.count; base += kSegBlock) {
+    const int i = base + tid;
+    const bool run = running(i);
+    if (run) atomicAdd(&running_s, 1);
+    block_incl_scan(run ? B.items[i].n : 0, wsum, &tot);
+    R += tot;
+  }
+  const long long budget = B.pool_cap - R;
+  long long carry = 0;
+  for (int base = 0; base < B.count; base += kSegBlock) {
+    const int i = base + tid;
+    const bool run = running(i);
+    long long grow = 0;
+    if (run) grow = 2 * B.items[i].n_split - B.items[i].n;
+    const long long pre = carry + block_incl_scan(grow > 0 ? grow : 0, wsum, &tot);
+    if (run) {
+      const bool admit = grow <= 0 || pre <= budget;
+      B.items[i].paused = admit ? 0 : 1;
+      if (admit) {
+        atomicOr(&admitted_s, 1);
+      } else {
+        atomicMax(&paused_hi, i);
+        atomicMin(&paused_lo, i);
+      }
+    }
+    carry += tot;
+  }
+  __syncthreads();
+  // Nothing can split: make room for the paused integral of lowest index
+  // (f) by evicting paused integrals from the highest index down, as few as
+  // free its missing room; if evicting all of them would not be enough, f
+  // cannot grow in this pool and stops instead.  Evicted integrals drop
+  // their regions and state and restart later from their initial partition.
+  if (admitted_s == 0 && paused_hi >= 0) {
+    const int f = paused_lo;
+    const long long need = (2 * B.items[f].n_split - B.items[f].n) - budget;
+    long long carry2 = 0, all = 0;
+    for (int base = 0; base < B.count; base += kSegBlock) {  // total of the others
+      const int i = base + tid;
+      const bool cand = i < B.count && i != f && running(i) && B.items[i].paused;
+      block_incl_scan(cand ? B.items[i].n : 0, wsum, &tot);
+      all += tot;
+    }
+    if (all < need) {
+      if (tid == 0) stop_first = 1;
+    } else {
+      for (int base = 0; base < B.count; base += kSegBlock) {  // suffix sums, high index first
+        const int i = B.count - 1 - (base + tid);
+        const bool cand = i >= 0 && i != f && running(i) && B.items[i].paused;
+        const long long suffix = carry2 + block_incl_scan(cand ? B.items[i].n : 0, wsum, &tot);
+        if (cand && suffix - B.items[i].n < need) {
+          BatchItem& v = B.items[i];
+          v.paused = 0;
+          v.deferred = 2;  // evicted this sweep: not restarted before the next
+          v.I_ret = v.E_ret = 0.0;
+          v.iters = 0;
+          v.regions = 0;
+          v.n = 0;
+          atomicAdd(&B.bs->evictions, 1);
+        }
+        carry2 += tot;
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && stop_first) {
+      BatchItem& v = B.items[f];
+      v.paused = 0;
+      v.flags |= kCapExceeded | kDone;
+    }
+  }
+  __syncthreads();
+  // sizes of the next list for the running integrals
+  long long used = 0;
+  for (int base = 0; base < B.count; base += kSegBlock) {
+    const int i = base + tid;
+    long long size = 0;
+    if (running(i)) {
+      BatchItem& it = B.items[i];
+      size = it.paused ? it.n : 2 * it.n_split;
+    }
+    block_incl_scan(size, wsum, &tot);
+    used += tot;
+  }
+  // waiting integrals (evicted, or not yet admitted) start, in index order,
+  // only in a sweep where nothing had to pause, and only while their
+  // initial partitions leave a quarter of the pool free for growth: an
+  // integral started into a full pool would only be evicted again
+  const bool slack = paused_hi < 0;
+  const long long room = B.pool_cap - used - B.pool_cap / 4;
+  carry = 0;
+  for (int base = 0; base < B.count; base += kSegBlock) {
+    const int i = base + tid;
+    const bool waiting = i < B.count && !(B.items[i].flags & kDone) && B.items[i].deferred == 1;
+    const long long need = waiting ? B.items[i].n0 : 0;
+    const long long pre = carry + block_incl_scan(need, wsum, &tot);
+    if (waiting && slack && pre <= room) {
+      B.items[i].deferred = 0;
+      B.items[i].restart = 1;
+    }
+    carry += tot;
+  }
+  __syncthreads();
+  carry = 0;
+  for (int base = 0; base < B.count; base += kSegBlock) {
+    const int i = base + tid;
+    long long size = 0;
+    if (i < B.count) {
+      BatchItem& it = B.items[i];
+      if (!(it.flags & kDone)) {
+        if (it.restart) {
+          size = it.n0;
+        } else if (it.deferred) {
+          size = 0;
+          it.deferred = 1;
+        } else if (it.paused) {
+          size = it.n;
+          it.iters -= 1;
+          it.regions -= it.n;
+          atomicAdd(&B.bs->pauses, 1);
+        } else {
+          size = 2 * it.n_split;
+          it.I_ret = __dadd_rn(it.I_ret, it.ret_i);
+          it.E_ret = __dadd_rn(it.E_ret, it.ret_e);
+        }
+        atomicAdd(&active_s, 1);
+      }
+    }
+    const long long incl = block_incl_scan(size, wsum, &tot);
+    if (i < B.count) B.items[i].noff = carry + incl - size;
+    carry += tot;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    B.bs->n_next = carry;
+    B.bs->active = active_s;
+  }
+}
+
+__global__ void __launch_bounds__(kSegBlock) k_batch_split(const BatchArgs B) {
+  __shared__ int wcount[32];
+  __shared__ long long carry_s;
+  BatchItem& it = B.items[blockIdx.x];
+  if ((it.flags & kDone) || it.deferred) return;
+  const int cur = B.bs->parity, nxt = cur ^ 1;
+  const double* C = B.c[cur];
+  const double* H = B.h[cur];
+  double* Co = B.c[nxt];
+  double* Ho = B.h[nxt];
+  int32_t* rido = B.rid[nxt];
+  const long long off = it.off, n = it.n, ns = it.n_split, noff = it.noff;
+  const int d = it.P.d;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (it.restart) {
+    // an evicted integral starts over: its initial partition
+    for (long long q = tid; q < it.n0; q += kSegBlock) {
+      long long rem = q;
+      for (int k = 0; k < d; ++k) {
+        const long long i = rem % it.s;
+        rem /= it.s;
+        Co[(int64_t)k * B.ld + noff + q] =
+            __dadd_rn(it.lo[k], __dmul_rn((double)(2 * i + 1), it.h0[k]));
+        Ho[(int64_t)k * B.ld + noff + q] = it.h0[k];
+      }
+      rido[noff + q] = (int32_t)blockIdx.x;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      it.off = noff;
+      it.n = it.n0;
+      it.restart = 0;
+    }
+    return;
+  }
+  if (it.paused) {
+    // no room this sweep: carry the segment over unchanged
+    for (long long i = tid; i < n; i += kSegBlock) {
+      for (int k = 0; k < d; ++k) {
+        Co[(int64_t)k * B.ld + noff + i] = C[(int64_t)k * B.ld + off + i];
+        Ho[(int64_t)k * B.ld + noff + i] = H[(int64_t)k * B.ld + off + i];
+      }
+      rido[noff + i] = (int32_t)blockIdx.x;
+    }
+    __syncthreads();
+    if (tid == 0) it.off = noff;
+    return;
+  }
+  if (tid == 0) carry_s = 0;
+  __syncthreads();
+  for (long long base = 0; base < n; base += kSegBlock) {
+    const long long i = base + tid;
+    const long long r = off + i;
+    const int f = (i < n) ? (int)B.flags[r] : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcount[warp] = __popc(bal);
+    __syncthreads();
+    int wpre = 0, tot = 0;
+    for (int w = 0; w < kSegBlock / 32; ++w) {
+      if (w < warp) wpre += wcount[w];
+      tot += wcount[w];
+    }
+    if (f) {
+      const long long pos = carry_s + wpre + __popc(bal & ((1u << lane) - 1u));
+      const int ax = B.axis[r] & 0x7f;
+      for (int k = 0; k < d; ++k) {
+        const double cv = C[(int64_t)k * B.ld + r];
+        const double hv = H[(int64_t)k * B.ld + r];
+        double cl = cv, cr = cv, hc = hv;
+        if (k == ax) {
+          hc = __dmul_rn(0.5, hv);
+          cl = __dsub_rn(cv, hc);
+          cr = __dadd_rn(cv, hc);
+        }
+        Co[(int64_t)k * B.ld + noff + pos] = cl;
+        Ho[(int64_t)k * B.ld + noff + pos] = hc;
+        Co[(int64_t)k * B.ld + noff + ns + pos] = cr;
+        Ho[(int64_t)k * B.ld + noff + ns + pos] = hc;
+      }
+      rido[noff + pos] = (int32_t)blockIdx.x;
+      rido[noff + ns + pos] = (int32_t)blockIdx.x;
+    }
+    __syncthreads();
+    if (tid == 0) carry_s += tot;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    it.off = noff;
+    it.n = 2 * ns;
+  }
+}
+
+__global__ void k_batch_advance(const BatchArgs B) {
+  BatchState* bs = B.bs;
+  bs->n_total = bs->n_next;
+  bs->parity ^= 1;
+  bs->sweep += 1;
+  // problems waiting for room count as active: a sweep with no regions
+  // still runs the scan that starts them
+  const bool more = bs->active > 0 && bs->sweep < bs->max_sweeps;
+  if (B.use_cond) cudaGraphSetConditional(B.cond, more ? 1u : 0u);
+}
+
+size_t batch_rule_smem(int dmax, int rb) {
+  return sizeof(double) * (size_t)(kXRows + 1) * (size_t)dmax * (size_t)rb;
+}
+
+template <int RB>
+static cudaError_t rule_launch_rb(const BatchArgs& B, int grid, cudaStream_t s) {
+  const size_t smem = batch_rule_smem(B.dmax, RB);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch_rule<RB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_batch_rule<RB><<<grid, RB, smem, s>>>(B);
+  return cudaGetLastError();
+}
+
+int batch_rule_max_blocks(int dmax, int rb) {
+  int nb = 0;
+  const size_t smem = batch_rule_smem(dmax, rb);
+  cudaError_t e;
+  if (rb == 64) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_batch_rule<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_rule<64>, 64, smem);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_batch_rule<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_rule<128>, 128, smem);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+cudaError_t batch_launch_partition(const BatchArgs& B, cudaStream_t s) {
+  k_batch_partition<<<B.count, 256, 0, s>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_launch_rule(const BatchArgs& B, int rb, int grid, cudaStream_t s) {
+  return rb == 64 ? rule_launch_rb<64>(B, grid, s) : rule_launch_rb<128>(B, grid, s);
+}
+
+cudaError_t batch_launch_rest(const BatchArgs& B, cudaStream_t s) {
+  k_batch_sums<<<B.count, kSegBlock, 0, s>>>(B);
+  k_batch_classify<<<B.count, kSegBlock, 0, s>>>(B);
+  k_batch_scan<<<1, kSegBlock, 0, s>>>(B);
+  k_batch_split<<<B.count, kSegBlock, 0, s>>>(B);
+  k_batch_advance<<<1, 1, 0, s>>>(B);
+  return cudaGetLastError();
+}
+
+}  // namespace gmq

@@ -266,6 +266,243 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule(const RuleArgs A) {
   }
 }
 
+// Integrand parameters in registers (compile-time dimension).
+template <int D>
+struct RegParams {
+  float a[D], u[D], b[D];
+  float c0;
+};
+
+// Mixed form, one thread per region, dimension D known at compile time.
+// The centre, axis and pair nodes (classes 1-4) go through the shared-memory
+// coordinate table as in k_rule; the 2^D sign-pattern nodes are walked in
+// Gray-code order over a register-resident node vector: consecutive
+// patterns differ in one coordinate, which moves between c_k + l5 h_k and
+// c_k - l5 h_k by XOR-ing the two FP32 bit patterns.  Eight patterns per
+// step: the coordinates that change inside an aligned group of eight are
+// axes 0, 1, 0, 2, 0, 1, 0 (known at compile time); the one changed on
+// entering the group (axis >= 3) is picked with a predicated select.
+template <int FAM, int D>
+__global__ void __launch_bounds__(kRuleBlock) k_rule_mixed_reg(const RuleArgs A) {
+  static_assert(D >= 3 && D <= 16, "gray walk needs D >= 3");
+  constexpr int RB = kRuleBlock;
+  constexpr int d = D;
+  extern __shared__ __align__(16) double smem[];
+  double* cd = smem;
+  double* hd = cd + d * RB;
+  float* xt = reinterpret_cast<float*>(hd + d * RB);
+  SmemParams<float>* P = reinterpret_cast<SmemParams<float>*>(xt + kXRows * d * RB);
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  for (int j = tid; j < d; j += RB) {
+    P->a[j] = (float)A.P.a[j];
+    P->u[j] = (float)A.P.u[j];
+    P->b[j] = (float)A.P.b[j];
+  }
+  if (tid == 0) P->c0 = (float)A.P.c0;
+  const double l2 = A.R.lam2, l3 = A.R.lam3, l5 = A.R.lam5;
+  for (int idx = tid; idx < d * RB; idx += RB) {
+    const int k = idx / RB, q = idx - k * RB;
+    const int64_t r = r0 + q;
+    double cv = 0.5, hv = 0.25;
+    if (r < A.n) {
+      cv = A.c[(int64_t)k * A.ld + r];
+      hv = A.h[(int64_t)k * A.ld + r];
+    }
+    cd[k * RB + q] = cv;
+    hd[k * RB + q] = hv;
+    xt[(kXC * d + k) * RB + q] = (float)cv;
+    xt[(kXP2 * d + k) * RB + q] = (float)fma(l2, hv, cv);
+    xt[(kXM2 * d + k) * RB + q] = (float)fma(-l2, hv, cv);
+    xt[(kXP3 * d + k) * RB + q] = (float)fma(l3, hv, cv);
+    xt[(kXM3 * d + k) * RB + q] = (float)fma(-l3, hv, cv);
+    xt[(kXP5 * d + k) * RB + q] = (float)fma(l5, hv, cv);
+    xt[(kXM5 * d + k) * RB + q] = (float)fma(-l5, hv, cv);
+  }
+  __syncthreads();
+  const int g = tid;
+  const int64_t r = r0 + g;
+  if (r >= A.n) return;
+  RegParams<D> rp;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    rp.a[j] = P->a[j];
+    rp.u[j] = P->u[j];
+    rp.b[j] = P->b[j];
+  }
+  rp.c0 = P->c0;
+  const int b4 = 1 + 4 * d;
+  const int b5 = b4 + 2 * d * (d - 1);
+  const double ratio = A.R.ratio;
+  Acc<float> S1, S2, S3, S4, S5;
+  double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
+  int kbest = 0, pj = 0, pk = 1, pc = 0;
+  // classes 1-4 through the table
+  for (int i = 0; i < b5; ++i) {
+    int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
+    if (i == 0) {
+      kind = 1;
+    } else if (i < b4) {
+      const int q = i - 1;
+      k1 = q >> 2;
+      w = q & 3;
+      r1 = kXP2 + w;
+      kind = (w < 2) ? 2 : 3;
+    } else {
+      const int q = i - b4;
+      k1 = pj;
+      k2 = pk;
+      r1 = (q & 2) ? kXM3 : kXP3;
+      r2 = (q & 1) ? kXM3 : kXP3;
+      kind = 4;
+      if (++pc == 4) {
+        pc = 0;
+        if (++pk == d) {
+          ++pj;
+          pk = pj + 1;
+        }
+      }
+    }
+    auto X = [&](int j) -> float {
+      const int row = (j == k1) ? r1 : ((j == k2) ? r2 : kXC);
+      return xt[(row * d + j) * RB + g];
+    };
+    const float v = Family<FAM>::template eval<float>(rp, D, X);
+    if (kind == 4) {
+      S4.add(v);
+    } else if (kind == 1) {
+      S1.add(v);
+      f0 = (double)v;
+    } else {
+      if (kind == 2)
+        S2.add(v);
+      else
+        S3.add(v);
+      const double vd = (double)v;
+      if (w == 0) {
+        q0 = vd;
+      } else if (w == 1) {
+        q1 = vd;
+      } else if (w == 2) {
+        q2 = vd;
+      } else {
+        const double two_f0 = __dmul_rn(2.0, f0);
+        const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
+        const double t2 = __dsub_rn(__dadd_rn(q2, vd), two_f0);
+        const double Dk = fabs(__dsub_rn(t1, __dmul_rn(ratio, t2)));
+        if (Dk > dbest) {
+          dbest = Dk;
+          kbest = k1;
+        }
+      }
+    }
+  }
+  // class 5: Gray-code walk over the 2^D sign patterns in registers
+  float x[D];
+  unsigned tog[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float p5 = xt[(kXP5 * d + k) * RB + g], m5 = xt[(kXM5 * d + k) * RB + g];
+    x[k] = p5;
+    tog[k] = __float_as_uint(p5) ^ __float_as_uint(m5);
+  }
+  auto XR = [&](int j) -> float { return x[j]; };
+  auto flip = [&](int k) { x[k] = __uint_as_float(__float_as_uint(x[k]) ^ tog[k]); };
+  for (unsigned tb = 0; tb < (1u << D); tb += 8u) {
+    if (tb) {
+      const int jb = __ffs(tb) - 1;
+#pragma unroll
+      for (int k = 3; k < D; ++k)
+        if (k == jb) flip(k);
+    }
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(0);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(1);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(0);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(2);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(0);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(1);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(0);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+  }
+  const double s1 = S1.value(), s2 = S2.value(), s3 = S3.value(), s4 = S4.value(),
+               s5 = S5.value();
+  double vol = 1.0;
+  for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, hd[k * RB + g]));
+  const double* w7 = A.R.w7;
+  const double* w5 = A.R.w5;
+  double t7 = __dmul_rn(w7[0], s1);
+  t7 = __dadd_rn(t7, __dmul_rn(w7[1], s2));
+  t7 = __dadd_rn(t7, __dmul_rn(w7[2], s3));
+  t7 = __dadd_rn(t7, __dmul_rn(w7[3], s4));
+  t7 = __dadd_rn(t7, __dmul_rn(w7[4], s5));
+  double t5 = __dmul_rn(w5[0], s1);
+  t5 = __dadd_rn(t5, __dmul_rn(w5[1], s2));
+  t5 = __dadd_rn(t5, __dmul_rn(w5[2], s3));
+  t5 = __dadd_rn(t5, __dmul_rn(w5[3], s4));
+  const double i7 = __dmul_rn(vol, t7);
+  const double i5 = __dmul_rn(vol, t5);
+  const double flat_thr = __dadd_rn(__dmul_rn(1e-14, fabs(f0)), 1e-300);
+  int ax = kbest;
+  if (!(dbest > flat_thr)) {
+    ax = 0;
+    double hb = hd[0 * RB + g];
+    for (int k = 1; k < d; ++k) {
+      const double hk = hd[k * RB + g];
+      if (hk > hb) {
+        hb = hk;
+        ax = k;
+      }
+    }
+  }
+  const double cs = cd[ax * RB + g];
+  const double hh = __dmul_rn(0.5, hd[ax * RB + g]);
+  const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
+  A.i7[r] = i7;
+  A.err[r] = fabs(__dsub_rn(i7, i5));
+  if (A.volfrac) A.volfrac[r] = __ddiv_rn(vol, A.R.vol_omega);
+  A.axis[r] = (uint8_t)(ax | (bad ? 0x80 : 0));
+}
+
+template <int FAM, int D>
+cudaError_t launch_mixed_reg_d(const RuleArgs& A, cudaStream_t s) {
+  const size_t smem = rule_smem_bytes(D, 1, (int)sizeof(float));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_rule_mixed_reg<FAM, D>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t blocks = (A.n + kRuleBlock - 1) / kRuleBlock;
+  if (blocks == 0) return cudaSuccess;
+  k_rule_mixed_reg<FAM, D><<<(unsigned)blocks, kRuleBlock, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+// The register-walk variant exists for 3 <= d <= 12; returns
+// cudaErrorNotSupported for other d.
+template <int FAM>
+cudaError_t launch_mixed_reg(const RuleArgs& A, cudaStream_t s) {
+  switch (A.P.d) {
+    case 3: return launch_mixed_reg_d<FAM, 3>(A, s);
+    case 4: return launch_mixed_reg_d<FAM, 4>(A, s);
+    case 5: return launch_mixed_reg_d<FAM, 5>(A, s);
+    case 6: return launch_mixed_reg_d<FAM, 6>(A, s);
+    case 7: return launch_mixed_reg_d<FAM, 7>(A, s);
+    case 8: return launch_mixed_reg_d<FAM, 8>(A, s);
+    case 9: return launch_mixed_reg_d<FAM, 9>(A, s);
+    case 10: return launch_mixed_reg_d<FAM, 10>(A, s);
+    case 11: return launch_mixed_reg_d<FAM, 11>(A, s);
+    case 12: return launch_mixed_reg_d<FAM, 12>(A, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 // Launch the rule kernel of one family for T lanes per region.
 template <int FAM>
 cudaError_t launch_rule_family(int precision, int T, const RuleArgs& A, cudaStream_t s);
@@ -300,6 +537,8 @@ cudaError_t launch_rule_real(int T, const RuleArgs& A, cudaStream_t s) {
   cudaError_t launch_rule_family<FAMV>(int precision, int T, const RuleArgs& A,         \
                                        cudaStream_t s) {                                \
     if (precision == GMQ_FP64) return launch_rule_real<FAMV, double>(T, A, s);         \
+    if (precision == GMQ_MIXED && T == 1 && A.P.d >= 3 && A.P.d <= 12)                 \
+      return launch_mixed_reg<FAMV>(A, s);                                             \
     if (precision == GMQ_MIXED) return launch_rule_real<FAMV, float>(T, A, s);         \
     return cudaErrorInvalidValue;                                                      \
   }

@@ -19,6 +19,7 @@
 #include "gm_adjoint.cuh"
 #include "gm_rule.cuh"
 #include "gmq_common.cuh"
+#include "gm_batch.cuh"
 #include "sweep_kernels.cuh"
 
 using namespace gmq;
@@ -57,6 +58,11 @@ struct gmq_context {
   // working memory of gmq_rule_grad
   char* gscratch = nullptr;
   size_t gscratch_bytes = 0;
+  // batched form: autotuned rule-kernel launch shape per largest dimension
+  int tuned_rb[GMQ_MAX_DIM + 1] = {};
+  int tuned_grid[GMQ_MAX_DIM + 1] = {};
+  gmq_batch_info last_batch = {};
+  cudaStream_t capture_stream = nullptr;  // private stream for graph capture
   // kernel timing (gmq_profile_*)
   bool prof_on = false;
   bool ev_made = false;
@@ -233,7 +239,11 @@ cudaError_t launch_rule(int fam, int precision, int T, const RuleArgs& A, cudaSt
   }
 }
 
+// Name of the last CUDA error a call of this thread turned into a status.
+thread_local const char* g_last_cuda_error = "cudaSuccess";
+
 gmq_status cuda_fail(cudaError_t e) {
+  g_last_cuda_error = cudaGetErrorName(e);
   if (e == cudaErrorMemoryAllocation) return GMQ_ERR_OOM;
   if (e == cudaErrorNotSupported) return GMQ_ERR_INVALID;
   return GMQ_ERR_CUDA;
@@ -366,6 +376,8 @@ const char* gmq_status_string(gmq_status s) {
   return "unknown status";
 }
 
+const char* gmq_last_cuda_error(void) { return g_last_cuda_error; }
+
 gmq_status gmq_create(gmq_context** out, int device, size_t pool_bytes_hint) {
   if (!out) return GMQ_ERR_INVALID;
   *out = nullptr;
@@ -412,6 +424,7 @@ gmq_status gmq_destroy(gmq_context* ctx) {
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->gscratch) cudaFree(ctx->gscratch);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->ev_made)
       for (int k = 0; k < 5; ++k)
         for (int j = 0; j < 2; ++j) cudaEventDestroy(ctx->ev[k][j]);
@@ -895,6 +908,285 @@ gmq_status gmq_partition_copy(gmq_context* ctx, double* d_center, double* d_half
   GMQ_CK(cudaMemcpy2DAsync(d_halfw, dpitch, ctx->part_h, spitch, sizeof(double) * (size_t)m,
                            ctx->part_d, cudaMemcpyDeviceToDevice, ctx->stream));
   GMQ_CK(cudaStreamSynchronize(ctx->stream));
+  return GMQ_OK;
+}
+
+gmq_status gmq_last_batch_info(gmq_context* ctx, gmq_batch_info* info) {
+  if (!ctx || !info) return GMQ_ERR_INVALID;
+  *info = ctx->last_batch;
+  return GMQ_OK;
+}
+
+gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_problem* probs,
+                               const double* rel_tols, const gmq_options* opt,
+                               int64_t pool_regions, gmq_result* results) {
+  if (!ctx || !opt || !results || !probs || count < 1 || count > (1 << 20) ||
+      pool_regions < 0 || pool_regions > ((int64_t)1 << 31))
+    return GMQ_ERR_INVALID;
+  const int64_t cap = opt->max_regions;  // per problem
+  if (!(opt->abs_tol >= 0.0) || cap < 1 || cap > kMaxRegions || opt->init_splits < 0 ||
+      opt->max_iters < 0 || (opt->flags & ~GMQ_BATCH_HOST_LOOP) || opt->precision != GMQ_FP64 ||
+      (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL))
+    return GMQ_ERR_INVALID;
+  std::memset(results, 0, sizeof(gmq_result) * (size_t)count);
+  const int max_iters = opt->max_iters > 0 ? opt->max_iters : 1000;
+  // per-problem descriptors and the initial segments
+  std::vector<BatchItem> items((size_t)count);
+  int dmax = 1;
+  int64_t total = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    const gmq_problem* p = &probs[i];
+    if (validate_problem(p) != GMQ_OK) return GMQ_ERR_INVALID;
+    const double tol = rel_tols ? rel_tols[i] : opt->rel_tol;
+    if (!(tol >= 0.0)) return GMQ_ERR_INVALID;
+    const int d = p->dim;
+    dmax = std::max(dmax, d);
+    BatchItem& it = items[(size_t)i];
+    std::memset(&it, 0, sizeof(it));
+    it.P = fam_params(p);
+    const RuleConst R = rule_const(d, p->lo, p->hi);
+    for (int c = 0; c < 5; ++c) {
+      it.w7[c] = R.w7[c];
+      it.w5[c] = R.w5[c];
+    }
+    it.vol_omega = R.vol_omega;
+    it.rel_tol = tol;
+    it.abs_tol = opt->abs_tol;
+    it.s = opt->init_splits > 0 ? opt->init_splits : auto_splits(d, cap);
+    it.nodes = (int32_t)R.nodes;
+    it.cap = cap;
+    int64_t n = 1;
+    for (int k = 0; k < d; ++k) {
+      const double lo = p->lo ? p->lo[k] : 0.0, hi = p->hi ? p->hi[k] : 1.0;
+      it.lo[k] = lo;
+      it.h0[k] = (hi - lo) / (2.0 * (double)it.s);
+      n *= it.s;
+      if (n > cap) return GMQ_ERR_INVALID;
+    }
+    it.off = total;
+    it.n = n;
+    it.n0 = n;
+    total += n;
+  }
+  // shared pool: the caller's size, or by default the per-problem cap
+  // (at least four times the initial partitions)
+  const int64_t pool = pool_regions > 0 ? pool_regions : std::max<int64_t>(cap, 4 * total);
+  // admission: problems start in index order while their initial
+  // partitions fill at most half the pool; the rest wait (deferred, holding
+  // no regions) and start when the loop finds room
+  total = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    BatchItem& it = items[(size_t)i];
+    // a waiting problem must be able to start in an empty pool
+    if (it.n0 > pool / 2) return GMQ_ERR_INVALID;
+    if (i == 0 || total + it.n0 <= pool / 2) {
+      it.off = total;
+      it.n = it.n0;
+      total += it.n0;
+    } else {
+      it.off = 0;
+      it.n = 0;
+      it.deferred = 1;
+    }
+  }
+
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  // pool: two lists of dmax rows with owner ids, rule outputs, flags,
+  // descriptors, loop state
+  const int64_t ld = (pool + 31) / 32 * 32;
+  const size_t list = align256(sizeof(double) * (size_t)dmax * (size_t)ld);
+  const size_t vec = align256(sizeof(double) * (size_t)ld);
+  const size_t ids = align256(sizeof(int32_t) * (size_t)ld);
+  const size_t bytes = align256((size_t)ld);
+  size_t p = 0;
+  const size_t o_c0 = p; p += list;
+  const size_t o_h0 = p; p += list;
+  const size_t o_c1 = p; p += list;
+  const size_t o_h1 = p; p += list;
+  const size_t o_r0 = p; p += ids;
+  const size_t o_r1 = p; p += ids;
+  const size_t o_i7 = p; p += vec;
+  const size_t o_err = p; p += vec;
+  const size_t o_vf = p; p += vec;
+  const size_t o_ax = p; p += bytes;
+  const size_t o_fl = p; p += bytes;
+  const size_t o_it = p; p += align256(sizeof(BatchItem) * (size_t)count);
+  const size_t o_bs = p; p += align256(sizeof(BatchState));
+  char* base = nullptr;
+  gmq_status ps = ensure_pool(ctx, p, &base);
+  if (ps != GMQ_OK) return ps;
+  ctx->part_count = -1;  // the pool no longer holds a kept partition
+
+  BatchArgs B;
+  std::memset(&B, 0, sizeof(B));
+  B.items = (BatchItem*)(base + o_it);
+  B.count = count;
+  B.bs = (BatchState*)(base + o_bs);
+  B.c[0] = (double*)(base + o_c0);
+  B.h[0] = (double*)(base + o_h0);
+  B.c[1] = (double*)(base + o_c1);
+  B.h[1] = (double*)(base + o_h1);
+  B.rid[0] = (int32_t*)(base + o_r0);
+  B.rid[1] = (int32_t*)(base + o_r1);
+  B.ld = ld;
+  B.pool_cap = pool;
+  B.i7 = (double*)(base + o_i7);
+  B.err = (double*)(base + o_err);
+  B.vf = (double*)(base + o_vf);
+  B.axis = (uint8_t*)(base + o_ax);
+  B.flags = (uint8_t*)(base + o_fl);
+  B.dmax = dmax;
+  B.classifier = opt->classifier;
+  B.guard = kGuardFp64;
+  const RuleConst R0 = rule_const(1, nullptr, nullptr);
+  B.lam2 = R0.lam2;
+  B.lam3 = R0.lam3;
+  B.lam5 = R0.lam5;
+  B.ratio = R0.ratio;
+  BatchState bs0;
+  std::memset(&bs0, 0, sizeof(bs0));
+  bs0.n_total = total;
+  bs0.active = count;
+  bs0.max_iters = max_iters;
+  // pauses (pool full) add sweeps; the device loop is bounded all the same
+  bs0.max_sweeps = 4 * max_iters;
+  cudaStream_t strm = ctx->stream;
+  GMQ_CK(cudaMemcpyAsync(B.items, items.data(), sizeof(BatchItem) * (size_t)count,
+                         cudaMemcpyHostToDevice, strm));
+  GMQ_CK(cudaMemcpyAsync(B.bs, &bs0, sizeof(BatchState), cudaMemcpyHostToDevice, strm));
+  GMQ_CK(batch_launch_partition(B, strm));
+  ctx->launches += 1;
+
+  // autotuner: time the rule kernel's candidate launch shapes on the
+  // initial list once per largest dimension (the launches only write the
+  // rule outputs, which the first sweep overwrites)
+  gmq_batch_info info;
+  std::memset(&info, 0, sizeof(info));
+  for (int c = 0; c < 4; ++c) info.tune_ms[c] = -1.0;
+  if (!ctx->tuned_rb[dmax]) {
+    const int rbs[2] = {64, 128};
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    GMQ_CK(cudaEventCreate(&e0));
+    GMQ_CK(cudaEventCreate(&e1));
+    for (int c = 0; c < 2; ++c) {
+      const int grid = ctx->sm_count * batch_rule_max_blocks(dmax, rbs[c]);
+      GMQ_CK(batch_launch_rule(B, rbs[c], grid, strm));  // warm-up
+      GMQ_CK(cudaEventRecord(e0, strm));
+      GMQ_CK(batch_launch_rule(B, rbs[c], grid, strm));
+      GMQ_CK(cudaEventRecord(e1, strm));
+      GMQ_CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GMQ_CK(cudaEventElapsedTime(&ms, e0, e1));
+      info.tune_ms[c] = ms;
+      ctx->launches += 2;
+      if (ms < best) {
+        best = ms;
+        ctx->tuned_rb[dmax] = rbs[c];
+        ctx->tuned_grid[dmax] = grid;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    info.autotuned = 1;
+  }
+  const int rb = ctx->tuned_rb[dmax], grid = ctx->tuned_grid[dmax];
+  batch_rule_max_blocks(dmax, rb);  // sets the kernel's shared-memory limit before any capture
+  info.rule_block = rb;
+  info.rule_grid = grid;
+
+  BatchState hs;
+  if (!(opt->flags & GMQ_BATCH_HOST_LOOP)) {
+    // one graph: a while node whose body is one sweep; the last kernel of
+    // the body sets the condition (false once every problem has stopped or
+    // max_iters sweeps ran)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    cudaGraphConditionalHandle handle = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1,
+                                                                cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp);
+    if (e == cudaSuccess) {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      B.cond = handle;
+      B.use_cond = 1;
+      // capture on the context's private stream: the caller's stream may be
+      // the legacy default stream, which cannot be captured; capturing runs
+      // nothing, the graph is launched on the caller's stream below
+      if (!ctx->capture_stream)
+        e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(ctx->capture_stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e1 = batch_launch_rule(B, rb, grid, ctx->capture_stream);
+        cudaError_t e2 = batch_launch_rest(B, ctx->capture_stream);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(ctx->capture_stream, &captured);
+        if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, strm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ctx->launches += 1;
+    info.used_graph = 1;
+  } else {
+    B.use_cond = 0;
+    for (;;) {
+      for (int k = 0; k < 8; ++k) {
+        GMQ_CK(batch_launch_rule(B, rb, grid, strm));
+        GMQ_CK(batch_launch_rest(B, strm));
+        ctx->launches += 6;
+      }
+      GMQ_CK(cudaMemcpyAsync(ctx->h_status, B.bs, sizeof(BatchState), cudaMemcpyDeviceToHost,
+                             strm));
+      GMQ_CK(cudaStreamSynchronize(strm));
+      std::memcpy(&hs, ctx->h_status, sizeof(BatchState));
+      if (hs.active == 0 || hs.sweep >= hs.max_sweeps) break;
+    }
+  }
+  GMQ_CK(cudaMemcpyAsync(ctx->h_status, B.bs, sizeof(BatchState), cudaMemcpyDeviceToHost, strm));
+  GMQ_CK(cudaMemcpyAsync(items.data(), B.items, sizeof(BatchItem) * (size_t)count,
+                         cudaMemcpyDeviceToHost, strm));
+  GMQ_CK(cudaStreamSynchronize(strm));
+  std::memcpy(&hs, ctx->h_status, sizeof(BatchState));
+  info.sweeps = hs.sweep;
+  info.pauses = hs.pauses;
+  info.evictions = hs.evictions;
+  ctx->last_batch = info;
+  for (int32_t i = 0; i < count; ++i) {
+    const BatchItem& it = items[(size_t)i];
+    gmq_result& r = results[i];
+    r.integral = it.I;
+    r.error = it.E;
+    r.regions_evaluated = it.regions;
+    r.function_evals = it.regions * (int64_t)it.nodes;
+    r.final_active = it.n;
+    r.iterations = it.iters;
+    if (it.flags & kNonfinite)
+      r.status = GMQ_ERR_NONFINITE;
+    else if (it.flags & kConverged)
+      r.status = GMQ_OK;
+    else if (it.flags & kLastSweep)
+      r.status = GMQ_MAX_ITERS;
+    else if (it.flags & kAllRetired)
+      r.status = GMQ_ROUNDOFF_LIMIT;
+    else if (it.flags & kCapExceeded)
+      r.status = GMQ_CAP_REACHED;
+    else
+      r.status = GMQ_MAX_ITERS;
+  }
   return GMQ_OK;
 }
 

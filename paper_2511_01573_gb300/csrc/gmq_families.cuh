@@ -42,9 +42,10 @@ struct Family;
 // cos(2 pi u_1 + sum a_j x_j)
 template <>
 struct Family<GMQ_OSCILLATORY> {
-  template <class Real, class X>
-  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+  template <class Real, class PT, class X>
+  __device__ __forceinline__ static Real eval(const PT& P, int d, X x) {
     Real s = P.c0;
+#pragma unroll
     for (int j = 0; j < d; ++j) s = fma(P.a[j], x(j), s);
     return gcos(s);
   }
@@ -54,9 +55,10 @@ struct Family<GMQ_OSCILLATORY> {
 // product of the denominators (b_j = a_j^-2)
 template <>
 struct Family<GMQ_PRODUCT_PEAK> {
-  template <class Real, class X>
-  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+  template <class Real, class PT, class X>
+  __device__ __forceinline__ static Real eval(const PT& P, int d, X x) {
     Real den = Real(1);
+#pragma unroll
     for (int j = 0; j < d; ++j) {
       Real t = x(j) - P.u[j];
       den *= fma(t, t, P.b[j]);
@@ -68,9 +70,10 @@ struct Family<GMQ_PRODUCT_PEAK> {
 // (1 + sum a_j x_j)^-(d+1)
 template <>
 struct Family<GMQ_CORNER_PEAK> {
-  template <class Real, class X>
-  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+  template <class Real, class PT, class X>
+  __device__ __forceinline__ static Real eval(const PT& P, int d, X x) {
     Real s = Real(1);
+#pragma unroll
     for (int j = 0; j < d; ++j) s = fma(P.a[j], x(j), s);
     return Real(1) / ipow(s, d + 1);
   }
@@ -79,9 +82,10 @@ struct Family<GMQ_CORNER_PEAK> {
 // exp(-sum a_j^2 (x_j - u_j)^2)  (b_j = a_j^2)
 template <>
 struct Family<GMQ_GAUSSIAN> {
-  template <class Real, class X>
-  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+  template <class Real, class PT, class X>
+  __device__ __forceinline__ static Real eval(const PT& P, int d, X x) {
     Real s = Real(0);
+#pragma unroll
     for (int j = 0; j < d; ++j) {
       Real t = x(j) - P.u[j];
       s = fma(P.b[j], t * t, s);
@@ -93,9 +97,10 @@ struct Family<GMQ_GAUSSIAN> {
 // exp(-sum a_j |x_j - u_j|)
 template <>
 struct Family<GMQ_C0> {
-  template <class Real, class X>
-  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+  template <class Real, class PT, class X>
+  __device__ __forceinline__ static Real eval(const PT& P, int d, X x) {
     Real s = Real(0);
+#pragma unroll
     for (int j = 0; j < d; ++j) s = fma(P.a[j], fabs(x(j) - P.u[j]), s);
     return gexp(-s);
   }
@@ -104,10 +109,11 @@ struct Family<GMQ_C0> {
 // 0 if any x_j > u_j, else exp(sum a_j x_j)
 template <>
 struct Family<GMQ_DISCONTINUOUS> {
-  template <class Real, class X>
-  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+  template <class Real, class PT, class X>
+  __device__ __forceinline__ static Real eval(const PT& P, int d, X x) {
     Real s = Real(0);
     bool zero = false;
+#pragma unroll
     for (int j = 0; j < d; ++j) {
       Real xj = x(j);
       zero = zero || (xj > P.u[j]);
@@ -120,9 +126,10 @@ struct Family<GMQ_DISCONTINUOUS> {
 // (sum x_j^2)^11
 template <>
 struct Family<GMQ_POLY_SUMSQ11> {
-  template <class Real, class X>
-  __device__ __forceinline__ static Real eval(const SmemParams<Real>& P, int d, X x) {
+  template <class Real, class PT, class X>
+  __device__ __forceinline__ static Real eval(const PT& P, int d, X x) {
     Real s = Real(0);
+#pragma unroll
     for (int j = 0; j < d; ++j) {
       Real xj = x(j);
       s = fma(xj, xj, s);

@@ -62,9 +62,17 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_default_options", "gmq_integrate", "gmq_last_trace", "gmq_seed_genz",
            "gmq_status_string", "gmq_launch_count", "gmq_eval_rule", "gmq_classify_split",
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
-           "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad")
+           "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad",
+           "gmq_integrate_batch", "gmq_last_batch_info")
 
 KEEP_PARTITION = 1
+BATCH_HOST_LOOP = 2
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("rule_block", C.c_int32), ("rule_grid", C.c_int32), ("sweeps", C.c_int32),
+                ("used_graph", C.c_int32), ("autotuned", C.c_int32), ("pauses", C.c_int32),
+                ("evictions", C.c_int32), ("reserved", C.c_int32), ("tune_ms", C.c_double * 4)]
 
 ERR_TOO_LARGE = -6
 NOALLOC_MAX_N = 1 << 23
@@ -73,7 +81,10 @@ NOALLOC_MAX_N = 1 << 23
 class GmqError(RuntimeError):
     def __init__(self, call, code):
         self.code = code
-        super().__init__(f"{call} failed: {status_string(code)} ({code})")
+        extra = ""
+        if code in (ERR_CUDA, ERR_OOM):
+            extra = f" [{lib().gmq_last_cuda_error().decode()}]"
+        super().__init__(f"{call} failed: {status_string(code)} ({code}){extra}")
 
 
 _lib = None
@@ -111,6 +122,9 @@ def lib():
         "gmq_tree_sum_noalloc": [i32, i64, vp, vp, vp],
         "gmq_partition_copy": [vp, vp, vp, i64, i64, C.POINTER(i64)],
         "gmq_rule_grad": [vp, C.POINTER(Problem), i64, vp, vp, i64, C.POINTER(dbl), _dp],
+        "gmq_integrate_batch": [vp, i32, C.POINTER(Problem), _dp, C.POINTER(Options), i64,
+                                C.POINTER(Result)],
+        "gmq_last_batch_info": [vp, C.POINTER(BatchInfo)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -118,6 +132,8 @@ def lib():
         f.restype = C.c_int
     L.gmq_status_string.argtypes = [C.c_int]
     L.gmq_status_string.restype = C.c_char_p
+    L.gmq_last_cuda_error.argtypes = []
+    L.gmq_last_cuda_error.restype = C.c_char_p
     _lib = L
     return L
 
@@ -278,6 +294,36 @@ class Context:
             _check("gmq_integrate", code, ok=(OK, CAP_REACHED, MAX_ITERS, ROUNDOFF_LIMIT))
         return IntegrateResult(r.integral, r.error, r.regions_evaluated, r.function_evals,
                                r.final_active, r.iterations, code)
+
+    def integrate_batch(self, problems, rel_tols=None, max_regions=1 << 24, abs_tol=1e-16,
+                        init_splits=0, max_iters=0, classifier=VOLUME_SHARE, host_loop=False,
+                        pool_regions=0):
+        """Integrate many problems in one device-resident loop.  problems:
+        objects with family, dim, a, u (and optional lo, hi, rel_tol).
+        max_regions is each problem's cap, pool_regions the shared pool (0:
+        the library's default).  Returns one IntegrateResult per problem."""
+        hs = [_ProblemHandle(p.family, p.a, p.u, getattr(p, "lo", None), getattr(p, "hi", None),
+                             p.dim) for p in problems]
+        arr = (Problem * len(hs))(*[h.s for h in hs])
+        if rel_tols is None:
+            rel_tols = [p.rel_tol for p in problems]
+        tols = _f64(rel_tols, len(hs))
+        o = Options(0.0, abs_tol, max_regions, init_splits, max_iters, FP64, classifier, 0,
+                    BATCH_HOST_LOOP if host_loop else 0)
+        res = (Result * len(hs))()
+        _check("gmq_integrate_batch", lib().gmq_integrate_batch(self.h, len(hs), arr, _ptr(tols),
+                                                                C.byref(o), pool_regions, res))
+        return [IntegrateResult(r.integral, r.error, r.regions_evaluated, r.function_evals,
+                                r.final_active, r.iterations, r.status) for r in res]
+
+    def last_batch_info(self):
+        info = BatchInfo()
+        _check("gmq_last_batch_info", lib().gmq_last_batch_info(self.h, C.byref(info)))
+        return {"rule_block": info.rule_block, "rule_grid": info.rule_grid,
+                "sweeps": info.sweeps, "used_graph": bool(info.used_graph),
+                "autotuned": bool(info.autotuned), "pauses": int(info.pauses),
+                "evictions": int(info.evictions),
+                "tune_ms": list(info.tune_ms)}
 
     def partition_copy(self):
         """The final partition of the last integrate(keep_partition=True) call

@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol(built):
     L = built.lib()
     for n in _declared():
         assert hasattr(L, n), n
-    assert set(_declared()) == set(built.EXPORTS) | {"gmq_status_string"}
+    assert set(_declared()) == set(built.EXPORTS) | {"gmq_status_string", "gmq_last_cuda_error"}
 
 
 def test_seed_genz_matches_input_module(built):

@@ -260,3 +260,19 @@ def test_e2e_caller_pool(gpu_ctx):
             gpu_ctx.integrate(G.GAUSSIAN, a, u, 1e-7, max_regions=1 << 19)
     finally:
         gpu_ctx.set_pool(None)
+
+
+def test_e2e_domain_classifier_and_dimension_edges(oracle, gpu_ctx):
+    # a non-unit box, the local-relative classifier, d = 1 and d = 16
+    a, u = G.seed_genz(9, G.GAUSSIAN, 3, 3.5)
+    lo, hi = [-1.0, 0.25, 0.0], [2.0, 1.5, 0.5]
+    _e2e(oracle, gpu_ctx, G.GAUSSIAN, a, u * 2 - 0.5, 1e-7, lo=lo, hi=hi)
+    a, u = G.seed_genz(4, G.C0, 4, 2.0)
+    _e2e(oracle, gpu_ctx, G.C0, a, u, 1e-5, classifier=1)
+    _e2e(oracle, gpu_ctx, G.PRODUCT_PEAK, [30.0], [0.3], 1e-10)
+    a, u = G.seed_genz(2, G.CORNER_PEAK, 16, 1.85)
+    o, g = _e2e(oracle, gpu_ctx, G.CORNER_PEAK, a, u, 1e-3, cap=1 << 16, init_splits=1)
+    assert g.regions_evaluated >= 1
+    # absolute tolerance only
+    a, u = G.seed_genz(6, G.OSCILLATORY, 3, 6.0)
+    _e2e(oracle, gpu_ctx, G.OSCILLATORY, a, u, 0.0, abs_tol=1e-9)
