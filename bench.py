@@ -8,7 +8,7 @@ evaluated per second over the whole step (device time, CUDA events on the
 library's stream).  e2e = the same through the public call, host wall clock,
 with the parameter upload and the per-sweep status reads inside.
 
---impl reference times the CPU oracle (FP64, one thread) on a bounded sample
+--impl reference times the CPU oracle (FP64, one process per host core) on a bounded sample
 of the same workload.  Under torchrun every rank runs the same workload as
 an independent replica (the method's sweep has no data-path exchange on one
 GPU); value is the sum over ranks divided by the slowest rank's time.
@@ -45,10 +45,13 @@ def parse():
                          "kernel 3 times per family on 2^20 random d=8 regions and exits")
     ap.add_argument("--probe-split", action="store_true",
                     help="profiling probe: classify + split on 2^22 random d=8 regions")
+    ap.add_argument("--kernel-sweep", action="store_true",
+                    help="isolated rule / classify / split rates against the region count")
     ap.add_argument("--all-configs", action="store_true",
                     help="report the other workloads (d=3, d=12 mixed, batch, gradients)")
     ap.add_argument("--seeds-d12", type=int, default=3)
     ap.add_argument("--grad-sets", type=int, default=32)
+    ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--lanes", type=int, default=1)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -192,61 +195,112 @@ def dist_setup():
     return ws, rank, local
 
 
+def _oracle_one(job):
+    """One integration by the CPU oracle in a host process, unless the
+    sample's wall-clock deadline has passed.  Returns (regions, done)."""
+    p, deadline = job
+    if time.time() > deadline:
+        return 0, 0
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    r = O.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=ORACLE_CAP)
+    return r.regions_evaluated, 1
+
+
+def _oracle_load(_):
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    O.lib()
+    return 0
+
+
+ORACLE_CAP = 1 << 16  # bounds one integration to about a second of oracle time
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The unchanged single-threaded oracle, one process per host core
+    (spawned, so it is safe after CUDA is initialised).  A sample hands the
+    problems out in tolerance order to whichever process is free; problems
+    not started by the deadline are skipped."""
+
+    def __init__(self, procs):
+        import multiprocessing as mp
+        from oracle import oracle as O
+        O.build()  # once, before the workers load it
+        self.procs = procs
+        self.pool = None
+        if procs > 1:
+            self.pool = mp.get_context("spawn").Pool(procs)
+            self.pool.map(_oracle_load, range(procs), chunksize=1)
+
+    def run(self, probs, seconds):
+        t0 = time.perf_counter()
+        jobs = [(p, time.time() + seconds) for p in probs]
+        if self.pool:
+            outs = self.pool.map(_oracle_one, jobs, chunksize=1)
+        else:
+            outs = [_oracle_one(j) for j in jobs]
+        wall = time.perf_counter() - t0
+        return sum(o[0] for o in outs) / wall, sum(o[1] for o in outs), wall
+
+    def close(self):
+        if self.pool:
+            self.pool.close()
+            self.pool.join()
+
+
 def run_reference(args):
-    """CPU oracle on a bounded sample of the workload (one thread)."""
+    """CPU oracle on a bounded sample of the workload, all host cores."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return
-    from oracle import oracle as O
-    O.build()
     probs = workload(args)
+    cores = host_cores()
+    pool = OraclePool(cores)
     per_step = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
     vals = []
     sample_desc = ""
     for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        regions = 0
-        done = 0
-        for p in probs:
-            # bounded: the loosest tolerances first, stop when the step's
-            # time budget is spent
-            if time.perf_counter() - t0 > per_step:
-                break
-            r = O.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=min(CAP, 1 << 20))
-            regions += r.regions_evaluated
-            done += 1
-        dt = time.perf_counter() - t0
+        v, done, wall = pool.run(probs, per_step)
         if step >= args.warmup:
-            vals.append(regions / dt)
-            sample_desc = f"first {done} of {len(probs)} integrations in tolerance order, pool 2^20"
+            vals.append(v)
+            sample_desc = (f"{done} of {len(probs)} integrations in tolerance order, "
+                           f"{cores} processes, problems started within {per_step:.1f} s "
+                           f"({wall:.1f} s), pool 2^16")
+    pool.close()
     v = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": "genz_d8_4families_seeds1-10_tol1e-3..1e-8_cap2^24"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample_desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(args, seconds):
-    from oracle import oracle as O
-    O.build()
+    """The oracle on one core and on all host cores, each on a bounded
+    sample of the workload (the loosest tolerances first)."""
     probs = workload(args)
-    t0 = time.perf_counter()
-    regions = 0
-    done = 0
-    for p in probs:
-        if time.perf_counter() - t0 > seconds:
-            break
-        r = O.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=min(CAP, 1 << 20))
-        regions += r.regions_evaluated
-        done += 1
-    dt = time.perf_counter() - t0
-    return {"value": regions / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of {len(probs)} integrations in tolerance order "
-                      f"({dt:.1f} s, pool 2^20)"}
+    one = OraclePool(1)
+    v1, done1, wall1 = one.run(probs, seconds)
+    cores = host_cores()
+    pool = OraclePool(cores)
+    v, done, wall = pool.run(probs, seconds)
+    pool.close()
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {len(probs)} integrations in tolerance order, one process "
+                      f"per core, started within {seconds:.0f} s ({wall:.1f} s), pool 2^16",
+            "single_core": {"value": v1, "cores": 1,
+                            "sample": f"first {done1} integrations ({wall1:.1f} s)"}}
 
 
 def probe_rule(args):
@@ -303,6 +357,72 @@ def probe_split(args):
         alg = 26.0 * n if k == "classify" else (1.0 * n + ns * (16 * d + 32 * d))
         print(f"{k}: {ms:.3f} ms/launch, n={n}, n_split={ns}, algorithmic {alg / 1e6:.1f} MB, "
               f"{alg / ms / 1e6:.1f} GB/s", flush=True)
+    ctx.close()
+
+
+def kernel_sweep(args):
+    """Isolated kernel rates against the region count: the rule kernel over
+    n = 2^16 .. 2^24 random sub-boxes of [0,1]^d for d = 3, 8, 12 (Gaussian
+    family, FP64 and mixed, lanes per region chosen by the library; sizes
+    whose launch would take more than about a second are skipped), and
+    classify + split over n = 2^20 .. 2^24 at d = 8 with about half the
+    regions split.  Event-timed, three launches each after one warm-up.
+    Prints one JSON object."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    ctx = gmq.Context(0)
+    ctx.profile(True)
+    g = torch.Generator(device="cuda").manual_seed(3)
+
+    def boxes(d, n):
+        lo = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.9
+        w = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.05 + 1e-3
+        return (lo + 0.5 * w).contiguous(), (0.5 * w).contiguous()
+
+    rows = []
+    for d in (3, 8, 12):
+        a, u = G.seed_genz(1, G.GAUSSIAN, d, 3.5)
+        for prec in (gmq.FP64, gmq.MIXED):
+            rate = None
+            for lg in range(16, 25, 2):
+                n = 1 << lg
+                if rate is not None and n / rate > 1.0:
+                    rows.append({"kernel": "rule", "d": d, "precision": prec, "n": n,
+                                 "skipped": "launch over 1 s"})
+                    continue
+                c, h = boxes(d, n)
+                ctx.eval_rule(G.GAUSSIAN, a, u, c, h, precision=prec)
+                ctx.profile_reset()
+                for _ in range(3):
+                    ctx.eval_rule(G.GAUSSIAN, a, u, c, h, precision=prec)
+                p = ctx.profile_read()["rule"]
+                ms = p["ms"] / p["launches"]
+                rate = n / ms * 1e3
+                rows.append({"kernel": "rule", "d": d, "precision": prec, "n": n,
+                             "ms": ms, "regions_per_s": rate,
+                             "node_evals_per_s": rate * ((1 << d) + 2 * d * d + 2 * d + 1)})
+                del c, h
+    d = 8
+    a, u = G.seed_genz(1, G.GAUSSIAN, d, 3.5)
+    for lg in range(20, 25, 2):
+        n = 1 << lg
+        c, h = boxes(d, n)
+        i7, err, vf, ax = ctx.eval_rule(G.GAUSSIAN, a, u, c, h, precision=gmq.MIXED)
+        budget = float(torch.median(err / vf).item())
+        ctx.classify_split(c, h, i7, err, vf, ax, budget)
+        ctx.profile_reset()
+        for _ in range(3):
+            out = ctx.classify_split(c, h, i7, err, vf, ax, budget)
+        p = ctx.profile_read()
+        ns = out["n_split"]
+        for k in ("classify", "split"):
+            ms = p[k]["ms"] / p[k]["launches"]
+            alg = 26.0 * n if k == "classify" else (1.0 * n + ns * (16 * d + 32 * d))
+            rows.append({"kernel": k, "d": d, "n": n, "n_split": ns, "ms": ms,
+                         "algorithmic_MB": alg / 1e6, "GB_per_s": alg / ms / 1e6})
+        del c, h, i7, err, vf, ax, out
+    print(json.dumps({"kernel_sweep": rows}), flush=True)
     ctx.close()
 
 
@@ -364,23 +484,21 @@ def all_configs(args):
                              / abs(r64.integral)})
     rep["d12_fp64_vs_mixed"] = rows
     # 4096 integrals in one batch against one-by-one calls on a sample
-    probs = G.batched_problems(count=4096)
+    # the first args.batch_count of the 4096 problems, batched and one by one
+    probs = G.batched_problems(count=4096)[: args.batch_count]
     bcap = 1 << 22  # per problem
     res, tb = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27))
     info = ctx.last_batch_info()
-    sample = probs[::64]
     seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
-                                           lanes=1) for q in sample])
-    same = sum(1 for q, sr in zip(range(0, 4096, 64), seq)
-               if sr.integral == res[q].integral and sr.regions_evaluated == res[q].regions_evaluated)
+                                           lanes=1) for q in probs])
+    same = sum(1 for sr, br in zip(seq, res)
+               if sr.integral == br.integral and sr.regions_evaluated == br.regions_evaluated)
     st = {}
     for x in res:
         st[str(x.status)] = st.get(str(x.status), 0) + 1
-    rep["batch_4096"] = {"s": tb, "regions": sum(x.regions_evaluated for x in res),
-                         "statuses": st, "info": info, "sample_sequential_s": ts,
-                         "sample_size": len(sample),
-                         "sequential_estimate_s": ts * len(probs) / len(sample),
-                         "sample_identical_to_single_runs": same}
+    rep["batch"] = {"problems": len(probs), "batched_s": tb, "sequential_s": ts,
+                    "speedup": ts / tb, "regions": sum(x.regions_evaluated for x in res),
+                    "statuses": st, "info": info, "identical_to_single_runs": same}
     # gradients of the d = 6 Gaussian over frozen partitions
     sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
     errs, tf, tg = [], 0.0, 0.0
@@ -408,6 +526,8 @@ def main():
         return probe_rule(args)
     if args.probe_split:
         return probe_split(args)
+    if args.kernel_sweep:
+        return kernel_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch
