@@ -101,7 +101,10 @@ typedef struct gmq_options {
   int32_t precision;   /* gmq_precision                                     */
   int32_t classifier;  /* gmq_classifier                                    */
   int32_t lanes;       /* threads per region in the rule kernel: 0 = chosen
-                          per sweep by the library, else 1, 4 or 32          */
+                          per sweep by the library, else 1, 4 or 32.  FP64
+                          results do not depend on it (every class sum is
+                          one fixed tree); mixed-precision results do, at
+                          the level of FP32 rounding                        */
   int32_t flags;       /* 0, or GMQ_KEEP_PARTITION                           */
 } gmq_options;
 
@@ -191,21 +194,26 @@ gmq_status gmq_partition_copy(gmq_context *ctx, double *d_center,
 
 /* How the last gmq_integrate_batch call ran. */
 typedef struct gmq_batch_info {
-  int32_t rule_block;   /* threads per block of the rule kernel (autotuned)  */
+  int32_t rule_block;   /* threads per block of the rule kernel             */
   int32_t rule_grid;    /* blocks of its persistent grid                    */
   int32_t sweeps;       /* sweeps of the device loop                        */
   int32_t used_graph;   /* 1: ran as one CUDA graph with a while node       */
-  int32_t autotuned;    /* 1: this call timed the candidate launch shapes   */
+  int32_t autotuned;    /* 1: this call timed the candidate mappings        */
   int32_t pauses;       /* problem-sweeps deferred because the pool was full */
   int32_t evictions;    /* problems evicted and restarted to make room      */
+  int32_t forced_lanes; /* opt->lanes when nonzero, else 0                  */
+  int64_t lanes_t1;     /* lists of >= lanes_t1 regions: 1 lane per region  */
+  int64_t lanes_t4;     /* >= lanes_t4: 4 lanes; shorter lists: 32 (a warp)  */
+  int32_t lane_sweeps[3]; /* sweeps run with 1, 4 and 32 lanes per region   */
   int32_t reserved;
-  double tune_ms[4];    /* rule-kernel time of each candidate (-1 if unused) */
+  int64_t tune_n[5];    /* list lengths the autotuner timed (0 if unused)   */
+  double tune_ms[5][3]; /* rule-kernel time per length and mapping 1/4/32   */
 } gmq_batch_info;
 
 /* Many independent integrals in one device-resident loop (no counterpart in
  * the paper, which integrates one problem at a time).  Every problem runs
  * the paper's loop (Sec. 3) with the same decisions, sums and child order
- * as gmq_integrate gives it alone with one thread per region; all of them
+ * as gmq_integrate gives it alone (with any lanes setting); all of them
  * advance one sweep per iteration, their active regions sharing one region
  * pool of pool_regions regions (0: max(opt->max_regions, 4 x the initial
  * partitions)); opt->max_regions is each problem's own cap.  probs[i] and
@@ -220,10 +228,12 @@ typedef struct gmq_batch_info {
  * that cannot grow even alone stops with GMQ_CAP_REACHED.  The device loop
  * is bounded by 4 x max_iters sweeps.  Device memory: about
  * pool_regions x (32 dmax + 30) bytes, dmax the largest dimension.  FP64 only
- * (opt->precision must be GMQ_FP64); opt->lanes is ignored: the rule
- * kernel's block size and persistent grid are chosen by timing the
- * candidates on the first call for each largest dimension (cached in the
- * context).  Returns GMQ_OK when the batch ran (see the per-problem
+ * (opt->precision must be GMQ_FP64).  Lanes per region: opt->lanes (1, 4
+ * or 32) for every sweep, or with 0 chosen per sweep from the list length
+ * by thresholds an autotuner sets on the first call for each largest
+ * dimension (it times the three mappings on copies of the initial list at
+ * up to five lengths; cached in the context).  The results do not depend
+ * on the mapping.  Returns GMQ_OK when the batch ran (see the per-problem
  * statuses), or an error. */
 gmq_status gmq_integrate_batch(gmq_context *ctx, int32_t count,
                                const gmq_problem *probs, const double *rel_tols,

@@ -7,8 +7,11 @@
 // Layout: one region pool holds every integral's active regions; integral i
 // owns the contiguous segment [off_i, off_i + n_i) of the current list (SoA,
 // dmax rows, plus an int32 owner id per region).  Per sweep:
-//   k_batch_rule      all regions of all integrals, one thread per region,
-//                     persistent grid; family and dimension per region
+//   k_batch_rule      all regions of all integrals, persistent grid; family
+//                     and dimension per region; 1, 4 or 32 lanes per region,
+//                     chosen per sweep from the list length (the per-region
+//                     work is gm_region64.cuh's, so the choice never changes
+//                     a result)
 //   k_batch_sums      one block per integral: pairwise-tree sums over its
 //                     segment, convergence / sweep-limit test
 //   k_batch_classify  one block per integral: flags, split count, retired
@@ -96,9 +99,22 @@ __global__ void k_batch_partition(const BatchArgs B) {
   }
 }
 
-template <int RB>
-__global__ void __launch_bounds__(RB) k_batch_rule(const BatchArgs B) {
-  extern __shared__ __align__(16) double smem[];
+// Doubles of the rule kernel's per-block coordinate tables for T lanes per
+// region: [kXRows + 1][dmax][128 / T] (coordinate rows and the half-widths)
+// and, for T > 1, the [4 dmax + 1][128 / T] axis-node scratch.
+__host__ __device__ constexpr long long batch_rule_doubles(int dmax, int T) {
+  return (long long)(kXRows + 1) * dmax * (kBatchRuleBlock / T) +
+         (T > 1 ? (long long)(4 * dmax + 1) * (kBatchRuleBlock / T) : 0);
+}
+
+// Pair tables of every dimension 2 .. dmax, one after the other: the table
+// of dimension d starts at entry d (d - 1) (d - 2) / 6.
+__host__ __device__ constexpr int batch_pairs_offset(int d) { return d * (d - 1) * (d - 2) / 6; }
+
+template <int T>
+__device__ __forceinline__ void batch_rule_lanes(const BatchArgs& B, double* smem,
+                                                 const unsigned short* pairs_all) {
+  constexpr int RPB = kBatchRuleBlock / T;  // regions per tile
   const BatchState* bs = B.bs;
   const long long n_total = bs->n_total;
   const int cur = bs->parity;
@@ -107,140 +123,92 @@ __global__ void __launch_bounds__(RB) k_batch_rule(const BatchArgs B) {
   const int32_t* rid = B.rid[cur];
   const int dm = B.dmax;
   const int tid = threadIdx.x;
-  // this thread's column of the coordinate table: rows kXC..kXM5 and h
-  double* col = smem + tid;  // element (row, k) at col[(row * dm + k) * RB]
-  auto T = [&](int row, int k) -> double& { return col[(row * dm + k) * RB]; };
-  for (long long tile = blockIdx.x; tile * RB < n_total; tile += gridDim.x) {
-    const long long r = tile * RB + tid;
-    if (r >= n_total) continue;
+  const int g = tid / T, lane = tid & (T - 1);
+  const unsigned mask = group_mask<T>();
+  double* tabs = smem;                                      // [kXRows + 1][dm][RPB]
+  double* fvs = smem + (long long)(kXRows + 1) * dm * RPB;  // [4 dm + 1][RPB]
+  auto tab = [&](int row, int k) -> double { return tabs[(row * dm + k) * RPB + g]; };
+  for (long long tile = blockIdx.x; tile * RPB < n_total; tile += gridDim.x) {
+    const long long r = tile * RPB + g;
+    if (r >= n_total) break;  // so are the group's later tiles
+    __syncwarp(mask);         // the group is done with the previous region's table
     const BatchItem& it = B.items[rid[r]];
     const int d = it.P.d;
-    const int fam = it.P.family;
-    for (int k = 0; k < d; ++k) {
+    for (int k = lane; k < d; k += T) {
       const double cv = C[(int64_t)k * B.ld + r], hv = H[(int64_t)k * B.ld + r];
-      T(kXC, k) = cv;
-      T(kXP2, k) = fma(B.lam2, hv, cv);
-      T(kXM2, k) = fma(-B.lam2, hv, cv);
-      T(kXP3, k) = fma(B.lam3, hv, cv);
-      T(kXM3, k) = fma(-B.lam3, hv, cv);
-      T(kXP5, k) = fma(B.lam5, hv, cv);
-      T(kXM5, k) = fma(-B.lam5, hv, cv);
-      T(kXRows, k) = hv;
+      double* col = tabs + (long long)k * RPB + g;
+      col[(long long)kXC * dm * RPB] = cv;
+      col[(long long)kXP2 * dm * RPB] = fma(B.lam2, hv, cv);
+      col[(long long)kXM2 * dm * RPB] = fma(-B.lam2, hv, cv);
+      col[(long long)kXP3 * dm * RPB] = fma(B.lam3, hv, cv);
+      col[(long long)kXM3 * dm * RPB] = fma(-B.lam3, hv, cv);
+      col[(long long)kXP5 * dm * RPB] = fma(B.lam5, hv, cv);
+      col[(long long)kXM5 * dm * RPB] = fma(-B.lam5, hv, cv);
+      col[(long long)kXRows * dm * RPB] = hv;
     }
-    const int N = it.nodes;
-    const int b4 = 1 + 4 * d, b5 = b4 + 2 * d * (d - 1);
-    double S1 = 0.0, S2 = 0.0, S3 = 0.0, S4 = 0.0, S5 = 0.0;
-    double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
-    int kbest = 0, pj = 0, pk = 1, pc = 0;
-    for (int i = 0; i < N; ++i) {
-      int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
-      unsigned m = 0u;
-      if (i == 0) {
-        kind = 1;
-      } else if (i < b4) {
-        const int q = i - 1;
-        k1 = q >> 2;
-        w = q & 3;
-        r1 = kXP2 + w;
-        kind = (w < 2) ? 2 : 3;
-      } else if (i < b5) {
-        const int q = i - b4;
-        k1 = pj;
-        k2 = pk;
-        r1 = (q & 2) ? kXM3 : kXP3;
-        r2 = (q & 1) ? kXM3 : kXP3;
-        kind = 4;
-        if (++pc == 4) {
-          pc = 0;
-          if (++pk == d) {
-            ++pj;
-            pk = pj + 1;
-          }
-        }
-      } else {
-        m = (unsigned)(i - b5);
-        kind = 5;
-      }
-      auto X = [&](int j) -> double {
-        int row;
-        if (kind == 5)
-          row = ((m >> j) & 1u) ? kXM5 : kXP5;
-        else
-          row = (j == k1) ? r1 : ((j == k2) ? r2 : kXC);
-        return T(row, j);
-      };
-      double v;
-      switch (fam) {
-        case GMQ_OSCILLATORY: v = Family<GMQ_OSCILLATORY>::template eval<double>(it.P, d, X); break;
-        case GMQ_PRODUCT_PEAK: v = Family<GMQ_PRODUCT_PEAK>::template eval<double>(it.P, d, X); break;
-        case GMQ_CORNER_PEAK: v = Family<GMQ_CORNER_PEAK>::template eval<double>(it.P, d, X); break;
-        case GMQ_GAUSSIAN: v = Family<GMQ_GAUSSIAN>::template eval<double>(it.P, d, X); break;
-        case GMQ_C0: v = Family<GMQ_C0>::template eval<double>(it.P, d, X); break;
-        case GMQ_DISCONTINUOUS: v = Family<GMQ_DISCONTINUOUS>::template eval<double>(it.P, d, X); break;
-        default: v = Family<GMQ_POLY_SUMSQ11>::template eval<double>(it.P, d, X); break;
-      }
-      if (kind == 5) {
-        S5 += v;
-      } else if (kind == 4) {
-        S4 += v;
-      } else if (kind == 1) {
-        S1 += v;
-        f0 = v;
-      } else {
-        if (kind == 2)
-          S2 += v;
-        else
-          S3 += v;
-        if (w == 0) {
-          q0 = v;
-        } else if (w == 1) {
-          q1 = v;
-        } else if (w == 2) {
-          q2 = v;
-        } else {
-          const double two_f0 = __dmul_rn(2.0, f0);
-          const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
-          const double t2 = __dsub_rn(__dadd_rn(q2, v), two_f0);
-          const double D = fabs(__dsub_rn(t1, __dmul_rn(B.ratio, t2)));
-          if (D > dbest) {
-            dbest = D;
-            kbest = k1;
-          }
-        }
-      }
+    __syncwarp(mask);
+    const unsigned short* pairs = pairs_all + batch_pairs_offset(d);
+    RegionSums o;
+    double* fv = fvs + g;
+    switch (it.P.family) {
+      case GMQ_OSCILLATORY:
+        region_sums64<GMQ_OSCILLATORY, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
+        break;
+      case GMQ_PRODUCT_PEAK:
+        region_sums64<GMQ_PRODUCT_PEAK, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
+        break;
+      case GMQ_CORNER_PEAK:
+        region_sums64<GMQ_CORNER_PEAK, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
+        break;
+      case GMQ_GAUSSIAN:
+        region_sums64<GMQ_GAUSSIAN, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
+        break;
+      case GMQ_C0:
+        region_sums64<GMQ_C0, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
+        break;
+      case GMQ_DISCONTINUOUS:
+        region_sums64<GMQ_DISCONTINUOUS, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
+        break;
+      default:
+        region_sums64<GMQ_POLY_SUMSQ11, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
+        break;
     }
-    double vol = 1.0;
-    for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, T(kXRows, k)));
-    double t7 = __dmul_rn(it.w7[0], S1);
-    t7 = __dadd_rn(t7, __dmul_rn(it.w7[1], S2));
-    t7 = __dadd_rn(t7, __dmul_rn(it.w7[2], S3));
-    t7 = __dadd_rn(t7, __dmul_rn(it.w7[3], S4));
-    t7 = __dadd_rn(t7, __dmul_rn(it.w7[4], S5));
-    double t5 = __dmul_rn(it.w5[0], S1);
-    t5 = __dadd_rn(t5, __dmul_rn(it.w5[1], S2));
-    t5 = __dadd_rn(t5, __dmul_rn(it.w5[2], S3));
-    t5 = __dadd_rn(t5, __dmul_rn(it.w5[3], S4));
-    const double i7 = __dmul_rn(vol, t7);
-    const double i5 = __dmul_rn(vol, t5);
-    const double flat_thr = __dadd_rn(__dmul_rn(1e-14, fabs(f0)), 1e-300);
-    int ax = kbest;
-    if (!(dbest > flat_thr)) {
-      ax = 0;
-      double hb = T(kXRows, 0);
-      for (int k = 1; k < d; ++k)
-        if (T(kXRows, k) > hb) {
-          hb = T(kXRows, k);
-          ax = k;
-        }
-    }
-    const double cs = T(kXC, ax);
-    const double hh = __dmul_rn(0.5, T(kXRows, ax));
-    const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
-    B.i7[r] = i7;
-    B.err[r] = fabs(__dsub_rn(i7, i5));
-    B.vf[r] = __ddiv_rn(vol, it.vol_omega);
-    B.axis[r] = (uint8_t)(ax | (bad ? 0x80 : 0));
+    if (lane == 0)
+      region_finish64(
+          o, d, it.w7, it.w5, it.vol_omega, [&](int k) { return tab(kXC, k); },
+          [&](int k) { return tab(kXRows, k); }, B.i7 + r, B.err + r, B.vf + r, B.axis + r);
   }
+}
+
+// Rule evaluation of every region of the current list: persistent grid of
+// kBatchRuleBlock-thread blocks, T = bs->lanes lanes per region (set per
+// sweep by k_batch_advance; the results do not depend on it).
+__global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule(const BatchArgs B) {
+  extern __shared__ __align__(16) double smem[];
+  const int dm = B.dmax;
+  long long most = batch_rule_doubles(dm, 1);
+  if (batch_rule_doubles(dm, 4) > most) most = batch_rule_doubles(dm, 4);
+  if (batch_rule_doubles(dm, 32) > most) most = batch_rule_doubles(dm, 32);
+  unsigned short* pairs_all = reinterpret_cast<unsigned short*>(smem + most);
+  for (int e = 2; e <= dm; ++e) {
+    const int np = e * (e - 1) / 2;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+      int j = 0, rem = p;
+      while (rem >= e - 1 - j) {
+        rem -= e - 1 - j;
+        ++j;
+      }
+      pairs_all[batch_pairs_offset(e) + p] = (unsigned short)((j << 8) | (j + 1 + rem));
+    }
+  }
+  __syncthreads();
+  const int lanes = B.bs->lanes;
+  if (lanes == 32)
+    batch_rule_lanes<32>(B, smem, pairs_all);
+  else if (lanes == 4)
+    batch_rule_lanes<4>(B, smem, pairs_all);
+  else
+    batch_rule_lanes<1>(B, smem, pairs_all);
 }
 
 __global__ void __launch_bounds__(kSegBlock) k_batch_sums(const BatchArgs B) {
@@ -614,47 +582,48 @@ __global__ void __launch_bounds__(kSegBlock) k_batch_split(const BatchArgs B) {
   }
 }
 
+// Copies of the initial list's regions [0, n0) into [n0, n), cyclically
+// (the autotuner's larger lists; valid regions of real integrals).
+__global__ void k_batch_tile(const BatchArgs B, long long n0, long long n) {
+  const long long i = n0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long src = i % n0;
+  for (int k = 0; k < B.dmax; ++k) {
+    B.c[0][(int64_t)k * B.ld + i] = B.c[0][(int64_t)k * B.ld + src];
+    B.h[0][(int64_t)k * B.ld + i] = B.h[0][(int64_t)k * B.ld + src];
+  }
+  B.rid[0][i] = B.rid[0][src];
+}
+
 __global__ void k_batch_advance(const BatchArgs B) {
   BatchState* bs = B.bs;
+  const int used = bs->lanes;
+  bs->lane_sweeps[used == 32 ? 2 : (used == 4 ? 1 : 0)] += 1;
   bs->n_total = bs->n_next;
   bs->parity ^= 1;
   bs->sweep += 1;
+  bs->lanes = batch_lanes_for(B, bs->n_total);
   // problems waiting for room count as active: a sweep with no regions
   // still runs the scan that starts them
   const bool more = bs->active > 0 && bs->sweep < bs->max_sweeps;
   if (B.use_cond) cudaGraphSetConditional(B.cond, more ? 1u : 0u);
 }
 
-size_t batch_rule_smem(int dmax, int rb) {
-  return sizeof(double) * (size_t)(kXRows + 1) * (size_t)dmax * (size_t)rb;
+size_t batch_rule_smem(int dmax) {
+  long long most = batch_rule_doubles(dmax, 1);
+  if (batch_rule_doubles(dmax, 4) > most) most = batch_rule_doubles(dmax, 4);
+  if (batch_rule_doubles(dmax, 32) > most) most = batch_rule_doubles(dmax, 32);
+  const size_t pairs = sizeof(unsigned short) * (size_t)batch_pairs_offset(dmax + 1);
+  return (sizeof(double) * (size_t)most + pairs + 15) & ~(size_t)15;
 }
 
-template <int RB>
-static cudaError_t rule_launch_rb(const BatchArgs& B, int grid, cudaStream_t s) {
-  const size_t smem = batch_rule_smem(B.dmax, RB);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch_rule<RB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_batch_rule<RB><<<grid, RB, smem, s>>>(B);
-  return cudaGetLastError();
-}
-
-int batch_rule_max_blocks(int dmax, int rb) {
+int batch_rule_max_blocks(int dmax) {
   int nb = 0;
-  const size_t smem = batch_rule_smem(dmax, rb);
-  cudaError_t e;
-  if (rb == 64) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_batch_rule<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_rule<64>, 64, smem);
-  } else {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_batch_rule<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_rule<128>, 128, smem);
-  }
-  if (e != cudaSuccess) {
+  const size_t smem = batch_rule_smem(dmax);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_batch_rule, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_rule, kBatchRuleBlock, smem) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -666,8 +635,22 @@ cudaError_t batch_launch_partition(const BatchArgs& B, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t batch_launch_rule(const BatchArgs& B, int rb, int grid, cudaStream_t s) {
-  return rb == 64 ? rule_launch_rb<64>(B, grid, s) : rule_launch_rb<128>(B, grid, s);
+cudaError_t batch_launch_rule(const BatchArgs& B, int grid, cudaStream_t s) {
+  const size_t smem = batch_rule_smem(B.dmax);
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_batch_rule, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_batch_rule<<<grid, kBatchRuleBlock, smem, s>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_launch_tile(const BatchArgs& B, long long n0, long long n, cudaStream_t s) {
+  if (n <= n0) return cudaSuccess;
+  const long long blocks = (n - n0 + 255) / 256;
+  k_batch_tile<<<(unsigned)blocks, 256, 0, s>>>(B, n0, n);
+  return cudaGetLastError();
 }
 
 cudaError_t batch_launch_rest(const BatchArgs& B, cudaStream_t s) {

@@ -7,6 +7,8 @@
 
 namespace gmq {
 
+constexpr int kBatchRuleBlock = 128;  // threads per block of the rule kernel
+
 // Per-integral descriptor (problem, rule constants) and loop state.
 struct BatchItem {
   FamParams P;
@@ -44,7 +46,8 @@ struct BatchState {
   int max_sweeps;          // bound of the device loop (pauses add sweeps)
   int pauses;              // integral-sweeps paused for lack of pool space
   int evictions;           // integrals evicted to make room (restarted later)
-  int pad;
+  int lanes;               // lanes per region of this sweep's rule kernel (1, 4, 32)
+  int lane_sweeps[3];      // sweeps run with 1, 4 and 32 lanes per region
 };
 
 // Arguments of every batch kernel (passed by value).
@@ -68,16 +71,28 @@ struct BatchArgs {
   double lam2, lam3, lam5, ratio;
   cudaGraphConditionalHandle cond;
   int use_cond;
+  // lanes per region of the rule kernel: forced_lanes if nonzero, else 1
+  // for lists of at least lanes_t1 regions, 4 from lanes_t4, 32 below
+  int forced_lanes;
+  long long lanes_t1, lanes_t4;
 };
 
+__host__ __device__ inline int batch_lanes_for(const BatchArgs& B, long long n) {
+  if (B.forced_lanes) return B.forced_lanes;
+  return n >= B.lanes_t1 ? 1 : (n >= B.lanes_t4 ? 4 : 32);
+}
 
-// Shared memory of the rule kernel for the largest dimension and block size.
-size_t batch_rule_smem(int dmax, int rb);
-// Resident blocks per SM of the rule kernel (rb = 64 or 128).
-int batch_rule_max_blocks(int dmax, int rb);
+
+// Shared memory of the rule kernel for the largest dimension.
+size_t batch_rule_smem(int dmax);
+// Resident blocks per SM of the rule kernel.
+int batch_rule_max_blocks(int dmax);
 cudaError_t batch_launch_partition(const BatchArgs& B, cudaStream_t s);
-// Rule evaluation of every region of the current list (persistent grid).
-cudaError_t batch_launch_rule(const BatchArgs& B, int rb, int grid, cudaStream_t s);
+// Rule evaluation of every region of the current list (persistent grid,
+// bs->lanes lanes per region).
+cudaError_t batch_launch_rule(const BatchArgs& B, int grid, cudaStream_t s);
+// Fill list 0 positions [n0, n) with copies of its regions [0, n0).
+cudaError_t batch_launch_tile(const BatchArgs& B, long long n0, long long n, cudaStream_t s);
 // Sums, classification, scan, split and loop advance of one sweep.
 cudaError_t batch_launch_rest(const BatchArgs& B, cudaStream_t s);
 

@@ -1,0 +1,312 @@
+// gm_region64.cuh -- FP64 evaluation of one region by a group of T lanes
+// (T in {1, 4, 32}), shared by the single-integral rule kernel (gm_rule.cuh)
+// and the batched rule kernel (gm_batch.cu): both compute every region with
+// the same operations in the same order.
+//
+// What is computed (paper Sec. 2, the Genz-Malik degree-7 rule with its
+// embedded degree-5 rule): the five class sums S1..S5 of f over the fully
+// symmetric node classes, the fourth differences D_k from the centre and
+// the +-lambda2, +-lambda3 axis nodes, and the split axis argmax_k D_k.
+//
+// Summation order.  Every class sum is one fixed tree, whatever T is.  The
+// class's nodes, in the order of their definition (class 2: axis k = 0..d-1,
+// +lambda2 then -lambda2; class 3 likewise with lambda3; class 4: pairs
+// j < k in lexicographic order, sign patterns ++, +-, -+, --; class 5: sign
+// patterns m = 0 .. 2^d - 1, bit j set = -lambda5 on axis j) are cut into 32
+// chunks of c = ceil(n / 32) consecutive nodes (trailing chunks may be short
+// or empty).  A chunk is summed left to right; the chunk sums are combined
+// by the adjacent-pairwise tree over the 32 chunk positions, in which a
+// subtree holding no node passes its sibling through unchanged.  Lane l of
+// a group of T takes the 32/T consecutive chunks that start at chunk
+// (32/T) * bitrev(l) (bitrev over log2 T bits), combines them with the same
+// tree, and the group finishes the tree with an xor butterfly: with that
+// bit-reversed assignment the butterfly's partners at offset T/2, T/4, ...
+// are exactly the tree's sibling subtrees at successive levels, and IEEE
+// addition is commutative, so every lane ends with the same value.  The
+// sums -- and everything computed from them -- are therefore bit-identical
+// for T = 1, 4 and 32: the lane mapping is a pure launch choice.
+#pragma once
+
+#include "gmq_common.cuh"
+#include "gmq_families.cuh"
+
+namespace gmq {
+
+// Node-coordinate rows of a region's table (lambda4 == lambda3, so pair
+// nodes reuse rows P3/M3).
+enum XRow { kXC = 0, kXP2 = 1, kXM2 = 2, kXP3 = 3, kXM3 = 4, kXP5 = 5, kXM5 = 6, kXRows = 7 };
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+
+// Lanes of this thread's group (T consecutive lanes of one warp).
+template <int T>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (T == 32) {
+    return 0xffffffffu;
+  } else {
+    const unsigned base = (threadIdx.x & 31u) & ~(unsigned)(T - 1);
+    return ((1u << T) - 1u) << base;
+  }
+}
+
+// First of the 32/T chunk positions lane `lane` of a group of T owns.
+template <int T>
+__device__ __forceinline__ int lane_first_chunk(int lane) {
+  if constexpr (T == 1) {
+    return 0;
+  } else {
+    constexpr int bits = ilog2c(T);
+    return (32 / T) * (int)(__brev((unsigned)lane) >> (32 - bits));
+  }
+}
+
+// Adjacent-pairwise tree over at most 32 leaves pushed left to right: a
+// binary counter of complete subtrees (L_j holds 2^j leaves while bit j of
+// the leaf count is set).  flush() combines the pending subtrees from the
+// rightmost up, so a missing right part of the tree passes through.
+struct PairTree {
+  double L0 = 0.0, L1 = 0.0, L2 = 0.0, L3 = 0.0, L4 = 0.0, L5 = 0.0;
+  int n = 0;
+  __device__ __forceinline__ void push(double x) {
+    const int p = n++;
+    if (!(p & 1)) { L0 = x; return; }
+    x = __dadd_rn(L0, x);
+    if (!(p & 2)) { L1 = x; return; }
+    x = __dadd_rn(L1, x);
+    if (!(p & 4)) { L2 = x; return; }
+    x = __dadd_rn(L2, x);
+    if (!(p & 8)) { L3 = x; return; }
+    x = __dadd_rn(L3, x);
+    if (!(p & 16)) { L4 = x; return; }
+    L5 = __dadd_rn(L4, x);
+  }
+  __device__ __forceinline__ double flush(bool& present) const {
+    present = n > 0;
+    if (n >= 32) return L5;
+    double x = 0.0;
+    bool have = false;
+    if (n & 1) { x = L0; have = true; }
+    if (n & 2) { x = have ? __dadd_rn(L1, x) : L1; have = true; }
+    if (n & 4) { x = have ? __dadd_rn(L2, x) : L2; have = true; }
+    if (n & 8) { x = have ? __dadd_rn(L3, x) : L3; have = true; }
+    if (n & 16) { x = have ? __dadd_rn(L4, x) : L4; }
+    return x;
+  }
+};
+
+// The group's xor butterfly over lane partial trees (absent partials pass
+// the other side through); every lane returns the full tree's value.
+template <int T>
+__device__ __forceinline__ double lanes_tree(double x, bool present, unsigned mask) {
+#pragma unroll
+  for (int off = T / 2; off > 0; off >>= 1) {
+    const double ox = __shfl_xor_sync(mask, x, off, T);
+    const int op = __shfl_xor_sync(mask, present ? 1 : 0, off, T);
+    if (present && op) {
+      x = __dadd_rn(x, ox);
+    } else if (op) {
+      x = ox;
+      present = true;
+    }
+  }
+  return present ? x : 0.0;
+}
+
+// One class sum over n nodes, val(q) = f at the class's node q.
+template <int T, class Val>
+__device__ __forceinline__ double class_sum(int n, int lane, unsigned mask, Val val) {
+  PairTree t;
+  if (n > 0) {
+    const int c = (n + 31) >> 5;
+    const int nch = (n + c - 1) / c;
+    const int p0 = lane_first_chunk<T>(lane);
+    const int p1 = min(p0 + 32 / T, nch);
+    for (int p = p0; p < p1; ++p) {
+      const int q0 = p * c, q1 = min(q0 + c, n);
+      double x = 0.0;
+      for (int q = q0; q < q1; ++q) {
+        const double v = val(q);
+        x = (q == q0) ? v : __dadd_rn(x, v);
+      }
+      t.push(x);
+    }
+  }
+  bool present;
+  const double x = t.flush(present);
+  return lanes_tree<T>(x, present, mask);
+}
+
+struct RegionSums {
+  double s1, s2, s3, s4, s5;  // class sums
+  double f0;                  // f(centre)
+  double dbest;               // largest fourth difference
+  int kbest;                  // its axis (lowest on ties)
+};
+
+// The class sums and the fourth-difference argmax of one region by the T
+// lanes of the calling group (all of them call it).  tab(row, j) is the
+// region's node coordinate on axis j for XRow `row`; pairs[p] = (j << 8) | k
+// for the p-th pair j < k of dimension d; fv points at the region's column
+// of a [4d + 1] x fvs scratch array (T > 1 only).
+template <int FAM, int T, class PT, class Tab>
+__device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned short* pairs,
+                                              const Tab& tab, double* fv, int fvs, double ratio,
+                                              RegionSums& o) {
+  const int lane = (T == 1) ? 0 : (int)(threadIdx.x & (unsigned)(T - 1));
+  const unsigned mask = group_mask<T>();
+  const int na = 1 + 4 * d;  // centre and axis nodes
+  double f0 = 0.0, dbest = -1.0, s2, s3;
+  int kbest = 0;
+  if (T == 1) {
+    PairTree t2, t3;
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    for (int i = 0; i < na; ++i) {
+      int k1 = -1, r1 = kXC, w = 0;
+      if (i > 0) {
+        k1 = (i - 1) >> 2;
+        w = (i - 1) & 3;
+        r1 = kXP2 + w;
+      }
+      const double v = Family<FAM>::template eval<double>(
+          P, d, [&](int j) -> double { return tab(j == k1 ? r1 : kXC, j); });
+      if (i == 0) {
+        f0 = v;
+        continue;
+      }
+      if (w < 2)
+        t2.push(v);
+      else
+        t3.push(v);
+      if (w == 0) {
+        q0 = v;
+      } else if (w == 1) {
+        q1 = v;
+      } else if (w == 2) {
+        q2 = v;
+      } else {
+        const double two_f0 = __dmul_rn(2.0, f0);
+        const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
+        const double tt = __dsub_rn(__dadd_rn(q2, v), two_f0);
+        const double D = fabs(__dsub_rn(t1, __dmul_rn(ratio, tt)));
+        if (D > dbest) {
+          dbest = D;
+          kbest = k1;
+        }
+      }
+    }
+    bool pr;
+    s2 = t2.flush(pr);
+    s3 = t3.flush(pr);
+  } else {
+    for (int i = lane; i < na; i += T) {
+      int k1 = -1, r1 = kXC, w = 0;
+      if (i > 0) {
+        k1 = (i - 1) >> 2;
+        w = (i - 1) & 3;
+        r1 = kXP2 + w;
+      }
+      const double v = Family<FAM>::template eval<double>(
+          P, d, [&](int j) -> double { return tab(j == k1 ? r1 : kXC, j); });
+      fv[(i == 0 ? 4 * d : w * d + k1) * fvs] = v;
+    }
+    __syncwarp(mask);
+    f0 = fv[4 * d * fvs];
+    const double two_f0 = __dmul_rn(2.0, f0);
+    for (int k = lane; k < d; k += T) {
+      const double t1 = __dsub_rn(__dadd_rn(fv[(0 * d + k) * fvs], fv[(1 * d + k) * fvs]), two_f0);
+      const double tt = __dsub_rn(__dadd_rn(fv[(2 * d + k) * fvs], fv[(3 * d + k) * fvs]), two_f0);
+      const double D = fabs(__dsub_rn(t1, __dmul_rn(ratio, tt)));
+      if (D > dbest) {
+        dbest = D;
+        kbest = k;
+      }
+    }
+    // argmax over the lanes: larger D wins, the lower axis on ties
+#pragma unroll
+    for (int off = T / 2; off > 0; off >>= 1) {
+      const double od = __shfl_xor_sync(mask, dbest, off, T);
+      const int ok = __shfl_xor_sync(mask, kbest, off, T);
+      if (od > dbest || (od == dbest && ok < kbest)) {
+        dbest = od;
+        kbest = ok;
+      }
+    }
+    // classes 2 and 3 hold 2d <= 32 nodes: one node per chunk
+    PairTree t2, t3;
+    const int p0 = lane_first_chunk<T>(lane), p1 = min(p0 + 32 / T, 2 * d);
+    for (int p = p0; p < p1; ++p) {
+      t2.push(fv[((p & 1) * d + (p >> 1)) * fvs]);
+      t3.push(fv[((2 + (p & 1)) * d + (p >> 1)) * fvs]);
+    }
+    bool pr2, pr3;
+    const double x2 = t2.flush(pr2), x3 = t3.flush(pr3);
+    s2 = lanes_tree<T>(x2, pr2, mask);
+    s3 = lanes_tree<T>(x3, pr3, mask);
+  }
+  // class 4: c +- lambda4 h_j e_j +- lambda4 h_k e_k, j < k
+  o.s4 = class_sum<T>(2 * d * (d - 1), lane, mask, [&](int q) -> double {
+    const unsigned pr = pairs[q >> 2];
+    const int kj = (int)(pr >> 8), kk = (int)(pr & 255u);
+    const int rj = (q & 2) ? kXM3 : kXP3, rk = (q & 1) ? kXM3 : kXP3;
+    return Family<FAM>::template eval<double>(
+        P, d, [&](int j) -> double { return tab(j == kj ? rj : (j == kk ? rk : kXC), j); });
+  });
+  // class 5: c + lambda5 (sigma o h) for the 2^d sign patterns
+  o.s5 = class_sum<T>(1 << d, lane, mask, [&](int m) -> double {
+    return Family<FAM>::template eval<double>(P, d, [&](int j) -> double {
+      return tab((((unsigned)m >> j) & 1u) ? kXM5 : kXP5, j);
+    });
+  });
+  o.s1 = f0;
+  o.s2 = s2;
+  o.s3 = s3;
+  o.f0 = f0;
+  o.dbest = dbest;
+  o.kbest = kbest;
+}
+
+// Rule values, error estimate, split axis and round-off guard of a region
+// from its class sums (one lane).  cval(k), hval(k): centre and half-width.
+template <class CV, class HV>
+__device__ __forceinline__ void region_finish64(const RegionSums& o, int d, const double* w7,
+                                                const double* w5, double vol_omega, CV cval,
+                                                HV hval, double* i7o, double* erro, double* vfo,
+                                                uint8_t* axo) {
+  double vol = 1.0;
+  for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, hval(k)));
+  double t7 = __dmul_rn(w7[0], o.s1);
+  t7 = __dadd_rn(t7, __dmul_rn(w7[1], o.s2));
+  t7 = __dadd_rn(t7, __dmul_rn(w7[2], o.s3));
+  t7 = __dadd_rn(t7, __dmul_rn(w7[3], o.s4));
+  t7 = __dadd_rn(t7, __dmul_rn(w7[4], o.s5));
+  double t5 = __dmul_rn(w5[0], o.s1);
+  t5 = __dadd_rn(t5, __dmul_rn(w5[1], o.s2));
+  t5 = __dadd_rn(t5, __dmul_rn(w5[2], o.s3));
+  t5 = __dadd_rn(t5, __dmul_rn(w5[3], o.s4));
+  const double i7 = __dmul_rn(vol, t7);
+  const double i5 = __dmul_rn(vol, t5);
+  // split axis: flat differences -> the widest axis (lowest index on ties)
+  const double flat_thr = __dadd_rn(__dmul_rn(1e-14, fabs(o.f0)), 1e-300);
+  int ax = o.kbest;
+  if (!(o.dbest > flat_thr)) {
+    ax = 0;
+    double hb = hval(0);
+    for (int k = 1; k < d; ++k) {
+      const double hk = hval(k);
+      if (hk > hb) {
+        hb = hk;
+        ax = k;
+      }
+    }
+  }
+  // round-off guard: bisection along ax must move the centre
+  const double cs = cval(ax);
+  const double hh = __dmul_rn(0.5, hval(ax));
+  const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
+  *i7o = i7;
+  *erro = fabs(__dsub_rn(i7, i5));
+  if (vfo) *vfo = __ddiv_rn(vol, vol_omega);
+  *axo = (uint8_t)(ax | (bad ? 0x80 : 0));
+}
+
+}  // namespace gmq

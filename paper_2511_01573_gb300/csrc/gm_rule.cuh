@@ -8,34 +8,33 @@
 //      arrays list into shared memory with coalesced loads (consecutive
 //      threads read consecutive regions of one axis) and expands them into a
 //      table of node coordinates c_k +- lambda h_k, one row per generator;
-//   2. walks the flat node index i = 0 .. N(d)-1 of each region, lane l of a
-//      region taking i = l, l+T, ...; a node's class, axes and signs are
-//      decoded from the bits of i (centre; 4d axis nodes; 4 sign patterns
-//      per axis pair; the 2^d sign patterns of the last class are the bits
-//      of i itself), and its coordinates are read from the table, so the
-//      only floating-point work per node is the integrand and one
-//      accumulation;
-//   3. reduces the five class sums over the T lanes with warp shuffles,
-//      finds the split axis (argmax of the fourth differences) with a
-//      shuffle argmax, and writes I7, |I7 - I5|, vol / vol(Omega) and the
-//      axis byte.
-// Real = double: every step in FP64.  Real = float (mixed form): node
+//   2. walks each class of nodes of each region by index: a node's axes and
+//      signs are decoded from the bits of its index (centre; 4d axis nodes;
+//      4 sign patterns per axis pair; the 2^d sign patterns of the last
+//      class are the bits of the index itself), and its coordinates are read
+//      from the table, so the only floating-point work per node is the
+//      integrand and one accumulation;
+//   3. combines the class sums over the T lanes with warp shuffles, finds the
+//      split axis (argmax of the fourth differences) with a shuffle argmax,
+//      and writes I7, |I7 - I5|, vol / vol(Omega) and the axis byte.
+// FP64 (k_rule64): the per-region work is region_sums64 / region_finish64
+// of gm_region64.cuh, whose fixed summation tree makes the results
+// bit-identical for every T.  Mixed form (k_rule with Real = float): node
 // coordinates are formed in FP64 and rounded to FP32, the integrand runs in
-// FP32 and the class sums are FP32 with TwoSum compensation; class sums,
-// fourth differences, axis choice, rule values and error estimate are FP64.
-// With T = 1 and Real = double the class sums are accumulated in the same
-// node order as the plain definition (centre; per axis +l2, -l2, +l3, -l3;
-// pairs j < k with sign patterns ++, +-, -+, --; patterns m = 0 .. 2^d-1).
+// FP32 and the class sums are FP32 with TwoSum compensation, accumulated in
+// node order per lane and combined over the lanes by a butterfly; class
+// sums, fourth differences, axis choice, rule values and error estimate are
+// FP64.  For one lane per region and 3 <= d <= 12 the mixed form walks the
+// sign patterns in registers (k_rule_mixed_reg).
 #pragma once
 
+#include <type_traits>
+
+#include "gm_region64.cuh"
 #include "gmq_common.cuh"
 #include "gmq_families.cuh"
 
 namespace gmq {
-
-// Node-coordinate rows of the shared-memory table (lambda4 == lambda3, so
-// pair nodes reuse rows P3/M3).
-enum XRow { kXC = 0, kXP2 = 1, kXM2 = 2, kXP3 = 3, kXM3 = 4, kXP5 = 5, kXM5 = 6, kXRows = 7 };
 
 // Shared-memory bytes of the rule kernel for dimension d, T lanes and an
 // integrand type of `real_bytes` bytes.
@@ -264,6 +263,71 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule(const RuleArgs A) {
     if (A.volfrac) A.volfrac[r] = __ddiv_rn(vol, A.R.vol_omega);
     A.axis[r] = (uint8_t)(ax | (bad ? 0x80 : 0));
   }
+}
+
+// FP64 rule kernel: same staging as k_rule, per-region work shared with the
+// batched kernel (gm_region64.cuh).
+template <int FAM, int T>
+__global__ void __launch_bounds__(kRuleBlock) k_rule64(const RuleArgs A) {
+  constexpr int RB = kRuleBlock / T;
+  extern __shared__ __align__(16) double smem[];
+  const int d = A.P.d;
+  double* cd = smem;                                  // [d][RB] centres
+  double* hd = cd + d * RB;                           // [d][RB] half-widths
+  double* fv = hd + d * RB;                           // [4d + 1][RB] axis-node values, f(c)
+  double* xt = fv + (T > 1 ? (4 * d + 1) * RB : 0);  // [kXRows][d][RB]
+  SmemParams<double>* P = reinterpret_cast<SmemParams<double>*>(xt + kXRows * d * RB);
+  unsigned short* pairs = reinterpret_cast<unsigned short*>(P + 1);
+
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  for (int j = tid; j < d; j += kRuleBlock) {
+    P->a[j] = A.P.a[j];
+    P->u[j] = A.P.u[j];
+    P->b[j] = A.P.b[j];
+  }
+  if (tid == 0) P->c0 = A.P.c0;
+  const int npairs = d * (d - 1) / 2;
+  for (int p = tid; p < npairs; p += kRuleBlock) {
+    int j = 0, rem = p;
+    while (rem >= d - 1 - j) {
+      rem -= d - 1 - j;
+      ++j;
+    }
+    pairs[p] = (unsigned short)((j << 8) | (j + 1 + rem));
+  }
+  const double l2 = A.R.lam2, l3 = A.R.lam3, l5 = A.R.lam5;
+  for (int idx = tid; idx < d * RB; idx += kRuleBlock) {
+    const int k = idx / RB, q = idx - k * RB;
+    const int64_t r = r0 + q;
+    double cv = 0.5, hv = 0.25;
+    if (r < A.n) {
+      cv = A.c[(int64_t)k * A.ld + r];
+      hv = A.h[(int64_t)k * A.ld + r];
+    }
+    cd[k * RB + q] = cv;
+    hd[k * RB + q] = hv;
+    xt[(kXC * d + k) * RB + q] = cv;
+    xt[(kXP2 * d + k) * RB + q] = fma(l2, hv, cv);
+    xt[(kXM2 * d + k) * RB + q] = fma(-l2, hv, cv);
+    xt[(kXP3 * d + k) * RB + q] = fma(l3, hv, cv);
+    xt[(kXM3 * d + k) * RB + q] = fma(-l3, hv, cv);
+    xt[(kXP5 * d + k) * RB + q] = fma(l5, hv, cv);
+    xt[(kXM5 * d + k) * RB + q] = fma(-l5, hv, cv);
+  }
+  __syncthreads();
+
+  const int g = tid / T;
+  const int64_t r = r0 + g;
+  if (r >= A.n) return;  // the whole group: its lanes share the region
+  auto tab = [&](int row, int j) -> double { return xt[(row * d + j) * RB + g]; };
+  RegionSums o;
+  region_sums64<FAM, T>(*P, d, pairs, tab, fv + g, RB, A.R.ratio, o);
+  if ((tid & (T - 1)) == 0)
+    region_finish64(
+        o, d, A.R.w7, A.R.w5, A.R.vol_omega, [&](int k) { return cd[k * RB + g]; },
+        [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
+        A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
 }
 
 // Integrand parameters in registers (compile-time dimension).
@@ -511,14 +575,19 @@ template <int FAM, int T, class Real>
 cudaError_t launch_rule_t(const RuleArgs& A, cudaStream_t s) {
   const int RB = kRuleBlock / T;
   const size_t smem = rule_smem_bytes(A.P.d, T, (int)sizeof(Real));
+  void (*kern)(const RuleArgs);
+  if constexpr (std::is_same<Real, double>::value)
+    kern = k_rule64<FAM, T>;
+  else
+    kern = k_rule<FAM, T, Real>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_rule<FAM, T, Real>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
   }
   const int64_t blocks = (A.n + RB - 1) / RB;
   if (blocks == 0) return cudaSuccess;
-  k_rule<FAM, T, Real><<<(unsigned)blocks, kRuleBlock, smem, s>>>(A);
+  kern<<<(unsigned)blocks, kRuleBlock, smem, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -58,9 +58,10 @@ struct gmq_context {
   // working memory of gmq_rule_grad
   char* gscratch = nullptr;
   size_t gscratch_bytes = 0;
-  // batched form: autotuned rule-kernel launch shape per largest dimension
-  int tuned_rb[GMQ_MAX_DIM + 1] = {};
-  int tuned_grid[GMQ_MAX_DIM + 1] = {};
+  // batched form: autotuned lanes-per-region thresholds per largest dimension
+  int tuned[GMQ_MAX_DIM + 1] = {};
+  long long tuned_t1[GMQ_MAX_DIM + 1] = {};
+  long long tuned_t4[GMQ_MAX_DIM + 1] = {};
   gmq_batch_info last_batch = {};
   cudaStream_t capture_stream = nullptr;  // private stream for graph capture
   // kernel timing (gmq_profile_*)
@@ -926,6 +927,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   const int64_t cap = opt->max_regions;  // per problem
   if (!(opt->abs_tol >= 0.0) || cap < 1 || cap > kMaxRegions || opt->init_splits < 0 ||
       opt->max_iters < 0 || (opt->flags & ~GMQ_BATCH_HOST_LOOP) || opt->precision != GMQ_FP64 ||
+      (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32) ||
       (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL))
     return GMQ_ERR_INVALID;
   std::memset(results, 0, sizeof(gmq_result) * (size_t)count);
@@ -1058,43 +1060,80 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   GMQ_CK(batch_launch_partition(B, strm));
   ctx->launches += 1;
 
-  // autotuner: time the rule kernel's candidate launch shapes on the
-  // initial list once per largest dimension (the launches only write the
-  // rule outputs, which the first sweep overwrites)
+  // lanes per region of the rule kernel: forced, or per sweep from the list
+  // length with thresholds the autotuner sets once per largest dimension by
+  // timing the three mappings on copies of the initial list (the launches
+  // only write rule outputs, which the first sweep overwrites)
   gmq_batch_info info;
   std::memset(&info, 0, sizeof(info));
-  for (int c = 0; c < 4; ++c) info.tune_ms[c] = -1.0;
-  if (!ctx->tuned_rb[dmax]) {
-    const int rbs[2] = {64, 128};
-    float best = 1e30f;
+  const int grid = ctx->sm_count * batch_rule_max_blocks(dmax);  // also sets the smem limit
+  B.forced_lanes = opt->lanes;
+  if (!opt->lanes && !ctx->tuned[dmax]) {
+    const int64_t wave = (int64_t)grid * kBatchRuleBlock;  // regions of one T = 1 wave
+    int64_t lens[5];
+    int nl = 0;
+    for (int64_t L : {wave / 64, wave / 16, wave / 4, wave, 4 * wave}) {
+      L = std::min<int64_t>(std::max<int64_t>(L, 1), pool);
+      if (nl == 0 || L > lens[nl - 1]) lens[nl++] = L;
+    }
+    GMQ_CK(batch_launch_tile(B, total, lens[nl - 1], strm));
+    ctx->launches += 1;
+    const int modes[3] = {1, 4, 32};
+    int best[5];
     cudaEvent_t e0, e1;
     GMQ_CK(cudaEventCreate(&e0));
     GMQ_CK(cudaEventCreate(&e1));
-    for (int c = 0; c < 2; ++c) {
-      const int grid = ctx->sm_count * batch_rule_max_blocks(dmax, rbs[c]);
-      GMQ_CK(batch_launch_rule(B, rbs[c], grid, strm));  // warm-up
-      GMQ_CK(cudaEventRecord(e0, strm));
-      GMQ_CK(batch_launch_rule(B, rbs[c], grid, strm));
-      GMQ_CK(cudaEventRecord(e1, strm));
-      GMQ_CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      GMQ_CK(cudaEventElapsedTime(&ms, e0, e1));
-      info.tune_ms[c] = ms;
-      ctx->launches += 2;
-      if (ms < best) {
-        best = ms;
-        ctx->tuned_rb[dmax] = rbs[c];
-        ctx->tuned_grid[dmax] = grid;
+    for (int i = 0; i < nl; ++i) {
+      float mbest = 1e30f;
+      float ms[3];
+      for (int m = 0; m < 3; ++m) {
+        BatchState t = bs0;
+        t.n_total = lens[i];
+        t.lanes = modes[m];
+        GMQ_CK(cudaMemcpyAsync(B.bs, &t, sizeof(BatchState), cudaMemcpyHostToDevice, strm));
+        GMQ_CK(batch_launch_rule(B, grid, strm));  // warm-up
+        GMQ_CK(cudaEventRecord(e0, strm));
+        GMQ_CK(batch_launch_rule(B, grid, strm));
+        GMQ_CK(cudaEventRecord(e1, strm));
+        GMQ_CK(cudaEventSynchronize(e1));
+        GMQ_CK(cudaEventElapsedTime(&ms[m], e0, e1));
+        ctx->launches += 2;
+        info.tune_ms[i][m] = ms[m];
+        mbest = std::min(mbest, ms[m]);
       }
+      // the fewest lanes within 5% of the fastest mapping
+      best[i] = 2;
+      for (int m = 2; m >= 0; --m)
+        if (ms[m] <= 1.05f * mbest) best[i] = m;
+      info.tune_n[i] = lens[i];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    auto between = [&](int i) -> long long {  // geometric middle of lens[i-1], lens[i]
+      return (long long)std::llround(std::sqrt((double)lens[i - 1] * (double)lens[i]));
+    };
+    // one lane from the shortest timed length where it wins there and at
+    // every longer one (beyond twice the longest if it never does)
+    int i1 = nl;
+    for (int i = nl - 1; i >= 0 && best[i] == 0; --i) i1 = i;
+    const long long t1 = i1 == nl ? 2 * lens[nl - 1] : (i1 == 0 ? 0 : between(i1));
+    int i4 = i1;
+    for (int i = i1 - 1; i >= 0 && best[i] <= 1; --i) i4 = i;
+    const long long t4 = i4 == i1 ? t1 : (i4 == 0 ? 0 : between(i4));
+    ctx->tuned[dmax] = 1;
+    ctx->tuned_t1[dmax] = t1;
+    ctx->tuned_t4[dmax] = t4;
     info.autotuned = 1;
   }
-  const int rb = ctx->tuned_rb[dmax], grid = ctx->tuned_grid[dmax];
-  batch_rule_max_blocks(dmax, rb);  // sets the kernel's shared-memory limit before any capture
-  info.rule_block = rb;
+  B.lanes_t1 = ctx->tuned_t1[dmax];
+  B.lanes_t4 = ctx->tuned_t4[dmax];
+  bs0.lanes = batch_lanes_for(B, bs0.n_total);
+  GMQ_CK(cudaMemcpyAsync(B.bs, &bs0, sizeof(BatchState), cudaMemcpyHostToDevice, strm));
+  info.rule_block = kBatchRuleBlock;
   info.rule_grid = grid;
+  info.forced_lanes = opt->lanes;
+  info.lanes_t1 = opt->lanes ? 0 : B.lanes_t1;
+  info.lanes_t4 = opt->lanes ? 0 : B.lanes_t4;
 
   BatchState hs;
   if (!(opt->flags & GMQ_BATCH_HOST_LOOP)) {
@@ -1126,7 +1165,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
         e = cudaStreamBeginCaptureToGraph(ctx->capture_stream, body, nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t e1 = batch_launch_rule(B, rb, grid, ctx->capture_stream);
+        cudaError_t e1 = batch_launch_rule(B, grid, ctx->capture_stream);
         cudaError_t e2 = batch_launch_rest(B, ctx->capture_stream);
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(ctx->capture_stream, &captured);
@@ -1145,7 +1184,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     B.use_cond = 0;
     for (;;) {
       for (int k = 0; k < 8; ++k) {
-        GMQ_CK(batch_launch_rule(B, rb, grid, strm));
+        GMQ_CK(batch_launch_rule(B, grid, strm));
         GMQ_CK(batch_launch_rest(B, strm));
         ctx->launches += 6;
       }
@@ -1164,6 +1203,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   info.sweeps = hs.sweep;
   info.pauses = hs.pauses;
   info.evictions = hs.evictions;
+  for (int m = 0; m < 3; ++m) info.lane_sweeps[m] = hs.lane_sweeps[m];
   ctx->last_batch = info;
   for (int32_t i = 0; i < count; ++i) {
     const BatchItem& it = items[(size_t)i];

@@ -72,7 +72,10 @@ BATCH_HOST_LOOP = 2
 class BatchInfo(C.Structure):
     _fields_ = [("rule_block", C.c_int32), ("rule_grid", C.c_int32), ("sweeps", C.c_int32),
                 ("used_graph", C.c_int32), ("autotuned", C.c_int32), ("pauses", C.c_int32),
-                ("evictions", C.c_int32), ("reserved", C.c_int32), ("tune_ms", C.c_double * 4)]
+                ("evictions", C.c_int32), ("forced_lanes", C.c_int32),
+                ("lanes_t1", C.c_int64), ("lanes_t4", C.c_int64),
+                ("lane_sweeps", C.c_int32 * 3), ("reserved", C.c_int32),
+                ("tune_n", C.c_int64 * 5), ("tune_ms", (C.c_double * 3) * 5)]
 
 ERR_TOO_LARGE = -6
 NOALLOC_MAX_N = 1 << 23
@@ -297,18 +300,20 @@ class Context:
 
     def integrate_batch(self, problems, rel_tols=None, max_regions=1 << 24, abs_tol=1e-16,
                         init_splits=0, max_iters=0, classifier=VOLUME_SHARE, host_loop=False,
-                        pool_regions=0):
+                        pool_regions=0, lanes=0):
         """Integrate many problems in one device-resident loop.  problems:
         objects with family, dim, a, u (and optional lo, hi, rel_tol).
         max_regions is each problem's cap, pool_regions the shared pool (0:
-        the library's default).  Returns one IntegrateResult per problem."""
+        the library's default); lanes 1, 4 or 32 fixes the rule kernel's
+        lanes per region (0: autotuned per sweep).  Returns one
+        IntegrateResult per problem."""
         hs = [_ProblemHandle(p.family, p.a, p.u, getattr(p, "lo", None), getattr(p, "hi", None),
                              p.dim) for p in problems]
         arr = (Problem * len(hs))(*[h.s for h in hs])
         if rel_tols is None:
             rel_tols = [p.rel_tol for p in problems]
         tols = _f64(rel_tols, len(hs))
-        o = Options(0.0, abs_tol, max_regions, init_splits, max_iters, FP64, classifier, 0,
+        o = Options(0.0, abs_tol, max_regions, init_splits, max_iters, FP64, classifier, lanes,
                     BATCH_HOST_LOOP if host_loop else 0)
         res = (Result * len(hs))()
         _check("gmq_integrate_batch", lib().gmq_integrate_batch(self.h, len(hs), arr, _ptr(tols),
@@ -322,8 +327,11 @@ class Context:
         return {"rule_block": info.rule_block, "rule_grid": info.rule_grid,
                 "sweeps": info.sweeps, "used_graph": bool(info.used_graph),
                 "autotuned": bool(info.autotuned), "pauses": int(info.pauses),
-                "evictions": int(info.evictions),
-                "tune_ms": list(info.tune_ms)}
+                "evictions": int(info.evictions), "forced_lanes": int(info.forced_lanes),
+                "lanes_t1": int(info.lanes_t1), "lanes_t4": int(info.lanes_t4),
+                "lane_sweeps": list(info.lane_sweeps),
+                "tune": [{"n": int(info.tune_n[i]), "ms": list(info.tune_ms[i])}
+                         for i in range(5) if info.tune_n[i] > 0]}
 
     def partition_copy(self):
         """The final partition of the last integrate(keep_partition=True) call

@@ -1,9 +1,11 @@
 """Batched form (gmq_integrate_batch) on the GPU.
 
 Every problem of a batch must get exactly the result gmq_integrate gives it
-alone with one thread per region (same node order, sums, decisions and
-child order): integral, error, region count, sweeps and status are
-compared for equality, in the CUDA-graph mode and in the host-driven mode.
+alone (the same per-region arithmetic, sums, decisions and child order,
+whatever lanes per region either side uses): integral, error, region count,
+sweeps and status are compared for equality, in the CUDA-graph mode and in
+the host-driven mode, with the autotuned per-sweep mapping and with each
+mapping forced.
 The single-problem path is itself checked against the CPU oracle in
 test_gpu_parity.py; here a sample of batch results is also checked against
 the oracle directly.
@@ -40,13 +42,29 @@ def test_batch_equals_single_runs(gpu_ctx, host_loop):
     res = gpu_ctx.integrate_batch(probs, max_regions=cap, host_loop=host_loop)
     info = gpu_ctx.last_batch_info()
     assert info["used_graph"] == (not host_loop)
-    assert info["rule_block"] in (64, 128)
+    assert info["rule_block"] == 128
+    assert sum(info["lane_sweeps"]) == info["sweeps"]
     for p, r in zip(probs, res):
         s = _single(gpu_ctx, p, cap)
         assert (r.status, r.iterations, r.regions_evaluated) == (s.status, s.iterations,
                                                                  s.regions_evaluated), p.label
         assert r.integral == s.integral and r.error == s.error
     assert info["sweeps"] >= max(r.iterations for r in res)
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+def test_batch_forced_lane_mappings(gpu_ctx, lanes):
+    probs = _mixed_batch(n=24, seed=13)
+    cap = 1 << 20
+    res = gpu_ctx.integrate_batch(probs, max_regions=cap, lanes=lanes)
+    info = gpu_ctx.last_batch_info()
+    assert info["forced_lanes"] == lanes and not info["autotuned"]
+    assert info["lane_sweeps"][{1: 0, 4: 1, 32: 2}[lanes]] == info["sweeps"]
+    for p, r in zip(probs, res):
+        s = gpu_ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=cap)
+        assert (r.status, r.iterations, r.regions_evaluated) == (s.status, s.iterations,
+                                                                 s.regions_evaluated), p.label
+        assert r.integral == s.integral and r.error == s.error
 
 
 def test_batch_against_oracle_sample(oracle, gpu_ctx):
@@ -80,9 +98,18 @@ def test_batch_many_integrals_workload_sample(gpu_ctx):
 def test_batch_autotune_cached_and_limits(gpu_ctx):
     from paper_2511_01573_gb300 import gmq
     probs = _mixed_batch(n=8, seed=3)
-    gpu_ctx.integrate_batch(probs)
+    first = gpu_ctx.integrate_batch(probs)
+    info = gpu_ctx.last_batch_info()
+    if info["autotuned"]:
+        tune = info["tune"]
+        assert 1 <= len(tune) <= 5 and all(len(t["ms"]) == 3 for t in tune)
+        assert all(t["ms"][m] > 0 for t in tune for m in range(3))
+        assert [t["n"] for t in tune] == sorted(t["n"] for t in tune)
+    assert 0 <= info["lanes_t4"] <= info["lanes_t1"]
     again = gpu_ctx.integrate_batch(probs)
     assert not gpu_ctx.last_batch_info()["autotuned"]  # cached per largest dimension
+    assert [(r.integral, r.regions_evaluated) for r in again] == [
+        (r.integral, r.regions_evaluated) for r in first]
     # sweep limit: every problem stops by the third sweep
     res = gpu_ctx.integrate_batch(probs, max_iters=3)
     assert all(r.iterations <= 3 for r in res)
@@ -95,4 +122,6 @@ def test_batch_autotune_cached_and_limits(gpu_ctx):
     with pytest.raises(gmq.GmqError):
         # an initial partition larger than half the pool could never start
         gpu_ctx.integrate_batch(probs, pool_regions=64)
+    with pytest.raises(gmq.GmqError):
+        gpu_ctx.integrate_batch(probs, lanes=8)
     assert len(again) == len(probs)
