@@ -122,6 +122,22 @@ def time_to_tol(ctx, stream, tol):
     out["speedup_batched_over_fp64"] = out["fp64_s"] / out["batched_s"]
     out["batched_max_rel_diff_vs_fp64"] = max(
         abs(b.integral - f.integral) / abs(f.integral) for b, f in zip(res, vals["fp64"]))
+    # batched mixed form (one graph launch, FP32 integrand)
+    ctx.integrate_batch(probs[:4], max_regions=CAP, precision=gmq.MIXED)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = ctx.integrate_batch(probs, max_regions=CAP, pool_regions=1 << 26, precision=gmq.MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["batched_mixed_s"] = e0.elapsed_time(e1) / 1000.0
+    out["batched_mixed_regions"] = sum(r.regions_evaluated for r in res)
+    out["batched_mixed_converged"] = sum(1 for r in res if r.status == 0)
+    out["speedup_batched_mixed_over_fp64"] = out["fp64_s"] / out["batched_mixed_s"]
+    out["speedup_batched_mixed_over_mixed"] = out["mixed_s"] / out["batched_mixed_s"]
+    out["batched_mixed_max_rel_diff_vs_fp64"] = max(
+        abs(b.integral - f.integral) / abs(f.integral) for b, f in zip(res, vals["fp64"]))
     return out
 
 
@@ -489,16 +505,27 @@ def all_configs(args):
     bcap = 1 << 22  # per problem
     res, tb = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27))
     info = ctx.last_batch_info()
-    seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
-                                           lanes=1) for q in probs])
+    seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap)
+                             for q in probs])
     same = sum(1 for sr, br in zip(seq, res)
                if sr.integral == br.integral and sr.regions_evaluated == br.regions_evaluated)
     st = {}
     for x in res:
         st[str(x.status)] = st.get(str(x.status), 0) + 1
+    resm, tbm = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27,
+                                                  precision=gmq.MIXED))
+    infom = ctx.last_batch_info()
+    seqm, tsm = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
+                                             precision=gmq.MIXED) for q in probs])
     rep["batch"] = {"problems": len(probs), "batched_s": tb, "sequential_s": ts,
                     "speedup": ts / tb, "regions": sum(x.regions_evaluated for x in res),
-                    "statuses": st, "info": info, "identical_to_single_runs": same}
+                    "statuses": st, "info": info, "identical_to_single_runs": same,
+                    "mixed": {"batched_s": tbm, "sequential_s": tsm, "speedup": tsm / tbm,
+                              "speedup_vs_fp64_sequential": ts / tbm,
+                              "regions": sum(x.regions_evaluated for x in resm), "info": infom,
+                              "max_rel_diff_vs_fp64": max(
+                                  abs(m.integral - f.integral) / abs(f.integral)
+                                  for m, f in zip(resm, res) if f.integral != 0.0)}}
     # gradients of the d = 6 Gaussian over frozen partitions
     sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
     errs, tf, tg = [], 0.0, 0.0

@@ -222,19 +222,23 @@ typedef struct gmq_batch_info {
  * sweep of all running problems does not fit in the pool, the problems
  * whose region lists grow are served in index order while they fit; the
  * others are paused for a sweep (their regions are carried over unchanged
- * and evaluated again, which leaves their results unchanged); if nothing
- * can split, the paused problem of highest index is evicted and later
- * restarts from its initial partition (same result again), and a problem
- * that cannot grow even alone stops with GMQ_CAP_REACHED.  The device loop
- * is bounded by 4 x max_iters sweeps.  Device memory: about
- * pool_regions x (32 dmax + 30) bytes, dmax the largest dimension.  FP64 only
- * (opt->precision must be GMQ_FP64).  Lanes per region: opt->lanes (1, 4
- * or 32) for every sweep, or with 0 chosen per sweep from the list length
- * by thresholds an autotuner sets on the first call for each largest
- * dimension (it times the three mappings on copies of the initial list at
- * up to five lengths; cached in the context).  The results do not depend
- * on the mapping.  Returns GMQ_OK when the batch ran (see the per-problem
- * statuses), or an error. */
+ * with their rule outputs and take the same decisions again, which leaves
+ * their results unchanged); if nothing can split, the paused problem of
+ * highest index is evicted and later restarts from its initial partition
+ * (same result again), and a problem that cannot grow even alone stops with
+ * GMQ_CAP_REACHED.  The device loop is bounded by 4 x max_iters sweeps.
+ * Device memory: about pool_regions x (32 dmax + 60) bytes, dmax the
+ * largest dimension.
+ * opt->precision GMQ_FP64: lanes per region opt->lanes (1, 4 or 32) for
+ * every sweep, or with 0 chosen per sweep from the list length by
+ * thresholds an autotuner sets on the first call for each largest dimension
+ * (it times the three mappings on copies of the initial list at up to five
+ * lengths; cached in the context); the results do not depend on the
+ * mapping.  opt->precision GMQ_MIXED: one lane per region (opt->lanes must
+ * be 0 or 1), one rule launch per family present per sweep, and every
+ * problem gets the bits gmq_integrate's mixed form gives it with lanes = 1.
+ * Returns GMQ_OK when the batch ran (see the per-problem statuses), or an
+ * error. */
 gmq_status gmq_integrate_batch(gmq_context *ctx, int32_t count,
                                const gmq_problem *probs, const double *rel_tols,
                                const gmq_options *opt, int64_t pool_regions,

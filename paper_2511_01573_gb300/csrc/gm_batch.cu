@@ -12,14 +12,20 @@
 //                     chosen per sweep from the list length (the per-region
 //                     work is gm_region64.cuh's, so the choice never changes
 //                     a result)
-//   k_batch_sums      one block per integral: pairwise-tree sums over its
-//                     segment, convergence / sweep-limit test
-//   k_batch_classify  one block per integral: flags, split count, retired
-//                     pairwise-tree sums, round-off guard, per-integral cap
+//   k_batch_sums      tiles of 4096 regions of one integral each
+//                     (persistent grid): pairwise-tree sums per tile; the
+//                     integral's last tile adds the tile sums and tests the
+//                     tolerance / sweep limit
+//   k_batch_classify  per tile: flags, split count, retired pairwise-tree
+//                     sums, round-off guard; the last tile: per-integral
+//                     totals, first child position of every tile, cap
 //   k_batch_scan      one block: new segment offsets (exclusive scan of
-//                     2 n_split over the integrals still running), pool check
-//   k_batch_split     one block per integral: left children then right
-//                     children of its split regions into its new segment
+//                     2 n_split over the integrals still running), pool
+//                     check, the next list's tile table
+//   k_batch_split     per tile: left children then right children of its
+//                     split regions into the integral's new segment
+//   k_batch_restart   initial partitions of evicted integrals let in again
+//   k_batch_commit    one thread per integral: its next segment
 //   k_batch_advance   one thread: swap the lists, count the sweep, and set
 //                     the graph's loop condition (bounded by max_iters)
 // Per-integral sums use the same pairwise tree over the segment as the
@@ -37,9 +43,6 @@ namespace gmq {
 
 namespace {
 
-constexpr int kSegBlock = 1024;  // threads of the per-integral kernels
-constexpr int kSegTile = 4 * kSegBlock;  // regions per tile (4 per thread)
-
 // Pairwise-tree sum of a tile of 4 * blockDim values, 4 consecutive values
 // per thread: ((v0 + v1) + (v2 + v3)) is the first two levels of the tree.
 __device__ __forceinline__ double tile_tree(double v0, double v1, double v2, double v3,
@@ -47,33 +50,63 @@ __device__ __forceinline__ double tile_tree(double v0, double v1, double v2, dou
   return block_tree_sum((v0 + v1) + (v2 + v3), scratch);
 }
 
-// Pairwise-tree sum over the segment values get(i), i in [0, count), by one
-// block: tiles of kSegTile are complete subtrees; tile sums (at most
-// kSegBlock per group) are summed with the same tree, and groups of
-// kSegBlock tiles once more.
-template <class Get>
-__device__ double seg_tree_sum(Get get, long long count, double* scratch, double* tsum,
-                               double* gsum) {
+// The upper levels of an integral's pairwise tree: its tiles' sums ts[0 ..
+// count), in groups of kSegBlock (complete subtrees), then the group sums
+// (at most kSegBlock: segments up to 2^32 regions).  The partials were
+// written by other blocks of this launch: read through L2 (__ldcg).
+__device__ double tiles_tree_sum(const double* ts, long long count, double* scratch,
+                                 double* gsum) {
   const int tid = threadIdx.x;
-  const long long ntiles = (count + kSegTile - 1) / kSegTile;
-  const long long ngroups = (ntiles + kSegBlock - 1) / kSegBlock;
+  const long long ngroups = (count + kSegBlock - 1) / kSegBlock;
   for (long long gi = 0; gi < ngroups; ++gi) {
-    const long long t0 = gi * kSegBlock;
-    const long long t1 = t0 + kSegBlock < ntiles ? t0 + kSegBlock : ntiles;
-    for (long long t = t0; t < t1; ++t) {
-      const long long i = t * kSegTile + 4LL * tid;
-      const double s = tile_tree(i < count ? get(i) : 0.0, i + 1 < count ? get(i + 1) : 0.0,
-                                 i + 2 < count ? get(i + 2) : 0.0, i + 3 < count ? get(i + 3) : 0.0,
-                                 scratch);
-      if (tid == 0) tsum[t - t0] = s;
-    }
-    __syncthreads();
-    const double g = block_tree_sum(tid < t1 - t0 ? tsum[tid] : 0.0, scratch);
+    const long long t = gi * kSegBlock + tid;
+    const double g = block_tree_sum(t < count ? __ldcg(ts + t) : 0.0, scratch);
     if (tid == 0) gsum[gi] = g;
-    __syncthreads();
   }
-  // at most kSegBlock groups (segments up to 2^32 regions)
+  __syncthreads();
   return block_tree_sum(tid < ngroups ? gsum[tid] : 0.0, scratch);
+}
+
+// The integral owning tile t: toff[i] <= t < toff[i + 1] (toff nondecreasing,
+// toff[0] = 0 <= t < toff[count]).
+__device__ __forceinline__ int tile_owner(const long long* toff, int count, long long t) {
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (toff[mid] <= t)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Inclusive scan of one value per thread over a block of kSegBlock threads;
+// *tot receives the block total.
+__device__ long long block_incl_scan(long long v, long long* wsum, long long* tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  const long long incl = x + (warp > 0 ? wsum[warp - 1] : 0);
+  *tot = wsum[31];
+  __syncthreads();
+  return incl;
 }
 
 }  // namespace
@@ -133,6 +166,7 @@ __device__ __forceinline__ void batch_rule_lanes(const BatchArgs& B, double* sme
     if (r >= n_total) break;  // so are the group's later tiles
     __syncwarp(mask);         // the group is done with the previous region's table
     const BatchItem& it = B.items[rid[r]];
+    if (it.paused) continue;  // carried over with last sweep's outputs
     const int d = it.P.d;
     for (int k = lane; k < d; k += T) {
       const double cv = C[(int64_t)k * B.ld + r], hv = H[(int64_t)k * B.ld + r];
@@ -176,7 +210,8 @@ __device__ __forceinline__ void batch_rule_lanes(const BatchArgs& B, double* sme
     if (lane == 0)
       region_finish64(
           o, d, it.w7, it.w5, it.vol_omega, [&](int k) { return tab(kXC, k); },
-          [&](int k) { return tab(kXRows, k); }, B.i7 + r, B.err + r, B.vf + r, B.axis + r);
+          [&](int k) { return tab(kXRows, k); }, B.i7[cur] + r, B.err[cur] + r, B.vf[cur] + r,
+          B.axis[cur] + r);
   }
 }
 
@@ -211,114 +246,163 @@ __global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule(const BatchArgs 
     batch_rule_lanes<1>(B, smem, pairs_all);
 }
 
+// Global sums and convergence test of every integral (persistent grid over
+// the current list's tiles): each tile's pairwise-tree sums of I7 and eps;
+// the last of an integral's tiles to finish (ticket) adds the tile sums
+// with the upper levels of the same tree and tests the tolerance.
 __global__ void __launch_bounds__(kSegBlock) k_batch_sums(const BatchArgs B) {
   __shared__ double scratch[33];
-  __shared__ double tsum[kSegBlock];
   __shared__ double gsum[kSegBlock];
-  BatchItem& it = B.items[blockIdx.x];
-  if ((it.flags & kDone) || it.deferred) return;
-  const long long off = it.off;
-  const double A = seg_tree_sum([&](long long i) { return B.i7[off + i]; }, it.n, scratch, tsum,
-                                gsum);
-  const double E2 = seg_tree_sum([&](long long i) { return B.err[off + i]; }, it.n, scratch, tsum,
-                                 gsum);
-  if (threadIdx.x == 0) {
-    const double I = __dadd_rn(it.I_ret, A);
-    const double E = __dadd_rn(it.E_ret, E2);
-    const double budget = fmax(it.abs_tol, __dmul_rn(it.rel_tol, fabs(I)));
-    it.I = I;
-    it.E = E;
-    it.budget = budget;
-    it.iters += 1;
-    it.regions += it.n;
-    int f = it.flags;
-    if (!isfinite(I) || !isfinite(E))
-      f |= kNonfinite | kDone;
-    else if (E <= budget)
-      f |= kConverged | kDone;
-    else if (it.iters >= B.bs->max_iters)
-      f |= kLastSweep | kDone;
-    it.flags = f;
+  __shared__ int owner, last;
+  const long long* toff = B.tile_off[B.bs->parity];
+  const long long nt = B.bs->n_tiles;
+  for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
+    if (threadIdx.x == 0) owner = tile_owner(toff, B.count, t);
+    __syncthreads();
+    BatchItem& it = B.items[owner];
+    const long long t0 = toff[owner], ntl = toff[owner + 1] - t0;
+    const long long base = (t - t0) * kSegTile;
+    const long long cnt = it.n - base < kSegTile ? it.n - base : kSegTile;
+    const int cur = B.bs->parity;
+    const double* I7 = B.i7[cur] + it.off + base;
+    const double* ER = B.err[cur] + it.off + base;
+    const long long j = 4LL * threadIdx.x;
+    const double a = tile_tree(j < cnt ? I7[j] : 0.0, j + 1 < cnt ? I7[j + 1] : 0.0,
+                               j + 2 < cnt ? I7[j + 2] : 0.0, j + 3 < cnt ? I7[j + 3] : 0.0,
+                               scratch);
+    const double e = tile_tree(j < cnt ? ER[j] : 0.0, j + 1 < cnt ? ER[j + 1] : 0.0,
+                               j + 2 < cnt ? ER[j + 2] : 0.0, j + 3 < cnt ? ER[j + 3] : 0.0,
+                               scratch);
+    if (threadIdx.x == 0) {
+      B.tile_a[t] = a;
+      B.tile_b[t] = e;
+      __threadfence();
+      last = atomicAdd(&it.tk_sum, 1u) == (unsigned)(ntl - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      const double A = tiles_tree_sum(B.tile_a + t0, ntl, scratch, gsum);
+      const double E2 = tiles_tree_sum(B.tile_b + t0, ntl, scratch, gsum);
+      if (threadIdx.x == 0) {
+        it.tk_sum = 0u;
+        const double I = __dadd_rn(it.I_ret, A);
+        const double E = __dadd_rn(it.E_ret, E2);
+        const double budget = fmax(it.abs_tol, __dmul_rn(it.rel_tol, fabs(I)));
+        it.I = I;
+        it.E = E;
+        it.budget = budget;
+        it.iters += 1;
+        it.regions += it.n;
+        int f = it.flags;
+        if (!isfinite(I) || !isfinite(E))
+          f |= kNonfinite | kDone;
+        else if (E <= budget)
+          f |= kConverged | kDone;
+        else if (it.iters >= B.bs->max_iters)
+          f |= kLastSweep | kDone;
+        it.flags = f;
+      }
+    }
+    __syncthreads();
   }
 }
 
+// Classification of every integral's regions (persistent grid over tiles):
+// flags, the tile's split count and its pairwise-tree sums of the retired
+// regions; the last tile of an integral adds them up (retired sums with the
+// upper tree levels), scans the tile counts into the tiles' first child
+// positions, and applies the per-integral cap.
 __global__ void __launch_bounds__(kSegBlock) k_batch_classify(const BatchArgs B) {
   __shared__ double scratch[33];
-  __shared__ double tsum[kSegBlock];
   __shared__ double gsum[kSegBlock];
-  __shared__ long long cnt;
-  BatchItem& it = B.items[blockIdx.x];
-  if ((it.flags & kDone) || it.deferred) return;
-  const long long off = it.off, n = it.n;
-  const double budget = it.budget;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
-  // flags and split count
-  for (long long base = 0; base < n; base += kSegBlock) {
-    const long long i = base + threadIdx.x;
-    int split = 0;
-    if (i < n) {
-      const long long r = off + i;
-      const double i7 = B.i7[r], e = B.err[r];
-      const double thr = (B.classifier == GMQ_LOCAL_REL) ? __dmul_rn(it.rel_tol, fabs(i7))
-                                                         : __dmul_rn(budget, B.vf[r]);
-      const bool retire = (e <= thr) || (e <= __dmul_rn(B.guard, fabs(i7))) || (B.axis[r] & 0x80);
-      split = retire ? 0 : 1;
-      B.flags[r] = (uint8_t)split;
+  __shared__ long long wsum[32];
+  __shared__ int owner, last, skip, cnt_s;
+  const int cur = B.bs->parity;
+  const long long* toff = B.tile_off[cur];
+  const long long nt = B.bs->n_tiles;
+  for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
+    __syncthreads();  // every thread is done with the previous tile's shared values
+    if (threadIdx.x == 0) {
+      owner = tile_owner(toff, B.count, t);
+      skip = (B.items[owner].flags & kDone) ? 1 : 0;
+      cnt_s = 0;
     }
-    const int c = __syncthreads_count(split);
-    if (threadIdx.x == 0) cnt += c;
-  }
-  __syncthreads();
-  // retired sums over the segment (split regions contribute zero)
-  const double ri = seg_tree_sum(
-      [&](long long i) { return B.flags[off + i] ? 0.0 : B.i7[off + i]; }, n, scratch, tsum, gsum);
-  const double re = seg_tree_sum(
-      [&](long long i) { return B.flags[off + i] ? 0.0 : B.err[off + i]; }, n, scratch, tsum, gsum);
-  if (threadIdx.x == 0) {
-    const long long total = cnt;
-    it.n_split = total;
-    int f = it.flags;
-    if (total == 0 || 2 * total > it.cap) {
-      // the integral stops this sweep either way: commit now
-      it.I_ret = __dadd_rn(it.I_ret, ri);
-      it.E_ret = __dadd_rn(it.E_ret, re);
-      f |= (total == 0 ? kAllRetired : kCapExceeded) | kDone;
-    } else {
-      // committed by the scan if the split fits in the pool this sweep
-      it.ret_i = ri;
-      it.ret_e = re;
-    }
-    it.flags = f;
-  }
-}
-
-// Inclusive scan of one value per thread over a block of kSegBlock threads;
-// *tot receives the block total.
-__device__ long long block_incl_scan(long long v, long long* wsum, long long* tot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long x = v;
+    __syncthreads();
+    if (skip) continue;  // block-uniform; the integral stopped at the sums
+    BatchItem& it = B.items[owner];
+    const long long t0 = toff[owner], ntl = toff[owner + 1] - t0;
+    const long long base = (t - t0) * kSegTile;
+    const long long cnt = it.n - base < kSegTile ? it.n - base : kSegTile;
+    const long long r0 = it.off + base;
+    const double budget = it.budget;
+    double ri[4], re[4];
+    int c = 0;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const long long y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    long long w = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
+    for (int q = 0; q < 4; ++q) {
+      const long long j = 4LL * threadIdx.x + q;
+      ri[q] = 0.0;
+      re[q] = 0.0;
+      if (j < cnt) {
+        const long long r = r0 + j;
+        const double i7 = B.i7[cur][r], e = B.err[cur][r];
+        const double thr = (B.classifier == GMQ_LOCAL_REL) ? __dmul_rn(it.rel_tol, fabs(i7))
+                                                           : __dmul_rn(budget, B.vf[cur][r]);
+        const bool retire =
+            (e <= thr) || (e <= __dmul_rn(B.guard, fabs(i7))) || (B.axis[cur][r] & 0x80);
+        B.flags[r] = retire ? 0 : 1;
+        if (retire) {
+          ri[q] = i7;
+          re[q] = e;
+        } else {
+          ++c;
+        }
+      }
     }
-    wsum[lane] = w;
+    if (c) atomicAdd(&cnt_s, c);
+    const double a = tile_tree(ri[0], ri[1], ri[2], ri[3], scratch);  // syncs: cnt_s is final
+    const double e = tile_tree(re[0], re[1], re[2], re[3], scratch);
+    if (threadIdx.x == 0) {
+      B.tile_cnt[t] = cnt_s;
+      B.tile_a[t] = a;
+      B.tile_b[t] = e;
+      __threadfence();
+      last = atomicAdd(&it.tk_cls, 1u) == (unsigned)(ntl - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      // split count and the tiles' first child positions (exclusive scan)
+      long long carry = 0, tot = 0;
+      for (long long b0 = 0; b0 < ntl; b0 += kSegBlock) {
+        const long long q = b0 + threadIdx.x;
+        const long long v = q < ntl ? __ldcg(B.tile_cnt + t0 + q) : 0;
+        const long long incl = block_incl_scan(v, wsum, &tot);
+        if (q < ntl) B.tile_pos[t0 + q] = carry + incl - v;
+        carry += tot;
+      }
+      const double rsum = tiles_tree_sum(B.tile_a + t0, ntl, scratch, gsum);
+      const double esum = tiles_tree_sum(B.tile_b + t0, ntl, scratch, gsum);
+      if (threadIdx.x == 0) {
+        it.tk_cls = 0u;
+        const long long total = carry;
+        it.n_split = total;
+        int f = it.flags;
+        if (total == 0 || 2 * total > it.cap) {
+          // the integral stops this sweep either way: commit now
+          it.I_ret = __dadd_rn(it.I_ret, rsum);
+          it.E_ret = __dadd_rn(it.E_ret, esum);
+          f |= (total == 0 ? kAllRetired : kCapExceeded) | kDone;
+        } else {
+          // committed by the scan if the split fits in the pool this sweep
+          it.ret_i = rsum;
+          it.ret_e = esum;
+        }
+        it.flags = f;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const long long incl = x + (warp > 0 ? wsum[warp - 1] : 0);
-  *tot = wsum[31];
-  __syncthreads();
-  return incl;
 }
 
 // Pool allocation of the next list.  Every running integral first keeps
@@ -455,6 +539,8 @@ __global__ void __launch_bounds__(kSegBlock) k_batch_scan(const BatchArgs B) {
   }
   __syncthreads();
   carry = 0;
+  long long* toff_next = B.tile_off[B.bs->parity ^ 1];
+  long long ttot = 0, tcarry = 0;
   for (int base = 0; base < B.count; base += kSegBlock) {
     const int i = base + tid;
     long long size = 0;
@@ -480,106 +566,148 @@ __global__ void __launch_bounds__(kSegBlock) k_batch_scan(const BatchArgs B) {
       }
     }
     const long long incl = block_incl_scan(size, wsum, &tot);
-    if (i < B.count) B.items[i].noff = carry + incl - size;
+    if (i < B.count) {
+      B.items[i].noff = carry + incl - size;
+      B.items[i].nnext = size;
+      for (int f = 0; f < 7; ++f)
+        if (i == B.fam_item_lo[f]) B.bs->fam_off[B.bs->parity ^ 1][f] = carry + incl - size;
+    }
     carry += tot;
+    // tiles of the next list
+    const long long tiles = (size + kSegTile - 1) / kSegTile;
+    const long long tincl = block_incl_scan(tiles, wsum, &ttot);
+    if (i < B.count) toff_next[i] = tcarry + tincl - tiles;
+    tcarry += ttot;
   }
   __syncthreads();
   if (tid == 0) {
     B.bs->n_next = carry;
     B.bs->active = active_s;
+    B.bs->n_tiles_next = tcarry;
+    toff_next[B.count] = tcarry;
+    for (int f = 0; f < 8; ++f)
+      if (B.fam_item_lo[f] >= B.count) B.bs->fam_off[B.bs->parity ^ 1][f] = carry;
   }
 }
 
+// Bisection (persistent grid over the current list's tiles): the split
+// regions of a tile go, in order, to positions tile_pos[t] + (split regions
+// before them in the tile) of their integral's new segment -- left children
+// first, right children n_split positions later; a paused integral's tile
+// is copied unchanged.
 __global__ void __launch_bounds__(kSegBlock) k_batch_split(const BatchArgs B) {
   __shared__ int wcount[32];
-  __shared__ long long carry_s;
-  BatchItem& it = B.items[blockIdx.x];
-  if ((it.flags & kDone) || it.deferred) return;
+  __shared__ int owner, skip;
   const int cur = B.bs->parity, nxt = cur ^ 1;
+  const long long* toff = B.tile_off[cur];
+  const long long nt = B.bs->n_tiles;
   const double* C = B.c[cur];
   const double* H = B.h[cur];
   double* Co = B.c[nxt];
   double* Ho = B.h[nxt];
   int32_t* rido = B.rid[nxt];
-  const long long off = it.off, n = it.n, ns = it.n_split, noff = it.noff;
-  const int d = it.P.d;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (it.restart) {
-    // an evicted integral starts over: its initial partition
-    for (long long q = tid; q < it.n0; q += kSegBlock) {
-      long long rem = q;
-      for (int k = 0; k < d; ++k) {
-        const long long i = rem % it.s;
-        rem /= it.s;
-        Co[(int64_t)k * B.ld + noff + q] =
-            __dadd_rn(it.lo[k], __dmul_rn((double)(2 * i + 1), it.h0[k]));
-        Ho[(int64_t)k * B.ld + noff + q] = it.h0[k];
-      }
-      rido[noff + q] = (int32_t)blockIdx.x;
-    }
+  for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
     __syncthreads();
     if (tid == 0) {
-      it.off = noff;
-      it.n = it.n0;
-      it.restart = 0;
-    }
-    return;
-  }
-  if (it.paused) {
-    // no room this sweep: carry the segment over unchanged
-    for (long long i = tid; i < n; i += kSegBlock) {
-      for (int k = 0; k < d; ++k) {
-        Co[(int64_t)k * B.ld + noff + i] = C[(int64_t)k * B.ld + off + i];
-        Ho[(int64_t)k * B.ld + noff + i] = H[(int64_t)k * B.ld + off + i];
-      }
-      rido[noff + i] = (int32_t)blockIdx.x;
+      owner = tile_owner(toff, B.count, t);
+      const BatchItem& w = B.items[owner];
+      skip = ((w.flags & kDone) || w.deferred) ? 1 : 0;
     }
     __syncthreads();
-    if (tid == 0) it.off = noff;
-    return;
-  }
-  if (tid == 0) carry_s = 0;
-  __syncthreads();
-  for (long long base = 0; base < n; base += kSegBlock) {
-    const long long i = base + tid;
-    const long long r = off + i;
-    const int f = (i < n) ? (int)B.flags[r] : 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) wcount[warp] = __popc(bal);
-    __syncthreads();
-    int wpre = 0, tot = 0;
-    for (int w = 0; w < kSegBlock / 32; ++w) {
-      if (w < warp) wpre += wcount[w];
-      tot += wcount[w];
-    }
-    if (f) {
-      const long long pos = carry_s + wpre + __popc(bal & ((1u << lane) - 1u));
-      const int ax = B.axis[r] & 0x7f;
-      for (int k = 0; k < d; ++k) {
-        const double cv = C[(int64_t)k * B.ld + r];
-        const double hv = H[(int64_t)k * B.ld + r];
-        double cl = cv, cr = cv, hc = hv;
-        if (k == ax) {
-          hc = __dmul_rn(0.5, hv);
-          cl = __dsub_rn(cv, hc);
-          cr = __dadd_rn(cv, hc);
+    if (skip) continue;
+    const int id = owner;
+    const BatchItem& it = B.items[id];
+    const long long t0 = toff[id];
+    const long long base = (t - t0) * kSegTile;
+    const long long cnt = it.n - base < kSegTile ? it.n - base : kSegTile;
+    const long long r0 = it.off + base, noff = it.noff, ns = it.n_split;
+    const int d = it.P.d;
+    if (it.paused) {
+      // no room this sweep: carry the tile over unchanged, with its rule
+      // outputs (the next sweep does not evaluate it again)
+      for (long long j = tid; j < cnt; j += kSegBlock) {
+        const long long q = noff + base + j, r = r0 + j;
+        for (int k = 0; k < d; ++k) {
+          Co[(int64_t)k * B.ld + q] = C[(int64_t)k * B.ld + r];
+          Ho[(int64_t)k * B.ld + q] = H[(int64_t)k * B.ld + r];
         }
-        Co[(int64_t)k * B.ld + noff + pos] = cl;
-        Ho[(int64_t)k * B.ld + noff + pos] = hc;
-        Co[(int64_t)k * B.ld + noff + ns + pos] = cr;
-        Ho[(int64_t)k * B.ld + noff + ns + pos] = hc;
+        rido[q] = (int32_t)id;
+        B.i7[nxt][q] = B.i7[cur][r];
+        B.err[nxt][q] = B.err[cur][r];
+        B.vf[nxt][q] = B.vf[cur][r];
+        B.axis[nxt][q] = B.axis[cur][r];
       }
-      rido[noff + pos] = (int32_t)blockIdx.x;
-      rido[noff + ns + pos] = (int32_t)blockIdx.x;
+      continue;
     }
-    __syncthreads();
-    if (tid == 0) carry_s += tot;
-    __syncthreads();
+    long long carry = B.tile_pos[t];
+    for (long long b0 = 0; b0 < cnt; b0 += kSegBlock) {
+      const long long j = b0 + tid;
+      const long long r = r0 + j;
+      const int f = (j < cnt) ? (int)B.flags[r] : 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) wcount[warp] = __popc(bal);
+      __syncthreads();
+      int wpre = 0, tot = 0;
+      for (int w = 0; w < kSegBlock / 32; ++w) {
+        if (w < warp) wpre += wcount[w];
+        tot += wcount[w];
+      }
+      if (f) {
+        const long long pos = carry + wpre + __popc(bal & ((1u << lane) - 1u));
+        const int ax = B.axis[cur][r] & 0x7f;
+        for (int k = 0; k < d; ++k) {
+          const double cv = C[(int64_t)k * B.ld + r];
+          const double hv = H[(int64_t)k * B.ld + r];
+          double cl = cv, cr = cv, hc = hv;
+          if (k == ax) {
+            hc = __dmul_rn(0.5, hv);
+            cl = __dsub_rn(cv, hc);
+            cr = __dadd_rn(cv, hc);
+          }
+          Co[(int64_t)k * B.ld + noff + pos] = cl;
+          Ho[(int64_t)k * B.ld + noff + pos] = hc;
+          Co[(int64_t)k * B.ld + noff + ns + pos] = cr;
+          Ho[(int64_t)k * B.ld + noff + ns + pos] = hc;
+        }
+        rido[noff + pos] = (int32_t)id;
+        rido[noff + ns + pos] = (int32_t)id;
+      }
+      carry += tot;
+      __syncthreads();  // wcount is rewritten by the next chunk
+    }
   }
-  if (tid == 0) {
-    it.off = noff;
-    it.n = 2 * ns;
+}
+
+// An evicted integral the scan let in again starts over: its initial
+// partition at its new offset (one block per integral; others return).
+__global__ void k_batch_restart(const BatchArgs B) {
+  const BatchItem& it = B.items[blockIdx.x];
+  if (!it.restart || (it.flags & kDone)) return;
+  const int nxt = B.bs->parity ^ 1;
+  const int d = it.P.d;
+  for (long long q = threadIdx.x; q < it.n0; q += blockDim.x) {
+    long long rem = q;
+    for (int k = 0; k < d; ++k) {
+      const long long i = rem % it.s;
+      rem /= it.s;
+      B.c[nxt][(int64_t)k * B.ld + it.noff + q] =
+          __dadd_rn(it.lo[k], __dmul_rn((double)(2 * i + 1), it.h0[k]));
+      B.h[nxt][(int64_t)k * B.ld + it.noff + q] = it.h0[k];
+    }
+    B.rid[nxt][it.noff + q] = (int32_t)blockIdx.x;
   }
+}
+
+// Every running integral's segment in the next list (one thread each).
+__global__ void k_batch_commit(const BatchArgs B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B.count) return;
+  BatchItem& it = B.items[i];
+  if ((it.flags & kDone) || it.deferred) return;
+  it.off = it.noff;
+  it.n = it.nnext;
+  it.restart = 0;
 }
 
 // Copies of the initial list's regions [0, n0) into [n0, n), cyclically
@@ -600,6 +728,7 @@ __global__ void k_batch_advance(const BatchArgs B) {
   const int used = bs->lanes;
   bs->lane_sweeps[used == 32 ? 2 : (used == 4 ? 1 : 0)] += 1;
   bs->n_total = bs->n_next;
+  bs->n_tiles = bs->n_tiles_next;
   bs->parity ^= 1;
   bs->sweep += 1;
   bs->lanes = batch_lanes_for(B, bs->n_total);
@@ -654,10 +783,12 @@ cudaError_t batch_launch_tile(const BatchArgs& B, long long n0, long long n, cud
 }
 
 cudaError_t batch_launch_rest(const BatchArgs& B, cudaStream_t s) {
-  k_batch_sums<<<B.count, kSegBlock, 0, s>>>(B);
-  k_batch_classify<<<B.count, kSegBlock, 0, s>>>(B);
+  k_batch_sums<<<B.tile_grid, kSegBlock, 0, s>>>(B);
+  k_batch_classify<<<B.tile_grid, kSegBlock, 0, s>>>(B);
   k_batch_scan<<<1, kSegBlock, 0, s>>>(B);
-  k_batch_split<<<B.count, kSegBlock, 0, s>>>(B);
+  k_batch_split<<<B.tile_grid, kSegBlock, 0, s>>>(B);
+  k_batch_restart<<<B.count, 256, 0, s>>>(B);
+  k_batch_commit<<<(B.count + 255) / 256, 256, 0, s>>>(B);
   k_batch_advance<<<1, 1, 0, s>>>(B);
   return cudaGetLastError();
 }

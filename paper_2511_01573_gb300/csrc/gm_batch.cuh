@@ -4,6 +4,7 @@
 #pragma once
 
 #include "gmq_common.cuh"
+#include "gmq_families.cuh"
 
 namespace gmq {
 
@@ -12,6 +13,7 @@ constexpr int kBatchRuleBlock = 128;  // threads per block of the rule kernel
 // Per-integral descriptor (problem, rule constants) and loop state.
 struct BatchItem {
   FamParams P;
+  SmemParams<float> Pf;    // the parameters rounded to FP32 (mixed form)
   double w7[5], w5[5];
   double vol_omega;
   double rel_tol, abs_tol;
@@ -33,6 +35,8 @@ struct BatchItem {
   int deferred;            // 1: evicted, holds no regions, waits for room
   int restart;             // 1: the split kernel writes the initial partition
   int pad;
+  long long nnext;         // regions of the next list (set by the scan)
+  unsigned tk_sum, tk_cls; // tiles of this integral done in the sums / classify kernels
 };
 
 // Batch-wide loop state.
@@ -48,7 +52,17 @@ struct BatchState {
   int evictions;           // integrals evicted to make room (restarted later)
   int lanes;               // lanes per region of this sweep's rule kernel (1, 4, 32)
   int lane_sweeps[3];      // sweeps run with 1, 4 and 32 lanes per region
+  long long n_tiles;       // tiles of the current list (kSegTile regions, one integral each)
+  long long n_tiles_next;  // tiles of the next list
+  long long fam_off[2][8]; // first region of each family in either list; [p][7] = length
 };
+
+// The per-integral sweep kernels work on tiles of kSegTile consecutive
+// regions of one integral (its last tile may be short): tile t of the list
+// of parity p belongs to the integral i with tile_off[p][i] <= t <
+// tile_off[p][i + 1].
+constexpr int kSegBlock = 1024;           // threads of the tile kernels
+constexpr int kSegTile = 4 * kSegBlock;   // regions per tile (4 per thread)
 
 // Arguments of every batch kernel (passed by value).
 struct BatchArgs {
@@ -60,10 +74,12 @@ struct BatchArgs {
   int32_t* rid[2];
   int64_t ld;
   int64_t pool_cap;
-  double* i7;
-  double* err;
-  double* vf;
-  uint8_t* axis;
+  // rule outputs of both lists (a paused integral's outputs move with its
+  // regions, and its regions are not evaluated again)
+  double* i7[2];
+  double* err[2];
+  double* vf[2];
+  uint8_t* axis[2];
   uint8_t* flags;
   int dmax;
   int classifier;
@@ -75,6 +91,16 @@ struct BatchArgs {
   // for lists of at least lanes_t1 regions, 4 from lanes_t4, 32 below
   int forced_lanes;
   long long lanes_t1, lanes_t4;
+  // tiles: per-integral tile offsets of both lists (count + 1 entries each)
+  // and per-tile partial results
+  long long* tile_off[2];
+  double* tile_a;
+  double* tile_b;
+  long long* tile_cnt;
+  long long* tile_pos;
+  int tile_grid;           // blocks of the persistent tile kernels
+  int fam_item_lo[8];      // items are in family order: family f is items
+                           // [fam_item_lo[f], fam_item_lo[f + 1]), [7] = count
 };
 
 __host__ __device__ inline int batch_lanes_for(const BatchArgs& B, long long n) {
@@ -91,6 +117,12 @@ cudaError_t batch_launch_partition(const BatchArgs& B, cudaStream_t s);
 // Rule evaluation of every region of the current list (persistent grid,
 // bs->lanes lanes per region).
 cudaError_t batch_launch_rule(const BatchArgs& B, int grid, cudaStream_t s);
+// Mixed form: rule evaluation of the current list's regions of family FAM
+// (gm_batch_mixed.cuh; one launch per family present in the batch).
+template <int FAM>
+cudaError_t batch_launch_rule_mixed_family(const BatchArgs& B, int grid, cudaStream_t s);
+template <int FAM>
+int batch_rule_mixed_max_blocks_family(int dmax);
 // Fill list 0 positions [n0, n) with copies of its regions [0, n0).
 cudaError_t batch_launch_tile(const BatchArgs& B, long long n0, long long n, cudaStream_t s);
 // Sums, classification, scan, split and loop advance of one sweep.

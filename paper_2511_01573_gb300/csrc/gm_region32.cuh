@@ -1,0 +1,241 @@
+// gm_region32.cuh -- mixed-form evaluation of one region by one thread,
+// shared by the single-integral mixed kernels (gm_rule.cuh) and the batched
+// mixed kernel, so both compute a region with the same operations in the
+// same order.
+//
+// Mixed form: node coordinates are FP64 values rounded to FP32 (the caller's
+// table), the integrand runs in FP32, and the class sums are FP32 with Knuth
+// TwoSum compensation, converted to FP64 before the weights; the fourth
+// differences and everything after the class sums are FP64
+// (region_finish64).
+#pragma once
+
+#include "gm_region64.cuh"
+#include "gmq_common.cuh"
+#include "gmq_families.cuh"
+
+namespace gmq {
+
+// Integrand parameters in registers (compile-time dimension).
+template <int D>
+struct RegParams {
+  float a[D], u[D], b[D];
+  float c0;
+};
+
+// Generic dimension: every node in the order of its definition (centre;
+// per axis +l2, -l2, +l3, -l3; pairs j < k with sign patterns ++, +-, -+,
+// --; sign patterns m = 0 .. 2^d - 1).  P holds FP32 parameters;
+// tab(row, j) is the FP32 node coordinate; pairs as in region_sums64.
+template <int FAM, class PT, class Tab>
+__device__ __forceinline__ void region_mixed_flat(const PT& P, int d, const unsigned short* pairs,
+                                                  const Tab& tab, double ratio, RegionSums& o) {
+  const int b4 = 1 + 4 * d;             // first pair node
+  const int b5 = b4 + 2 * d * (d - 1);  // first sign-pattern node
+  const int N = b5 + (1 << d);
+  Acc<float> S1, S2, S3, S4, S5;
+  double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
+  int kbest = 0;
+  for (int i = 0; i < N; ++i) {
+    int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
+    unsigned m = 0u;
+    if (i == 0) {
+      kind = 1;
+    } else if (i < b4) {
+      const int q = i - 1;
+      k1 = q >> 2;
+      w = q & 3;
+      r1 = kXP2 + w;
+      kind = (w < 2) ? 2 : 3;
+    } else if (i < b5) {
+      const int q = i - b4;
+      const unsigned pr = pairs[q >> 2];
+      k1 = (int)(pr >> 8);
+      k2 = (int)(pr & 255u);
+      r1 = (q & 2) ? kXM3 : kXP3;
+      r2 = (q & 1) ? kXM3 : kXP3;
+      kind = 4;
+    } else {
+      m = (unsigned)(i - b5);
+      kind = 5;
+    }
+    const float v = Family<FAM>::template eval<float>(P, d, [&](int j) -> float {
+      int row;
+      if (kind == 5)
+        row = ((m >> j) & 1u) ? kXM5 : kXP5;
+      else
+        row = (j == k1) ? r1 : ((j == k2) ? r2 : kXC);
+      return tab(row, j);
+    });
+    if (kind == 5) {
+      S5.add(v);
+    } else if (kind == 4) {
+      S4.add(v);
+    } else if (kind == 1) {
+      S1.add(v);
+      f0 = (double)v;
+    } else {
+      if (kind == 2)
+        S2.add(v);
+      else
+        S3.add(v);
+      const double vd = (double)v;
+      if (w == 0) {
+        q0 = vd;
+      } else if (w == 1) {
+        q1 = vd;
+      } else if (w == 2) {
+        q2 = vd;
+      } else {
+        const double two_f0 = __dmul_rn(2.0, f0);
+        const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
+        const double t2 = __dsub_rn(__dadd_rn(q2, vd), two_f0);
+        const double Dk = fabs(__dsub_rn(t1, __dmul_rn(ratio, t2)));
+        if (Dk > dbest) {
+          dbest = Dk;
+          kbest = k1;
+        }
+      }
+    }
+  }
+  o.s1 = S1.value();
+  o.s2 = S2.value();
+  o.s3 = S3.value();
+  o.s4 = S4.value();
+  o.s5 = S5.value();
+  o.f0 = f0;
+  o.dbest = dbest;
+  o.kbest = kbest;
+}
+
+// Dimension D known at compile time (3 <= D <= 16).  The centre, axis and
+// pair nodes (classes 1-4) are read from the table in definition order; the
+// 2^D sign-pattern nodes are walked in Gray-code order over a
+// register-resident node vector: consecutive patterns differ in one
+// coordinate, which moves between c_k + l5 h_k and c_k - l5 h_k by XOR-ing
+// the two FP32 bit patterns.  Eight patterns per step: the coordinates that
+// change inside an aligned group of eight are axes 0, 1, 0, 2, 0, 1, 0
+// (known at compile time); the one changed on entering the group (axis >= 3)
+// is picked with a predicated select.  Pf holds the FP32 parameters (read
+// once into registers).
+template <int FAM, int D, class PT, class Tab>
+__device__ __forceinline__ void region_mixed_walk(const PT& Pf, const Tab& tab, double ratio,
+                                                  RegionSums& o) {
+  static_assert(D >= 3 && D <= 16, "the Gray walk needs D >= 3");
+  constexpr int d = D;
+  RegParams<D> rp;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    rp.a[j] = Pf.a[j];
+    rp.u[j] = Pf.u[j];
+    rp.b[j] = Pf.b[j];
+  }
+  rp.c0 = Pf.c0;
+  const int b4 = 1 + 4 * d;
+  const int b5 = b4 + 2 * d * (d - 1);
+  Acc<float> S1, S2, S3, S4, S5;
+  double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
+  int kbest = 0, pj = 0, pk = 1, pc = 0;
+  // classes 1-4 through the table
+  for (int i = 0; i < b5; ++i) {
+    int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
+    if (i == 0) {
+      kind = 1;
+    } else if (i < b4) {
+      const int q = i - 1;
+      k1 = q >> 2;
+      w = q & 3;
+      r1 = kXP2 + w;
+      kind = (w < 2) ? 2 : 3;
+    } else {
+      const int q = i - b4;
+      k1 = pj;
+      k2 = pk;
+      r1 = (q & 2) ? kXM3 : kXP3;
+      r2 = (q & 1) ? kXM3 : kXP3;
+      kind = 4;
+      if (++pc == 4) {
+        pc = 0;
+        if (++pk == d) {
+          ++pj;
+          pk = pj + 1;
+        }
+      }
+    }
+    const float v = Family<FAM>::template eval<float>(rp, D, [&](int j) -> float {
+      return tab((j == k1) ? r1 : ((j == k2) ? r2 : kXC), j);
+    });
+    if (kind == 4) {
+      S4.add(v);
+    } else if (kind == 1) {
+      S1.add(v);
+      f0 = (double)v;
+    } else {
+      if (kind == 2)
+        S2.add(v);
+      else
+        S3.add(v);
+      const double vd = (double)v;
+      if (w == 0) {
+        q0 = vd;
+      } else if (w == 1) {
+        q1 = vd;
+      } else if (w == 2) {
+        q2 = vd;
+      } else {
+        const double two_f0 = __dmul_rn(2.0, f0);
+        const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
+        const double t2 = __dsub_rn(__dadd_rn(q2, vd), two_f0);
+        const double Dk = fabs(__dsub_rn(t1, __dmul_rn(ratio, t2)));
+        if (Dk > dbest) {
+          dbest = Dk;
+          kbest = k1;
+        }
+      }
+    }
+  }
+  // class 5: Gray-code walk over the 2^D sign patterns in registers
+  float x[D];
+  unsigned tog[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float p5 = tab(kXP5, k), m5 = tab(kXM5, k);
+    x[k] = p5;
+    tog[k] = __float_as_uint(p5) ^ __float_as_uint(m5);
+  }
+  auto XR = [&](int j) -> float { return x[j]; };
+  auto flip = [&](int k) { x[k] = __uint_as_float(__float_as_uint(x[k]) ^ tog[k]); };
+  for (unsigned tb = 0; tb < (1u << D); tb += 8u) {
+    if (tb) {
+      const int jb = __ffs(tb) - 1;
+#pragma unroll
+      for (int k = 3; k < D; ++k)
+        if (k == jb) flip(k);
+    }
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(0);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(1);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(0);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(2);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(0);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(1);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+    flip(0);
+    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
+  }
+  o.s1 = S1.value();
+  o.s2 = S2.value();
+  o.s3 = S3.value();
+  o.s4 = S4.value();
+  o.s5 = S5.value();
+  o.f0 = f0;
+  o.dbest = dbest;
+  o.kbest = kbest;
+}
+
+}  // namespace gmq

@@ -19,7 +19,7 @@
 //      and writes I7, |I7 - I5|, vol / vol(Omega) and the axis byte.
 // FP64 (k_rule64): the per-region work is region_sums64 / region_finish64
 // of gm_region64.cuh, whose fixed summation tree makes the results
-// bit-identical for every T.  Mixed form (k_rule with Real = float): node
+// bit-identical for every T.  Mixed form (k_rule_mixed): node
 // coordinates are formed in FP64 and rounded to FP32, the integrand runs in
 // FP32 and the class sums are FP32 with TwoSum compensation, accumulated in
 // node order per lane and combined over the lanes by a butterfly; class
@@ -30,6 +30,7 @@
 
 #include <type_traits>
 
+#include "gm_region32.cuh"
 #include "gm_region64.cuh"
 #include "gmq_common.cuh"
 #include "gmq_families.cuh"
@@ -47,8 +48,10 @@ inline size_t rule_smem_bytes(int d, int T, int real_bytes) {
   return (bytes + 15) & ~(size_t)15;
 }
 
-template <int FAM, int T, class Real>
-__global__ void __launch_bounds__(kRuleBlock) k_rule(const RuleArgs A) {
+// Mixed form, any dimension, T lanes per region.
+template <int FAM, int T>
+__global__ void __launch_bounds__(kRuleBlock) k_rule_mixed(const RuleArgs A) {
+  using Real = float;
   constexpr int RB = kRuleBlock / T;
   extern __shared__ __align__(16) double smem[];
   const int d = A.P.d;
@@ -106,6 +109,19 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule(const RuleArgs A) {
   const int lane = tid % T;  // lane within the region's group
   const int64_t r = r0 + g;
   const bool active = r < A.n;
+  if constexpr (T == 1) {
+    // one thread per region: the per-region work of the batched kernel
+    if (!active) return;
+    RegionSums o;
+    region_mixed_flat<FAM>(
+        *P, d, pairs, [&](int row, int j) -> float { return xt[(row * d + j) * RB + g]; },
+        A.R.ratio, o);
+    region_finish64(
+        o, d, A.R.w7, A.R.w5, A.R.vol_omega, [&](int k) { return cd[k * RB + g]; },
+        [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
+        A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
+    return;
+  }
   const int N = (int)A.R.nodes;
   const int b4 = 1 + 4 * d;             // first pair node
   const int b5 = b4 + 2 * d * (d - 1);  // first sign-class node
@@ -224,48 +240,23 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule(const RuleArgs A) {
   }
 
   if (active && lane == 0) {
-    // volume, rule values and error estimate
-    double vol = 1.0;
-    for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, hd[k * RB + g]));
-    const double* w7 = A.R.w7;
-    const double* w5 = A.R.w5;
-    double t7 = __dmul_rn(w7[0], s1);
-    t7 = __dadd_rn(t7, __dmul_rn(w7[1], s2));
-    t7 = __dadd_rn(t7, __dmul_rn(w7[2], s3));
-    t7 = __dadd_rn(t7, __dmul_rn(w7[3], s4));
-    t7 = __dadd_rn(t7, __dmul_rn(w7[4], s5));
-    double t5 = __dmul_rn(w5[0], s1);
-    t5 = __dadd_rn(t5, __dmul_rn(w5[1], s2));
-    t5 = __dadd_rn(t5, __dmul_rn(w5[2], s3));
-    t5 = __dadd_rn(t5, __dmul_rn(w5[3], s4));
-    const double i7 = __dmul_rn(vol, t7);
-    const double i5 = __dmul_rn(vol, t5);
-    // split axis: flat differences -> widest axis (lowest index on ties)
-    const double flat_thr = __dadd_rn(__dmul_rn(1e-14, fabs(f0)), 1e-300);
-    int ax = kbest;
-    if (!(dbest > flat_thr)) {
-      ax = 0;
-      double hb = hd[0 * RB + g];
-      for (int k = 1; k < d; ++k) {
-        const double hk = hd[k * RB + g];
-        if (hk > hb) {
-          hb = hk;
-          ax = k;
-        }
-      }
-    }
-    // round-off guard: bisection along ax must move the centre
-    const double cs = cd[ax * RB + g];
-    const double hh = __dmul_rn(0.5, hd[ax * RB + g]);
-    const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
-    A.i7[r] = i7;
-    A.err[r] = fabs(__dsub_rn(i7, i5));
-    if (A.volfrac) A.volfrac[r] = __ddiv_rn(vol, A.R.vol_omega);
-    A.axis[r] = (uint8_t)(ax | (bad ? 0x80 : 0));
+    RegionSums o;
+    o.s1 = s1;
+    o.s2 = s2;
+    o.s3 = s3;
+    o.s4 = s4;
+    o.s5 = s5;
+    o.f0 = f0;
+    o.dbest = dbest;
+    o.kbest = kbest;
+    region_finish64(
+        o, d, A.R.w7, A.R.w5, A.R.vol_omega, [&](int k) { return cd[k * RB + g]; },
+        [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
+        A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
   }
 }
 
-// FP64 rule kernel: same staging as k_rule, per-region work shared with the
+// FP64 rule kernel: same staging as k_rule_mixed, per-region work shared with the
 // batched kernel (gm_region64.cuh).
 template <int FAM, int T>
 __global__ void __launch_bounds__(kRuleBlock) k_rule64(const RuleArgs A) {
@@ -330,22 +321,9 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule64(const RuleArgs A) {
         A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
 }
 
-// Integrand parameters in registers (compile-time dimension).
-template <int D>
-struct RegParams {
-  float a[D], u[D], b[D];
-  float c0;
-};
-
-// Mixed form, one thread per region, dimension D known at compile time.
-// The centre, axis and pair nodes (classes 1-4) go through the shared-memory
-// coordinate table as in k_rule; the 2^D sign-pattern nodes are walked in
-// Gray-code order over a register-resident node vector: consecutive
-// patterns differ in one coordinate, which moves between c_k + l5 h_k and
-// c_k - l5 h_k by XOR-ing the two FP32 bit patterns.  Eight patterns per
-// step: the coordinates that change inside an aligned group of eight are
-// axes 0, 1, 0, 2, 0, 1, 0 (known at compile time); the one changed on
-// entering the group (axis >= 3) is picked with a predicated select.
+// Mixed form, one thread per region, dimension D known at compile time:
+// the sign-pattern nodes are walked in Gray-code order in registers
+// (region_mixed_walk).
 template <int FAM, int D>
 __global__ void __launch_bounds__(kRuleBlock) k_rule_mixed_reg(const RuleArgs A) {
   static_assert(D >= 3 && D <= 16, "gray walk needs D >= 3");
@@ -387,151 +365,13 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_mixed_reg(const RuleArgs A)
   const int g = tid;
   const int64_t r = r0 + g;
   if (r >= A.n) return;
-  RegParams<D> rp;
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    rp.a[j] = P->a[j];
-    rp.u[j] = P->u[j];
-    rp.b[j] = P->b[j];
-  }
-  rp.c0 = P->c0;
-  const int b4 = 1 + 4 * d;
-  const int b5 = b4 + 2 * d * (d - 1);
-  const double ratio = A.R.ratio;
-  Acc<float> S1, S2, S3, S4, S5;
-  double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
-  int kbest = 0, pj = 0, pk = 1, pc = 0;
-  // classes 1-4 through the table
-  for (int i = 0; i < b5; ++i) {
-    int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
-    if (i == 0) {
-      kind = 1;
-    } else if (i < b4) {
-      const int q = i - 1;
-      k1 = q >> 2;
-      w = q & 3;
-      r1 = kXP2 + w;
-      kind = (w < 2) ? 2 : 3;
-    } else {
-      const int q = i - b4;
-      k1 = pj;
-      k2 = pk;
-      r1 = (q & 2) ? kXM3 : kXP3;
-      r2 = (q & 1) ? kXM3 : kXP3;
-      kind = 4;
-      if (++pc == 4) {
-        pc = 0;
-        if (++pk == d) {
-          ++pj;
-          pk = pj + 1;
-        }
-      }
-    }
-    auto X = [&](int j) -> float {
-      const int row = (j == k1) ? r1 : ((j == k2) ? r2 : kXC);
-      return xt[(row * d + j) * RB + g];
-    };
-    const float v = Family<FAM>::template eval<float>(rp, D, X);
-    if (kind == 4) {
-      S4.add(v);
-    } else if (kind == 1) {
-      S1.add(v);
-      f0 = (double)v;
-    } else {
-      if (kind == 2)
-        S2.add(v);
-      else
-        S3.add(v);
-      const double vd = (double)v;
-      if (w == 0) {
-        q0 = vd;
-      } else if (w == 1) {
-        q1 = vd;
-      } else if (w == 2) {
-        q2 = vd;
-      } else {
-        const double two_f0 = __dmul_rn(2.0, f0);
-        const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
-        const double t2 = __dsub_rn(__dadd_rn(q2, vd), two_f0);
-        const double Dk = fabs(__dsub_rn(t1, __dmul_rn(ratio, t2)));
-        if (Dk > dbest) {
-          dbest = Dk;
-          kbest = k1;
-        }
-      }
-    }
-  }
-  // class 5: Gray-code walk over the 2^D sign patterns in registers
-  float x[D];
-  unsigned tog[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const float p5 = xt[(kXP5 * d + k) * RB + g], m5 = xt[(kXM5 * d + k) * RB + g];
-    x[k] = p5;
-    tog[k] = __float_as_uint(p5) ^ __float_as_uint(m5);
-  }
-  auto XR = [&](int j) -> float { return x[j]; };
-  auto flip = [&](int k) { x[k] = __uint_as_float(__float_as_uint(x[k]) ^ tog[k]); };
-  for (unsigned tb = 0; tb < (1u << D); tb += 8u) {
-    if (tb) {
-      const int jb = __ffs(tb) - 1;
-#pragma unroll
-      for (int k = 3; k < D; ++k)
-        if (k == jb) flip(k);
-    }
-    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
-    flip(0);
-    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
-    flip(1);
-    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
-    flip(0);
-    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
-    flip(2);
-    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
-    flip(0);
-    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
-    flip(1);
-    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
-    flip(0);
-    S5.add(Family<FAM>::template eval<float>(rp, D, XR));
-  }
-  const double s1 = S1.value(), s2 = S2.value(), s3 = S3.value(), s4 = S4.value(),
-               s5 = S5.value();
-  double vol = 1.0;
-  for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, hd[k * RB + g]));
-  const double* w7 = A.R.w7;
-  const double* w5 = A.R.w5;
-  double t7 = __dmul_rn(w7[0], s1);
-  t7 = __dadd_rn(t7, __dmul_rn(w7[1], s2));
-  t7 = __dadd_rn(t7, __dmul_rn(w7[2], s3));
-  t7 = __dadd_rn(t7, __dmul_rn(w7[3], s4));
-  t7 = __dadd_rn(t7, __dmul_rn(w7[4], s5));
-  double t5 = __dmul_rn(w5[0], s1);
-  t5 = __dadd_rn(t5, __dmul_rn(w5[1], s2));
-  t5 = __dadd_rn(t5, __dmul_rn(w5[2], s3));
-  t5 = __dadd_rn(t5, __dmul_rn(w5[3], s4));
-  const double i7 = __dmul_rn(vol, t7);
-  const double i5 = __dmul_rn(vol, t5);
-  const double flat_thr = __dadd_rn(__dmul_rn(1e-14, fabs(f0)), 1e-300);
-  int ax = kbest;
-  if (!(dbest > flat_thr)) {
-    ax = 0;
-    double hb = hd[0 * RB + g];
-    for (int k = 1; k < d; ++k) {
-      const double hk = hd[k * RB + g];
-      if (hk > hb) {
-        hb = hk;
-        ax = k;
-      }
-    }
-  }
-  const double cs = cd[ax * RB + g];
-  const double hh = __dmul_rn(0.5, hd[ax * RB + g]);
-  const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
-  A.i7[r] = i7;
-  A.err[r] = fabs(__dsub_rn(i7, i5));
-  if (A.volfrac) A.volfrac[r] = __ddiv_rn(vol, A.R.vol_omega);
-  A.axis[r] = (uint8_t)(ax | (bad ? 0x80 : 0));
+  RegionSums o;
+  region_mixed_walk<FAM, D>(
+      *P, [&](int row, int j) -> float { return xt[(row * d + j) * RB + g]; }, A.R.ratio, o);
+  region_finish64(
+      o, d, A.R.w7, A.R.w5, A.R.vol_omega, [&](int k) { return cd[k * RB + g]; },
+      [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
+      A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
 }
 
 template <int FAM, int D>
@@ -579,7 +419,7 @@ cudaError_t launch_rule_t(const RuleArgs& A, cudaStream_t s) {
   if constexpr (std::is_same<Real, double>::value)
     kern = k_rule64<FAM, T>;
   else
-    kern = k_rule<FAM, T, Real>;
+    kern = k_rule_mixed<FAM, T>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -1,8 +1,10 @@
-// gm_rule_inst.cu -- instantiates the rule kernel (FP64 and mixed) and the
-// adjoint kernel for one integrand family.  The build compiles this file
+// gm_rule_inst.cu -- instantiates the rule kernels (FP64 and mixed, single
+// integral and batched mixed) and the adjoint kernel for one integrand
+// family.  The build compiles this file
 // once per family with -DGMQ_FAM=<code>, so the instantiations compile in
 // parallel.
 #include "gm_adjoint.cuh"
+#include "gm_batch_mixed.cuh"
 #include "gm_rule.cuh"
 
 #ifndef GMQ_FAM
@@ -12,4 +14,5 @@
 namespace gmq {
 GMQ_DEFINE_RULE_FAMILY(GMQ_FAM)
 GMQ_DEFINE_GRAD_FAMILY(GMQ_FAM)
+GMQ_DEFINE_BATCH_MIXED_FAMILY(GMQ_FAM)
 }  // namespace gmq

@@ -46,7 +46,7 @@ struct gmq_context {
   size_t ext_bytes = 0;
   char* scratch = nullptr;
   size_t scratch_bytes = 0;
-  DevStatus* h_status = nullptr;  // pinned
+  DevStatus* h_status = nullptr;  // pinned, large enough for a BatchState too
   std::vector<gmq_sweep> trace;
   int64_t launches = 0;
   // final partition of the last integration (GMQ_KEEP_PARTITION)
@@ -240,6 +240,31 @@ cudaError_t launch_rule(int fam, int precision, int T, const RuleArgs& A, cudaSt
   }
 }
 
+cudaError_t batch_launch_rule_mixed(int fam, const BatchArgs& B, int grid, cudaStream_t s) {
+  switch (fam) {
+    case GMQ_OSCILLATORY: return batch_launch_rule_mixed_family<GMQ_OSCILLATORY>(B, grid, s);
+    case GMQ_PRODUCT_PEAK: return batch_launch_rule_mixed_family<GMQ_PRODUCT_PEAK>(B, grid, s);
+    case GMQ_CORNER_PEAK: return batch_launch_rule_mixed_family<GMQ_CORNER_PEAK>(B, grid, s);
+    case GMQ_GAUSSIAN: return batch_launch_rule_mixed_family<GMQ_GAUSSIAN>(B, grid, s);
+    case GMQ_C0: return batch_launch_rule_mixed_family<GMQ_C0>(B, grid, s);
+    case GMQ_DISCONTINUOUS: return batch_launch_rule_mixed_family<GMQ_DISCONTINUOUS>(B, grid, s);
+    case GMQ_POLY_SUMSQ11: return batch_launch_rule_mixed_family<GMQ_POLY_SUMSQ11>(B, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int batch_rule_mixed_max_blocks(int fam, int dmax) {
+  switch (fam) {
+    case GMQ_OSCILLATORY: return batch_rule_mixed_max_blocks_family<GMQ_OSCILLATORY>(dmax);
+    case GMQ_PRODUCT_PEAK: return batch_rule_mixed_max_blocks_family<GMQ_PRODUCT_PEAK>(dmax);
+    case GMQ_CORNER_PEAK: return batch_rule_mixed_max_blocks_family<GMQ_CORNER_PEAK>(dmax);
+    case GMQ_GAUSSIAN: return batch_rule_mixed_max_blocks_family<GMQ_GAUSSIAN>(dmax);
+    case GMQ_C0: return batch_rule_mixed_max_blocks_family<GMQ_C0>(dmax);
+    case GMQ_DISCONTINUOUS: return batch_rule_mixed_max_blocks_family<GMQ_DISCONTINUOUS>(dmax);
+    default: return batch_rule_mixed_max_blocks_family<GMQ_POLY_SUMSQ11>(dmax);
+  }
+}
+
 // Name of the last CUDA error a call of this thread turned into a status.
 thread_local const char* g_last_cuda_error = "cudaSuccess";
 
@@ -399,7 +424,10 @@ gmq_status gmq_create(gmq_context** out, int device, size_t pool_bytes_hint) {
     return GMQ_ERR_CUDA;
   }
   ctx->sm_count = prop.multiProcessorCount;
-  if (cudaHostAlloc((void**)&ctx->h_status, sizeof(DevStatus), cudaHostAllocDefault) != cudaSuccess) {
+  // pinned status buffer: one sweep's DevStatus, or a batch's BatchState
+  constexpr size_t kHostStatusBytes =
+      sizeof(DevStatus) > sizeof(BatchState) ? sizeof(DevStatus) : sizeof(BatchState);
+  if (cudaHostAlloc((void**)&ctx->h_status, kHostStatusBytes, cudaHostAllocDefault) != cudaSuccess) {
     delete ctx;
     return GMQ_ERR_CUDA;
   }
@@ -926,26 +954,53 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     return GMQ_ERR_INVALID;
   const int64_t cap = opt->max_regions;  // per problem
   if (!(opt->abs_tol >= 0.0) || cap < 1 || cap > kMaxRegions || opt->init_splits < 0 ||
-      opt->max_iters < 0 || (opt->flags & ~GMQ_BATCH_HOST_LOOP) || opt->precision != GMQ_FP64 ||
+      opt->max_iters < 0 || (opt->flags & ~GMQ_BATCH_HOST_LOOP) ||
+      (opt->precision != GMQ_FP64 && opt->precision != GMQ_MIXED) ||
       (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32) ||
+      (opt->precision == GMQ_MIXED && opt->lanes > 1) ||
       (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL))
     return GMQ_ERR_INVALID;
   std::memset(results, 0, sizeof(gmq_result) * (size_t)count);
   const int max_iters = opt->max_iters > 0 ? opt->max_iters : 1000;
   // per-problem descriptors and the initial segments
   std::vector<BatchItem> items((size_t)count);
+  bool fam_present[7] = {};
+  const bool mixed = opt->precision == GMQ_MIXED;
   int dmax = 1;
   int64_t total = 0;
-  for (int32_t i = 0; i < count; ++i) {
+  // the batch runs in (family, dimension) order, so each family's regions
+  // form one contiguous range of every list (the mixed form launches its
+  // rule kernel per family over that range); results return in the
+  // caller's order, and the order changes no result
+  for (int32_t i = 0; i < count; ++i)
+    if (validate_problem(&probs[i]) != GMQ_OK) return GMQ_ERR_INVALID;
+  std::vector<int32_t> perm((size_t)count);
+  for (int32_t i = 0; i < count; ++i) perm[(size_t)i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) {
+    if (probs[x].family != probs[y].family) return probs[x].family < probs[y].family;
+    return probs[x].dim < probs[y].dim;
+  });
+  int fam_item_lo[8];
+  for (int f = 0; f <= 7; ++f) fam_item_lo[f] = count;
+  for (int32_t k = count - 1; k >= 0; --k)
+    for (int f = 0; f <= probs[perm[(size_t)k]].family; ++f) fam_item_lo[f] = k;
+  for (int32_t k = 0; k < count; ++k) {
+    const int32_t i = perm[(size_t)k];
     const gmq_problem* p = &probs[i];
-    if (validate_problem(p) != GMQ_OK) return GMQ_ERR_INVALID;
     const double tol = rel_tols ? rel_tols[i] : opt->rel_tol;
     if (!(tol >= 0.0)) return GMQ_ERR_INVALID;
     const int d = p->dim;
     dmax = std::max(dmax, d);
-    BatchItem& it = items[(size_t)i];
+    BatchItem& it = items[(size_t)k];
     std::memset(&it, 0, sizeof(it));
     it.P = fam_params(p);
+    for (int k = 0; k < GMQ_MAX_DIM; ++k) {
+      it.Pf.a[k] = (float)it.P.a[k];
+      it.Pf.u[k] = (float)it.P.u[k];
+      it.Pf.b[k] = (float)it.P.b[k];
+    }
+    it.Pf.c0 = (float)it.P.c0;
+    fam_present[p->family] = true;
     const RuleConst R = rule_const(d, p->lo, p->hi);
     for (int c = 0; c < 5; ++c) {
       it.w7[c] = R.w7[c];
@@ -1008,13 +1063,23 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   const size_t o_h1 = p; p += list;
   const size_t o_r0 = p; p += ids;
   const size_t o_r1 = p; p += ids;
-  const size_t o_i7 = p; p += vec;
-  const size_t o_err = p; p += vec;
-  const size_t o_vf = p; p += vec;
-  const size_t o_ax = p; p += bytes;
+  const size_t o_i7 = p; p += 2 * vec;
+  const size_t o_err = p; p += 2 * vec;
+  const size_t o_vf = p; p += 2 * vec;
+  const size_t o_ax = p; p += 2 * bytes;
   const size_t o_fl = p; p += bytes;
   const size_t o_it = p; p += align256(sizeof(BatchItem) * (size_t)count);
   const size_t o_bs = p; p += align256(sizeof(BatchState));
+  // tiles: at most pool / kSegTile full tiles plus one short tile per integral
+  const int64_t tile_cap = pool / kSegTile + count + 1;
+  const size_t toffs = align256(sizeof(long long) * ((size_t)count + 1));
+  const size_t tvec = align256(sizeof(double) * (size_t)tile_cap);
+  const size_t o_to0 = p; p += toffs;
+  const size_t o_to1 = p; p += toffs;
+  const size_t o_ta = p; p += tvec;
+  const size_t o_tb = p; p += tvec;
+  const size_t o_tc = p; p += tvec;
+  const size_t o_tp = p; p += tvec;
   char* base = nullptr;
   gmq_status ps = ensure_pool(ctx, p, &base);
   if (ps != GMQ_OK) return ps;
@@ -1033,14 +1098,23 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   B.rid[1] = (int32_t*)(base + o_r1);
   B.ld = ld;
   B.pool_cap = pool;
-  B.i7 = (double*)(base + o_i7);
-  B.err = (double*)(base + o_err);
-  B.vf = (double*)(base + o_vf);
-  B.axis = (uint8_t*)(base + o_ax);
+  for (int q = 0; q < 2; ++q) {
+    B.i7[q] = (double*)(base + o_i7 + q * vec);
+    B.err[q] = (double*)(base + o_err + q * vec);
+    B.vf[q] = (double*)(base + o_vf + q * vec);
+    B.axis[q] = (uint8_t*)(base + o_ax + q * bytes);
+  }
   B.flags = (uint8_t*)(base + o_fl);
   B.dmax = dmax;
+  B.tile_off[0] = (long long*)(base + o_to0);
+  B.tile_off[1] = (long long*)(base + o_to1);
+  B.tile_a = (double*)(base + o_ta);
+  B.tile_b = (double*)(base + o_tb);
+  B.tile_cnt = (long long*)(base + o_tc);
+  B.tile_pos = (long long*)(base + o_tp);
+  B.tile_grid = 2 * ctx->sm_count;
   B.classifier = opt->classifier;
-  B.guard = kGuardFp64;
+  B.guard = mixed ? kGuardMixed : kGuardFp64;
   const RuleConst R0 = rule_const(1, nullptr, nullptr);
   B.lam2 = R0.lam2;
   B.lam3 = R0.lam3;
@@ -1054,6 +1128,28 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   // pauses (pool full) add sweeps; the device loop is bounded all the same
   bs0.max_sweeps = 4 * max_iters;
   cudaStream_t strm = ctx->stream;
+  // the initial list's tile table
+  std::vector<long long> toff0((size_t)count + 1);
+  long long ntiles = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    toff0[(size_t)i] = ntiles;
+    ntiles += (items[(size_t)i].n + kSegTile - 1) / kSegTile;
+  }
+  toff0[(size_t)count] = ntiles;
+  bs0.n_tiles = ntiles;
+  // first region of each family in the initial list
+  {
+    long long pos = 0;
+    int f = 0;
+    for (int32_t k = 0; k <= count; ++k) {
+      while (f < 8 && fam_item_lo[f] == k) bs0.fam_off[0][f++] = pos;
+      if (k < count) pos += items[(size_t)k].n;
+    }
+    while (f < 8) bs0.fam_off[0][f++] = pos;
+  }
+  for (int f = 0; f < 8; ++f) B.fam_item_lo[f] = fam_item_lo[f];
+  GMQ_CK(cudaMemcpyAsync(B.tile_off[0], toff0.data(), sizeof(long long) * ((size_t)count + 1),
+                         cudaMemcpyHostToDevice, strm));
   GMQ_CK(cudaMemcpyAsync(B.items, items.data(), sizeof(BatchItem) * (size_t)count,
                          cudaMemcpyHostToDevice, strm));
   GMQ_CK(cudaMemcpyAsync(B.bs, &bs0, sizeof(BatchState), cudaMemcpyHostToDevice, strm));
@@ -1066,9 +1162,29 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   // only write rule outputs, which the first sweep overwrites)
   gmq_batch_info info;
   std::memset(&info, 0, sizeof(info));
-  const int grid = ctx->sm_count * batch_rule_max_blocks(dmax);  // also sets the smem limit
-  B.forced_lanes = opt->lanes;
-  if (!opt->lanes && !ctx->tuned[dmax]) {
+  // mixed form: one rule launch per family present, one lane per region
+  int grid = 0;
+  int fam_grid[7] = {};
+  if (mixed) {
+    for (int f = 0; f < 7; ++f)
+      if (fam_present[f]) fam_grid[f] = ctx->sm_count * batch_rule_mixed_max_blocks(f, dmax);
+  } else {
+    grid = ctx->sm_count * batch_rule_max_blocks(dmax);  // also sets the smem limit
+  }
+  auto launch_rule_step = [&](cudaStream_t st) -> cudaError_t {
+    if (!mixed) return batch_launch_rule(B, grid, st);
+    for (int f = 0; f < 7; ++f) {
+      if (!fam_present[f]) continue;
+      const cudaError_t e = batch_launch_rule_mixed(f, B, fam_grid[f], st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  int rule_launches = 0;
+  for (int f = 0; f < 7; ++f) rule_launches += fam_present[f] ? 1 : 0;
+  if (!mixed) rule_launches = 1;
+  B.forced_lanes = mixed ? 1 : opt->lanes;
+  if (!mixed && !opt->lanes && !ctx->tuned[dmax]) {
     const int64_t wave = (int64_t)grid * kBatchRuleBlock;  // regions of one T = 1 wave
     int64_t lens[5];
     int nl = 0;
@@ -1131,9 +1247,11 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   GMQ_CK(cudaMemcpyAsync(B.bs, &bs0, sizeof(BatchState), cudaMemcpyHostToDevice, strm));
   info.rule_block = kBatchRuleBlock;
   info.rule_grid = grid;
-  info.forced_lanes = opt->lanes;
-  info.lanes_t1 = opt->lanes ? 0 : B.lanes_t1;
-  info.lanes_t4 = opt->lanes ? 0 : B.lanes_t4;
+  if (mixed)
+    for (int f = 0; f < 7; ++f) info.rule_grid = std::max(info.rule_grid, fam_grid[f]);
+  info.forced_lanes = B.forced_lanes;
+  info.lanes_t1 = B.forced_lanes ? 0 : B.lanes_t1;
+  info.lanes_t4 = B.forced_lanes ? 0 : B.lanes_t4;
 
   BatchState hs;
   if (!(opt->flags & GMQ_BATCH_HOST_LOOP)) {
@@ -1165,7 +1283,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
         e = cudaStreamBeginCaptureToGraph(ctx->capture_stream, body, nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t e1 = batch_launch_rule(B, grid, ctx->capture_stream);
+        cudaError_t e1 = launch_rule_step(ctx->capture_stream);
         cudaError_t e2 = batch_launch_rest(B, ctx->capture_stream);
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(ctx->capture_stream, &captured);
@@ -1184,9 +1302,9 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     B.use_cond = 0;
     for (;;) {
       for (int k = 0; k < 8; ++k) {
-        GMQ_CK(batch_launch_rule(B, grid, strm));
+        GMQ_CK(launch_rule_step(strm));
         GMQ_CK(batch_launch_rest(B, strm));
-        ctx->launches += 6;
+        ctx->launches += 7 + rule_launches;
       }
       GMQ_CK(cudaMemcpyAsync(ctx->h_status, B.bs, sizeof(BatchState), cudaMemcpyDeviceToHost,
                              strm));
@@ -1205,9 +1323,9 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   info.evictions = hs.evictions;
   for (int m = 0; m < 3; ++m) info.lane_sweeps[m] = hs.lane_sweeps[m];
   ctx->last_batch = info;
-  for (int32_t i = 0; i < count; ++i) {
-    const BatchItem& it = items[(size_t)i];
-    gmq_result& r = results[i];
+  for (int32_t k = 0; k < count; ++k) {
+    const BatchItem& it = items[(size_t)k];
+    gmq_result& r = results[perm[(size_t)k]];
     r.integral = it.I;
     r.error = it.E;
     r.regions_evaluated = it.regions;

@@ -300,20 +300,20 @@ class Context:
 
     def integrate_batch(self, problems, rel_tols=None, max_regions=1 << 24, abs_tol=1e-16,
                         init_splits=0, max_iters=0, classifier=VOLUME_SHARE, host_loop=False,
-                        pool_regions=0, lanes=0):
+                        pool_regions=0, lanes=0, precision=FP64):
         """Integrate many problems in one device-resident loop.  problems:
         objects with family, dim, a, u (and optional lo, hi, rel_tol).
         max_regions is each problem's cap, pool_regions the shared pool (0:
         the library's default); lanes 1, 4 or 32 fixes the rule kernel's
-        lanes per region (0: autotuned per sweep).  Returns one
-        IntegrateResult per problem."""
+        lanes per region (0: autotuned per sweep; MIXED runs one lane per
+        region).  Returns one IntegrateResult per problem."""
         hs = [_ProblemHandle(p.family, p.a, p.u, getattr(p, "lo", None), getattr(p, "hi", None),
                              p.dim) for p in problems]
         arr = (Problem * len(hs))(*[h.s for h in hs])
         if rel_tols is None:
             rel_tols = [p.rel_tol for p in problems]
         tols = _f64(rel_tols, len(hs))
-        o = Options(0.0, abs_tol, max_regions, init_splits, max_iters, FP64, classifier, lanes,
+        o = Options(0.0, abs_tol, max_regions, init_splits, max_iters, precision, classifier, lanes,
                     BATCH_HOST_LOOP if host_loop else 0)
         res = (Result * len(hs))()
         _check("gmq_integrate_batch", lib().gmq_integrate_batch(self.h, len(hs), arr, _ptr(tols),

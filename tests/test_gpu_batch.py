@@ -67,6 +67,42 @@ def test_batch_forced_lane_mappings(gpu_ctx, lanes):
         assert r.integral == s.integral and r.error == s.error
 
 
+def _mixed_precision_batch():
+    probs = _mixed_batch(n=32, seed=17)
+    extra = [(G.PRODUCT_PEAK, 1, 1e-6), (G.GAUSSIAN, 12, 1e-3), (G.C0, 13, 1e-2),
+             (G.DISCONTINUOUS, 3, 1e-3), (G.POLY_SUMSQ11, 2, 1e-5), (G.OSCILLATORY, 10, 1e-4)]
+    for i, (fam, d, tol) in enumerate(extra):
+        a, u = G.seed_genz(900 + i, fam, d, G.GENZ_TARGET_SUM.get(fam, 2.0))
+        if fam == G.PRODUCT_PEAK:
+            a, u = G.seed_genz(900 + i, fam, d, 5.0)
+        if fam == G.DISCONTINUOUS:
+            u = 0.3 + 0.6 * u
+        probs.append(G.Problem(fam, d, a, u, tol))
+    return probs
+
+
+@pytest.mark.parametrize("host_loop", [False, True])
+def test_batch_mixed_equals_single_mixed(gpu_ctx, host_loop):
+    """Mixed form: one lane per region, the single path's per-region code
+    (register walk for 3 <= d <= 12, generic otherwise), so every problem
+    gets the bits of gmq_integrate's mixed form with lanes = 1."""
+    from paper_2511_01573_gb300 import gmq
+    probs = _mixed_precision_batch()
+    cap = 1 << 20
+    res = gpu_ctx.integrate_batch(probs, max_regions=cap, precision=gmq.MIXED,
+                                  host_loop=host_loop)
+    info = gpu_ctx.last_batch_info()
+    assert info["forced_lanes"] == 1 and info["lane_sweeps"][0] == info["sweeps"]
+    for p, r in zip(probs, res):
+        s = gpu_ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=cap, lanes=1,
+                              precision=gmq.MIXED)
+        assert (r.status, r.iterations, r.regions_evaluated) == (s.status, s.iterations,
+                                                                 s.regions_evaluated), p.label
+        assert r.integral == s.integral and r.error == s.error
+    with pytest.raises(gmq.GmqError):
+        gpu_ctx.integrate_batch(probs[:4], precision=gmq.MIXED, lanes=4)
+
+
 def test_batch_against_oracle_sample(oracle, gpu_ctx):
     probs = _mixed_batch(n=12, seed=11)
     res = gpu_ctx.integrate_batch(probs, max_regions=1 << 20)
