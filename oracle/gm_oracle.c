@@ -288,6 +288,109 @@ void or_rule_regions(const or_family *fam, int64_t n, const double *c,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Tensor-product Gauss-Kronrod (7, 15) rule (paper Sec. 3).                */
+/* ------------------------------------------------------------------------ */
+
+int64_t or_gk_nodes(int d) {
+  int64_t n = 1;
+  int k;
+  for (k = 0; k < d; ++k) n *= 15;
+  return n;
+}
+
+void or_rule_gk(int d, const double *c, const double *h, or_integrand f,
+                const void *ctx, const double *gk, double *E, or_gk_out *out) {
+  const double *node = gk, *wk = gk + 15, *wg = gk + 30;
+  int64_t nn = or_gk_nodes(d), i, q;
+  int dig[16];
+  double x[16], Ek[16];
+  double hprod = 1.0, vol = 1.0, SK = 0.0, SG = 0.0, A = 0.0, v, wkp, wgp, wo;
+  int j, k;
+  for (k = 0; k < d; ++k) {
+    hprod = hprod * h[k];
+    vol = vol * (2.0 * h[k]);
+    Ek[k] = 0.0;
+  }
+  for (i = 0; i < nn; ++i) {
+    q = i;
+    for (k = 0; k < d; ++k) {
+      dig[k] = (int)(q % 15);
+      q /= 15;
+      x[k] = fma(node[dig[k]], h[k], c[k]);
+    }
+    v = f(x, d, ctx);
+    wkp = 1.0;
+    wgp = 1.0;
+    for (k = 0; k < d; ++k) {
+      wkp = wkp * wk[dig[k]];
+      wgp = wgp * wg[dig[k]];
+    }
+    SK = SK + wkp * v;
+    SG = SG + wgp * v;
+    A = A + wkp * fabs(v);
+    for (k = 0; k < d; ++k) {
+      wo = 1.0;
+      for (j = 0; j < d; ++j)
+        if (j != k) wo = wo * wk[dig[j]];
+      Ek[k] = Ek[k] + wo * (wk[dig[k]] - wg[dig[k]]) * v;
+    }
+  }
+  out->ik = hprod * SK;
+  out->ig = hprod * SG;
+  out->err = fabs(out->ik - out->ig);
+  out->vol = vol;
+  out->scale = hprod * A;
+  for (k = 0; k < d; ++k) Ek[k] = hprod * fabs(Ek[k]);
+  if (E)
+    for (k = 0; k < d; ++k) E[k] = Ek[k];
+  {
+    int best = 0, second = -1, hb = 0;
+    double flat_thr = 1e-11 * out->scale + 1e-300, band;
+    for (k = 1; k < d; ++k)
+      if (Ek[k] > Ek[best]) best = k;
+    for (k = 0; k < d; ++k)
+      if (k != best && (second < 0 || Ek[k] > Ek[second])) second = k;
+    band = 1e-12 * Ek[best] + 1e-12 * out->scale;
+    out->axis_tie = 0;
+    if (second >= 0 && Ek[best] - Ek[second] <= band) out->axis_tie = 1;
+    if (fabs(Ek[best] - flat_thr) <= band) out->axis_tie = 1;
+    out->flat = Ek[best] <= flat_thr;
+    if (out->flat) {
+      for (k = 1; k < d; ++k)
+        if (h[k] > h[hb]) hb = k;
+      out->axis = hb;
+    } else {
+      out->axis = best;
+    }
+  }
+  {
+    int s = out->axis;
+    double hh = 0.5 * h[s];
+    out->split_bad = (hh == 0.0) || (c[s] - hh == c[s]) || (c[s] + hh == c[s]);
+  }
+}
+
+void or_rule_gk_regions(const or_family *fam, int64_t n, const double *c,
+                        const double *h, const double *gk, double *ik,
+                        double *ig, double *err, double *vol, int32_t *axis,
+                        int32_t *axis_tie, int32_t *split_bad, double *scale) {
+  int64_t r;
+  int d = fam->d;
+  for (r = 0; r < n; ++r) {
+    or_gk_out o;
+    or_rule_gk(d, c + r * d, h + r * d, or_family_eval, fam, gk, NULL, &o);
+    if (ik) ik[r] = o.ik;
+    if (ig) ig[r] = o.ig;
+    if (err) err[r] = o.err;
+    if (vol) vol[r] = o.vol;
+    if (axis) axis[r] = o.axis;
+    if (axis_tie) axis_tie[r] = o.axis_tie;
+    if (split_bad) split_bad[r] = o.split_bad;
+    if (scale) scale[r] = o.scale;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Global sums.                                                             */
 /* ------------------------------------------------------------------------ */
 
@@ -491,7 +594,8 @@ static int32_t integrate_impl(const or_family *fam, const double *lo,
   *n_leaves = 0;
   memset(res, 0, sizeof(*res));
   if (d < 1 || d > 20 || cap < 1 || !(opt->rel_tol >= 0.0) ||
-      !(opt->abs_tol >= 0.0)) {
+      !(opt->abs_tol >= 0.0) || (opt->rule != 0 && opt->rule != 1) ||
+      (opt->rule == 1 && (!opt->gk || d > 6))) {
     res->status = -1;
     return -1;
   }
@@ -534,9 +638,14 @@ static int32_t integrate_impl(const or_family *fam, const double *lo,
     double I, E, budget, ret_i, ret_e;
     int64_t nsplit, ties = 0;
     /* evaluate every active region */
-    or_rule_regions(fam, n, c, h, i7, NULL, err, vol, axis, atie, bad, scl);
+    if (opt->rule == 1) {
+      or_rule_gk_regions(fam, n, c, h, opt->gk, i7, NULL, err, vol, axis, atie, bad, scl);
+      res->function_evals += n * or_gk_nodes(d);
+    } else {
+      or_rule_regions(fam, n, c, h, i7, NULL, err, vol, axis, atie, bad, scl);
+      res->function_evals += n * or_num_nodes(d);
+    }
     res->regions_evaluated += n;
-    res->function_evals += n * or_num_nodes(d);
     iters++;
     /* global estimates */
     I = I_ret + or_pairwise_sum(i7, n);

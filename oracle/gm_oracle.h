@@ -60,7 +60,17 @@ typedef struct {
   int32_t init_splits; /* 0 = automatic */
   int32_t max_iters;   /* 0 = 1000 */
   int32_t classifier;  /* 0 = volume share, 1 = local relative */
+  int32_t rule;        /* 0 = Genz-Malik, 1 = tensor-product Gauss-Kronrod */
+  const double *gk;    /* rule 1: the 45-double table of or_rule_gk        */
 } or_options;
+
+/* Result of the tensor-product Gauss-Kronrod rule on one region. */
+typedef struct {
+  double ik, ig, err; /* K15^d value, G7^d value, |ik - ig|                 */
+  double vol;         /* prod_k 2 h_k                                       */
+  double scale;       /* prod_k h_k * sum over nodes of |K weight * f|      */
+  int32_t axis, axis_tie, flat, split_bad;
+} or_gk_out;
 
 typedef struct {
   double integral, error;
@@ -96,6 +106,25 @@ void or_rule_regions(const or_family *fam, int64_t n, const double *c,
                      int32_t *split_bad, double *i7abs);
 
 /* Pairwise (binary tree over a zero-padded power of two) sum. */
+/* Tensor-product Gauss-Kronrod (7, 15) rule on one region (the paper's
+ * Sec. 3 names the rule, not its order or its split axis; these are
+ * readings).  gk: 15 nodes of [-1, 1] in ascending order, then their K15
+ * weights, then the G7 weights (0 at the 8 Kronrod-only nodes).  Nodes
+ * x = fma(node, h_k, c_k) over all 15^d index tuples, axis 0 fastest;
+ * ik = prod h_k sum w_K f, ig the same with the G7 weights, err = |ik - ig|.
+ * E_k (written to E if not NULL) = prod h_k |sum (prod_{j != k} w_K)(w_K,k -
+ * w_G,k) f|: the error estimate in direction k (G7 along axis k, K15 along
+ * the others, against K15 everywhere); the split axis is argmax E_k, the
+ * lowest index on ties, or the widest axis when every E_k is below 1e-11
+ * of scale (rounding noise).  d <= 6. */
+int64_t or_gk_nodes(int d);
+void or_rule_gk(int d, const double *c, const double *h, or_integrand f,
+                const void *ctx, const double *gk, double *E, or_gk_out *out);
+void or_rule_gk_regions(const or_family *fam, int64_t n, const double *c,
+                        const double *h, const double *gk, double *ik,
+                        double *ig, double *err, double *vol, int32_t *axis,
+                        int32_t *axis_tie, int32_t *split_bad, double *scale);
+
 double or_pairwise_sum(const double *v, int64_t n);
 
 /* Initial uniform partition: returns s used; writes s^d regions. */

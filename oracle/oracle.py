@@ -37,7 +37,38 @@ class RuleOut(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_regions", C.c_int64),
-                ("init_splits", C.c_int32), ("max_iters", C.c_int32), ("classifier", C.c_int32)]
+                ("init_splits", C.c_int32), ("max_iters", C.c_int32), ("classifier", C.c_int32),
+                ("rule", C.c_int32), ("gk", _dp)]
+
+
+class GkOut(C.Structure):
+    _fields_ = [("ik", C.c_double), ("ig", C.c_double), ("err", C.c_double),
+                ("vol", C.c_double), ("scale", C.c_double), ("axis", C.c_int32),
+                ("axis_tie", C.c_int32), ("flat", C.c_int32), ("split_bad", C.c_int32)]
+
+
+RULE_GM = 0
+RULE_GK = 1
+_GK = None
+
+
+def gk_table():
+    """The 45-double Gauss-Kronrod table (nodes, K15 weights, G7 weights)
+    from gk_tables (exact rational arithmetic, rounded)."""
+    global _GK
+    if _GK is None:
+        from oracle.gk_tables import gk15_float
+        x, wk, wg = gk15_float()
+        _GK = np.ascontiguousarray(np.array(x + wk + wg, dtype=np.float64))
+    return _GK
+
+
+def _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, rule):
+    gk = gk_table() if rule == RULE_GK else None
+    o = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, rule,
+                _p(gk) if gk is not None else None)
+    o._keep = gk
+    return o
 
 
 class Result(C.Structure):
@@ -94,6 +125,12 @@ def lib():
                                   C.POINTER(C.c_int64)]
         L.or_bisect.restype = C.c_int64
         L.or_bisect.argtypes = [C.c_int, C.c_int64, _dp, _dp, _i32p, _u8p, _dp, _dp]
+        L.or_gk_nodes.restype = C.c_int64
+        L.or_gk_nodes.argtypes = [C.c_int]
+        L.or_rule_gk.argtypes = [C.c_int, _dp, _dp, C.c_void_p, C.c_void_p, _dp, _dp,
+                                 C.POINTER(GkOut)]
+        L.or_rule_gk_regions.argtypes = [C.POINTER(Family), C.c_int64, _dp, _dp, _dp, _dp, _dp,
+                                         _dp, _dp, _i32p, _i32p, _i32p, _dp]
         L.or_integrate.restype = C.c_int32
         L.or_integrate.argtypes = [C.POINTER(Family), _dp, _dp, C.POINTER(Options),
                                    C.POINTER(Result), C.POINTER(Trace), C.c_int32]
@@ -195,6 +232,53 @@ def rule_regions(family: int, a, u, c, h):
     return out
 
 
+def gk_nodes(d: int) -> int:
+    return 15 ** d
+
+
+def rule_gk(c, h, f=None, family=None, a=None, u=None):
+    """Tensor-product Gauss-Kronrod rule on one region; f a Python callable
+    or a built-in family.  Returns (GkOut fields as a dict, E ndarray)."""
+    c = _f64(c)
+    h = _f64(h)
+    d = len(c)
+    E = np.zeros(d)
+    out = GkOut()
+    L = lib()
+    if f is not None:
+        def cb(xp, dd, _ctx):
+            return float(f(np.ctypeslib.as_array(xp, shape=(dd,)).copy()))
+        cfun = INTEGRAND(cb)
+        L.or_rule_gk(d, _p(c), _p(h), C.cast(cfun, C.c_void_p), None, _p(gk_table()), _p(E),
+                     C.byref(out))
+    else:
+        fh = _FamilyHandle(family, a, u)
+        fn = C.cast(L.or_family_eval, C.c_void_p)
+        L.or_rule_gk(d, _p(c), _p(h), fn, C.cast(C.pointer(fh.s), C.c_void_p), _p(gk_table()),
+                     _p(E), C.byref(out))
+    r = {k: getattr(out, k) for k, _ in GkOut._fields_}
+    for k in ("axis_tie", "flat", "split_bad"):
+        r[k] = bool(r[k])
+    return r, E
+
+
+def rule_gk_regions(family: int, a, u, c, h):
+    """Gauss-Kronrod rule over n regions (c, h: n x d).  Returns a dict of
+    arrays: ik, ig, err, vol, scale, axis, axis_tie, split_bad."""
+    c = _f64(c)
+    h = _f64(h)
+    n, d = c.shape
+    fh = _FamilyHandle(family, a, u)
+    out = {k: np.zeros(n) for k in ("ik", "ig", "err", "vol", "scale")}
+    ints = {k: np.zeros(n, dtype=np.int32) for k in ("axis", "axis_tie", "split_bad")}
+    lib().or_rule_gk_regions(C.byref(fh.s), n, _p(c), _p(h), _p(gk_table()), _p(out["ik"]),
+                             _p(out["ig"]), _p(out["err"]), _p(out["vol"]),
+                             _p(ints["axis"], C.c_int32), _p(ints["axis_tie"], C.c_int32),
+                             _p(ints["split_bad"], C.c_int32), _p(out["scale"]))
+    out.update(ints)
+    return out
+
+
 def pairwise_sum(v) -> float:
     v = _f64(v)
     return float(lib().or_pairwise_sum(_p(v), len(v)))
@@ -258,12 +342,12 @@ class IntegrateResult:
 
 def integrate(family: int, a, u, rel_tol: float, lo=None, hi=None, abs_tol: float = 1e-16,
               max_regions: int = 100000, init_splits: int = 0, max_iters: int = 0,
-              classifier: int = 0, max_trace: int = 256) -> IntegrateResult:
+              classifier: int = 0, max_trace: int = 256, rule: int = RULE_GM) -> IntegrateResult:
     fh = _FamilyHandle(family, a, u)
     d = len(fh.a)
     lo = _f64(np.zeros(d) if lo is None else lo)
     hi = _f64(np.ones(d) if hi is None else hi)
-    opt = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier)
+    opt = _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, rule)
     res = Result()
     tr = (Trace * max_trace)()
     lib().or_integrate(C.byref(fh.s), _p(lo), _p(hi), C.byref(opt), C.byref(res), tr, max_trace)
@@ -308,7 +392,7 @@ def integrate_partition(family: int, a, u, rel_tol: float, lo=None, hi=None,
     co = np.zeros((ml, d))
     ho = np.zeros((ml, d))
     nl = C.c_int64()
-    opt = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier)
+    opt = _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, RULE_GM)
     res = Result()
     _lib_grad().or_integrate_partition(C.byref(fh.s), _p(lo), _p(hi), C.byref(opt), C.byref(res),
                                        _p(co), _p(ho), ml, C.byref(nl))
