@@ -45,6 +45,10 @@ def parse():
                          "kernel 3 times per family on 2^20 random d=8 regions and exits")
     ap.add_argument("--probe-split", action="store_true",
                     help="profiling probe: classify + split on 2^22 random d=8 regions")
+    ap.add_argument("--probe-batch", action="store_true",
+                    help="profiling probe: the d=8 tol 1e-6 problems as one batch, FP64 and mixed")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="with --probe-batch: the host-driven sweep loop instead of the graph")
     ap.add_argument("--kernel-sweep", action="store_true",
                     help="isolated rule / classify / split rates against the region count")
     ap.add_argument("--all-configs", action="store_true",
@@ -72,11 +76,11 @@ CAP = 1 << 24
 # (profiles/rule_fp64_d8.md).  The counts are fixed by the integrand and d:
 # the four families take no data-dependent branch.  Family codes: 0
 # oscillatory, 1 product peak, 2 corner peak, 3 Gaussian, 4 C0.
-RULE_FP64_INST_D8 = {0: 11032.0, 1: 12235.0, 2: 9027.0, 3: 16646.0, 4: 13438.0}
-RULE_FP64_FLOPS_D8 = {0: 17090.0, 1: 17491.0, 2: 14283.0, 3: 25511.0, 4: 22303.0}
+RULE_FP64_INST_D8 = {0: 11069.0, 1: 12272.0, 2: 9064.0, 3: 16683.0, 4: 13475.0}
+RULE_FP64_FLOPS_D8 = {0: 17127.0, 1: 17528.0, 2: 14320.0, 3: 25548.0, 4: 22340.0}
 # DRAM bytes per region of the rule kernel in the same capture (128 B read,
 # ~13 B written of 25 B of outputs); traffic per launch scales with regions.
-RULE_DRAM_BYTES_PER_REGION_D8 = 141.7
+RULE_DRAM_BYTES_PER_REGION_D8 = 141.3
 
 
 def time_to_tol(ctx, stream, tol):
@@ -442,6 +446,34 @@ def kernel_sweep(args):
     ctx.close()
 
 
+def probe_batch(args):
+    """The 40 d = 8 problems at tolerance 1e-6 as one batch, FP64 then
+    mixed (one call each after a warm-up call), for ncu launch lists of the
+    batched form (--host-loop launches every sweep's kernels from the host,
+    where a profiler sees them one by one); prints the event-timed seconds."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    probs = G.genz_d8_problems(tols=(1e-6,))
+    stream = torch.cuda.Stream(device=0)
+    ctx = gmq.Context(0, stream=stream)
+    for name, prec in (("fp64", gmq.FP64), ("mixed", gmq.MIXED)):
+        ctx.integrate_batch(probs[:4], max_regions=CAP, precision=prec)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = ctx.integrate_batch(probs, max_regions=CAP, pool_regions=1 << 26, precision=prec,
+                                  host_loop=args.host_loop)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info = ctx.last_batch_info()
+        print(f"batch {name}: {e0.elapsed_time(e1) / 1e3:.4f} s, "
+              f"{sum(r.regions_evaluated for r in res)} regions, {info['sweeps']} sweeps, "
+              f"lane sweeps {info['lane_sweeps']}", flush=True)
+    ctx.close()
+
+
 def _closed_gauss(a, u):
     import math
     g = [math.sqrt(math.pi) / (2 * ai) * (math.erf(ai * (1 - ui)) + math.erf(ai * ui))
@@ -555,6 +587,8 @@ def main():
         return probe_split(args)
     if args.kernel_sweep:
         return kernel_sweep(args)
+    if args.probe_batch:
+        return probe_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -648,7 +682,7 @@ def main():
         roof = {"bound": "alu", "achieved": ach, "peak": peak_inst,
                 "unit": "G FP64 lane-inst/s", "frac": ach / peak_inst,
                 "traffic": RULE_DRAM_BYTES_PER_REGION_D8 * rule["regions"] / n_launch,
-                "kernel": "k_rule (FP64 rule evaluation)",
+                "kernel": "k_rule64 (FP64 rule evaluation)",
                 "peak_basis": (f"2 FP64 lanes/clk/SM (1.25 TFLOP/s nominal) x 152 SMs "
                                f"x median {mhz:.0f} MHz"),
                 "flops_view": {"achieved_gflops": flops / avg_s / 1e9,

@@ -82,6 +82,24 @@ typedef enum gmq_classifier {
   GMQ_LOCAL_REL = 1     /* retire r if eps_r <= rel_tol |I_r|                                    */
 } gmq_classifier;
 
+/* Quadrature rule (paper Sec. 3: the framework accommodates several rules).
+ * GMQ_RULE_GENZ_MALIK: the degree-7 Genz-Malik rule with its embedded
+ * degree-5 rule (Sec. 2), any dim.  GMQ_RULE_GAUSS_KRONROD: the
+ * tensor-product Gauss-Kronrod rule, 7-point Gauss / 15-point Kronrod per
+ * axis (15^dim nodes per region; the paper names the rule but not its order
+ * -- this is the classic pair), FP64 only, dim <= GMQ_GK_MAX_DIM (the paper
+ * finds its cost prohibitive from dim 7).  Its error estimate is
+ * |I_K - I_G|; its split axis is the one with the largest directional
+ * estimate prod h_k |sum (prod_{j != k} wK)(wK_k - wG_k) f| (G7 along that
+ * axis only), or the widest axis when all of those are below 1e-11 of the
+ * terms' magnitude. */
+typedef enum gmq_rule {
+  GMQ_RULE_GENZ_MALIK = 0,
+  GMQ_RULE_GAUSS_KRONROD = 1
+} gmq_rule;
+
+#define GMQ_GK_MAX_DIM 6
+
 typedef struct gmq_problem {
   int32_t dim;       /* 1 <= dim <= GMQ_MAX_DIM                             */
   int32_t family;    /* gmq_family                                          */
@@ -106,6 +124,7 @@ typedef struct gmq_options {
                           one fixed tree); mixed-precision results do, at
                           the level of FP32 rounding                        */
   int32_t flags;       /* 0, or GMQ_KEEP_PARTITION                           */
+  int32_t rule;        /* gmq_rule (GMQ_RULE_GENZ_MALIK by default)          */
 } gmq_options;
 
 /* gmq_options.flags: record the final partition of the run (every region
@@ -308,6 +327,23 @@ gmq_status gmq_eval_rule(gmq_context *ctx, const gmq_problem *prob,
                          const double *d_center, const double *d_halfw,
                          int64_t ld, double *d_integral, double *d_error,
                          double *d_volfrac, uint8_t *d_axis);
+
+/* The tensor-product Gauss-Kronrod rule (gmq_rule) on n regions, FP64, one
+ * warp per region; outputs as for gmq_eval_rule with d_integral[r] = I_K
+ * (the 15^dim-node value) and d_error[r] = |I_K - I_G|.  dim <=
+ * GMQ_GK_MAX_DIM, else GMQ_ERR_INVALID.  Synchronous on the context stream. */
+gmq_status gmq_eval_rule_gk(gmq_context *ctx, const gmq_problem *prob, int64_t n,
+                            const double *d_center, const double *d_halfw,
+                            int64_t ld, double *d_integral, double *d_error,
+                            double *d_volfrac, uint8_t *d_axis);
+
+/* The library's 1-D Gauss-Kronrod tables on [-1, 1] (host memory, 45
+ * doubles): out[0..15) the 15 nodes in ascending order, out[15..30) their
+ * Kronrod weights, out[30..45) the Gauss weights (0 at the 8 Kronrod-only
+ * nodes).  Computed on the host (Newton iteration for the Legendre zeros,
+ * bisection for the zeros of the Stieltjes polynomial, an 8 x 8 solve for
+ * the Kronrod weights); no device work. */
+gmq_status gmq_gk_table(double *out);
 
 /* Classification and bisection of one sweep (paper Sec. 3) given the rule
  * outputs above and the sweep's budget = max(abs_tol, rel_tol |I|).

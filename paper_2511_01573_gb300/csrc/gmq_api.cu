@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "gm_adjoint.cuh"
+#include "gm_gk.cuh"
 #include "gm_rule.cuh"
 #include "gmq_common.cuh"
 #include "gm_batch.cuh"
@@ -34,6 +35,13 @@ extern template cudaError_t launch_rule_grad_family<GMQ_GAUSSIAN>(const GradArgs
 extern template cudaError_t launch_rule_grad_family<GMQ_C0>(const GradArgs&, cudaStream_t);
 extern template cudaError_t launch_rule_grad_family<GMQ_DISCONTINUOUS>(const GradArgs&, cudaStream_t);
 extern template cudaError_t launch_rule_grad_family<GMQ_POLY_SUMSQ11>(const GradArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_gk_family<GMQ_OSCILLATORY>(const GkArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_gk_family<GMQ_PRODUCT_PEAK>(const GkArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_gk_family<GMQ_CORNER_PEAK>(const GkArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_gk_family<GMQ_GAUSSIAN>(const GkArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_gk_family<GMQ_C0>(const GkArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_gk_family<GMQ_DISCONTINUOUS>(const GkArgs&, cudaStream_t);
+extern template cudaError_t launch_rule_gk_family<GMQ_POLY_SUMSQ11>(const GkArgs&, cudaStream_t);
 }
 
 struct gmq_context {
@@ -57,6 +65,7 @@ struct gmq_context {
   const double* part_h = nullptr;
   // working memory of gmq_rule_grad
   char* gscratch = nullptr;
+  GkConst* gk_dev = nullptr;  // device copy of the Gauss-Kronrod tables
   size_t gscratch_bytes = 0;
   // batched form: autotuned lanes-per-region thresholds per largest dimension
   int tuned[GMQ_MAX_DIM + 1] = {};
@@ -265,6 +274,168 @@ int batch_rule_mixed_max_blocks(int fam, int dmax) {
   }
 }
 
+// ---- Gauss-Kronrod (7, 15) tables, computed on the host in FP64 ----------
+// P_n(x) and P_n'(x) by the three-term recurrence.
+void legendre_pd(int n, double x, double* p, double* dp) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    *p = 1.0;
+    *dp = 0.0;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *p = p1;
+  *dp = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+// The n / 2 positive zeros of P_n (descending) by Newton from the usual
+// cosine guesses cos(pi (i + 3/4) / (n + 1/2)), i = 0 .. n/2 - 1 (for odd n
+// the zero at 0 is not among them); ws (if not null) the Gauss weights.
+void gauss_positive(int n, double* xs, double* ws) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n / 2; ++i) {
+    double x = std::cos(pi * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre_pd(n, x, &p, &dp);
+      const double dx = p / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-17) break;
+    }
+    double p, dp;
+    legendre_pd(n, x, &p, &dp);
+    xs[i] = x;
+    if (ws) ws[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+// Dense solve with partial pivoting (n <= 8).
+void solve_small(int n, double* a, double* b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[r * n + c]) > std::fabs(a[piv * n + c])) piv = r;
+    for (int k = 0; k < n; ++k) std::swap(a[c * n + k], a[piv * n + k]);
+    std::swap(b[c], b[piv]);
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[r * n + c] / a[c * n + c];
+      for (int k = 0; k < n; ++k) a[r * n + k] -= f * a[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int c = 0; c < n; ++c) b[c] /= a[c * n + c];
+}
+
+GkConst make_gk() {
+  GkConst K;
+  // positive G7 nodes (ascending) and weights; the centre separately
+  double g[3], gw[3];
+  gauss_positive(7, g, gw);
+  std::sort(g, g + 3);
+  for (int i = 0; i < 3; ++i) {
+    double p, dp;
+    legendre_pd(7, g[i], &p, &dp);
+    gw[i] = 2.0 / ((1.0 - g[i] * g[i]) * dp * dp);
+  }
+  double p0, dp0;
+  legendre_pd(7, 0.0, &p0, &dp0);
+  const double gw0 = 2.0 / (dp0 * dp0);
+  // Stieltjes polynomial E8 = sum_{m<=4} a_m P_{2m}, a_4 = 1, orthogonal to
+  // P7 x^k (k odd; the even k vanish by parity): moments by a 16-point
+  // Gauss rule (exact to degree 31 >= 8 + 7 + 7)
+  double q[8], qw[8];
+  gauss_positive(16, q, qw);
+  auto moment = [&](int m2, int k) {
+    double acc = 0.0;
+    for (int i = 0; i < 8; ++i) {
+      double pa, da, pb, db;
+      legendre_pd(m2, q[i], &pa, &da);
+      legendre_pd(7, q[i], &pb, &db);
+      acc += 2.0 * qw[i] * pa * pb * std::pow(q[i], k);  // the integrand is even
+    }
+    return acc;
+  };
+  double M[16], rhs[4];
+  const int ks[4] = {1, 3, 5, 7};
+  for (int r = 0; r < 4; ++r) {
+    for (int m = 0; m < 4; ++m) M[r * 4 + m] = moment(2 * m, ks[r]);
+    rhs[r] = -moment(8, ks[r]);
+  }
+  solve_small(4, M, rhs);
+  auto e8 = [&](double x) {
+    double v = 0.0, p, dp;
+    for (int m = 0; m < 4; ++m) {
+      legendre_pd(2 * m, x, &p, &dp);
+      v += rhs[m] * p;
+    }
+    legendre_pd(8, x, &p, &dp);
+    return v + p;
+  };
+  // its positive zeros interlace the Gauss nodes: bisection in each gap
+  const double edges[5] = {0.0, g[0], g[1], g[2], 1.0};
+  double kz[4];
+  for (int i = 0; i < 4; ++i) {
+    double lo = edges[i], hi = edges[i + 1], flo = e8(lo);
+    for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      const double fm = e8(mid);
+      if ((fm > 0.0) == (flo > 0.0)) {
+        lo = mid;
+        flo = fm;
+      } else {
+        hi = mid;
+      }
+    }
+    kz[i] = 0.5 * (lo + hi);
+  }
+  // the 7 positive nodes, alternating Kronrod-only and Gauss
+  const double pos[7] = {kz[0], g[0], kz[1], g[1], kz[2], g[2], kz[3]};
+  // K15 weights: exactness for P_0, P_2, ..., P_14 over the centre and the
+  // 7 symmetric pairs
+  double W[64], wb[8];
+  const double dist[8] = {0.0, pos[0], pos[1], pos[2], pos[3], pos[4], pos[5], pos[6]};
+  for (int r = 0; r < 8; ++r) {
+    for (int j = 0; j < 8; ++j) {
+      double p, dp;
+      legendre_pd(2 * r, dist[j], &p, &dp);
+      W[r * 8 + j] = (j == 0 ? 1.0 : 2.0) * p;
+    }
+    wb[r] = (r == 0) ? 2.0 : 0.0;
+  }
+  solve_small(8, W, wb);
+  for (int i = 0; i < 7; ++i) {
+    K.x[6 - i] = -pos[i];
+    K.x[8 + i] = pos[i];
+    K.wk[6 - i] = K.wk[8 + i] = wb[1 + i];
+    const double gwi = (i % 2 == 1) ? gw[i / 2] : 0.0;
+    K.wg[6 - i] = K.wg[8 + i] = gwi;
+  }
+  K.x[7] = 0.0;
+  K.wk[7] = wb[0];
+  K.wg[7] = gw0;
+  for (int j = 0; j < 15; ++j) K.r[j] = 1.0 - K.wg[j] / K.wk[j];
+  return K;
+}
+
+cudaError_t launch_rule_gk(int fam, const GkArgs& G, cudaStream_t s) {
+  switch (fam) {
+    case GMQ_OSCILLATORY: return launch_rule_gk_family<GMQ_OSCILLATORY>(G, s);
+    case GMQ_PRODUCT_PEAK: return launch_rule_gk_family<GMQ_PRODUCT_PEAK>(G, s);
+    case GMQ_CORNER_PEAK: return launch_rule_gk_family<GMQ_CORNER_PEAK>(G, s);
+    case GMQ_GAUSSIAN: return launch_rule_gk_family<GMQ_GAUSSIAN>(G, s);
+    case GMQ_C0: return launch_rule_gk_family<GMQ_C0>(G, s);
+    case GMQ_DISCONTINUOUS: return launch_rule_gk_family<GMQ_DISCONTINUOUS>(G, s);
+    case GMQ_POLY_SUMSQ11: return launch_rule_gk_family<GMQ_POLY_SUMSQ11>(G, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Name of the last CUDA error a call of this thread turned into a status.
 thread_local const char* g_last_cuda_error = "cudaSuccess";
 
@@ -384,6 +555,32 @@ gmq_status ensure_scratch(gmq_context* ctx, int64_t n, Scratch* S) {
 
 }  // namespace
 
+const GkConst& gmq::gk_const() {
+  static const GkConst K = make_gk();
+  return K;
+}
+
+namespace {
+
+// The context's device copy of the Gauss-Kronrod tables (made on first use).
+gmq_status ensure_gk(gmq_context* ctx) {
+  if (ctx->gk_dev) return GMQ_OK;
+  void* q = nullptr;
+  if (cudaMalloc(&q, sizeof(GkConst)) != cudaSuccess) {
+    cudaGetLastError();
+    return GMQ_ERR_OOM;
+  }
+  const cudaError_t e = cudaMemcpy(q, &gk_const(), sizeof(GkConst), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(q);
+    return cuda_fail(e);
+  }
+  ctx->gk_dev = (GkConst*)q;
+  return GMQ_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* gmq_status_string(gmq_status s) {
@@ -452,6 +649,7 @@ gmq_status gmq_destroy(gmq_context* ctx) {
     if (ctx->own) cudaFree(ctx->own);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->gscratch) cudaFree(ctx->gscratch);
+    if (ctx->gk_dev) cudaFree(ctx->gk_dev);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->ev_made)
@@ -493,6 +691,7 @@ gmq_status gmq_default_options(gmq_options* opt) {
   opt->max_iters = 1000;
   opt->precision = GMQ_FP64;
   opt->classifier = GMQ_VOLUME_SHARE;
+  opt->rule = GMQ_RULE_GENZ_MALIK;
   return GMQ_OK;
 }
 
@@ -547,8 +746,12 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
       opt->init_splits < 0 || opt->max_iters < 0 || (opt->flags & ~GMQ_KEEP_PARTITION) ||
       (opt->precision != GMQ_FP64 && opt->precision != GMQ_MIXED) ||
       (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL) ||
-      (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32))
+      (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32) ||
+      (opt->rule != GMQ_RULE_GENZ_MALIK && opt->rule != GMQ_RULE_GAUSS_KRONROD) ||
+      (opt->rule == GMQ_RULE_GAUSS_KRONROD &&
+       (opt->precision != GMQ_FP64 || d > GMQ_GK_MAX_DIM)))
     return out->status = GMQ_ERR_INVALID, GMQ_ERR_INVALID;
+  const bool gk = opt->rule == GMQ_RULE_GAUSS_KRONROD;
   const int s = opt->init_splits > 0 ? opt->init_splits : auto_splits(d, cap);
   int64_t n = 1;
   for (int k = 0; k < d; ++k) {
@@ -575,6 +778,13 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
 
   const FamParams P = fam_params(prob);
   const RuleConst R = rule_const(d, prob->lo, prob->hi);
+  int64_t nodes_per_region = R.nodes;
+  if (gk) {
+    gmq_status gs = ensure_gk(ctx);
+    if (gs != GMQ_OK) return out->status = gs, gs;
+    nodes_per_region = 1;
+    for (int k = 0; k < d; ++k) nodes_per_region *= 15;
+  }
 
   // initial uniform partition
   PartArgs PA;
@@ -612,7 +822,14 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
     A.P = P;
     A.R = R;
     prof_begin(ctx, kKRule);
-    GMQ_CK(launch_rule(prob->family, opt->precision, T, A, strm));
+    if (gk) {
+      GkArgs GA;
+      GA.A = A;
+      GA.K = ctx->gk_dev;
+      GMQ_CK(launch_rule_gk(prob->family, GA, strm));
+    } else {
+      GMQ_CK(launch_rule(prob->family, opt->precision, T, A, strm));
+    }
     prof_end(ctx, kKRule, n);
 
     SweepArgs S;
@@ -664,7 +881,7 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
 
     ++iters;
     out->regions_evaluated += n;
-    out->function_evals += n * R.nodes;
+    out->function_evals += n * nodes_per_region;
     out->final_active = n;
     out->integral = h.I;
     out->error = h.E;
@@ -762,6 +979,53 @@ gmq_status gmq_eval_rule(gmq_context* ctx, const gmq_problem* prob, int32_t prec
   ctx->launches += 1;
   GMQ_CK(cudaStreamSynchronize(ctx->stream));
   prof_collect(ctx);
+  return GMQ_OK;
+}
+
+gmq_status gmq_eval_rule_gk(gmq_context* ctx, const gmq_problem* prob, int64_t n,
+                            const double* d_center, const double* d_halfw, int64_t ld,
+                            double* d_integral, double* d_error, double* d_volfrac,
+                            uint8_t* d_axis) {
+  if (!ctx) return GMQ_ERR_INVALID;
+  gmq_status vs = validate_problem(prob);
+  if (vs != GMQ_OK) return vs;
+  if (prob->dim > GMQ_GK_MAX_DIM) return GMQ_ERR_INVALID;
+  if (n < 0 || ld < n || (n > 0 && (!d_center || !d_halfw || !d_integral || !d_error || !d_axis)))
+    return GMQ_ERR_INVALID;
+  if (n == 0) return GMQ_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  gmq_status gs = ensure_gk(ctx);
+  if (gs != GMQ_OK) return gs;
+  GkArgs G;
+  G.A.c = d_center;
+  G.A.h = d_halfw;
+  G.A.ld = ld;
+  G.A.n = n;
+  G.A.i7 = d_integral;
+  G.A.err = d_error;
+  G.A.volfrac = d_volfrac;
+  G.A.axis = d_axis;
+  G.A.P = fam_params(prob);
+  G.A.R = rule_const(prob->dim, prob->lo, prob->hi);
+  G.K = ctx->gk_dev;
+  prof_begin(ctx, kKRule);
+  GMQ_CK(launch_rule_gk(prob->family, G, ctx->stream));
+  prof_end(ctx, kKRule, n);
+  ctx->launches += 1;
+  GMQ_CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  return GMQ_OK;
+}
+
+gmq_status gmq_gk_table(double* out) {
+  if (!out) return GMQ_ERR_INVALID;
+  const GkConst& K = gk_const();
+  for (int j = 0; j < 15; ++j) {
+    out[j] = K.x[j];
+    out[15 + j] = K.wk[j];
+    out[30 + j] = K.wg[j];
+  }
   return GMQ_OK;
 }
 
@@ -957,7 +1221,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
       opt->max_iters < 0 || (opt->flags & ~GMQ_BATCH_HOST_LOOP) ||
       (opt->precision != GMQ_FP64 && opt->precision != GMQ_MIXED) ||
       (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32) ||
-      (opt->precision == GMQ_MIXED && opt->lanes > 1) ||
+      (opt->precision == GMQ_MIXED && opt->lanes > 1) || opt->rule != GMQ_RULE_GENZ_MALIK ||
       (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL))
     return GMQ_ERR_INVALID;
   std::memset(results, 0, sizeof(gmq_result) * (size_t)count);

@@ -37,7 +37,8 @@ class Problem(C.Structure):
 class Options(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_regions", C.c_int64),
                 ("init_splits", C.c_int32), ("max_iters", C.c_int32), ("precision", C.c_int32),
-                ("classifier", C.c_int32), ("lanes", C.c_int32), ("flags", C.c_int32)]
+                ("classifier", C.c_int32), ("lanes", C.c_int32), ("flags", C.c_int32),
+                ("rule", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -63,10 +64,13 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_status_string", "gmq_launch_count", "gmq_eval_rule", "gmq_classify_split",
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
            "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad",
-           "gmq_integrate_batch", "gmq_last_batch_info")
+           "gmq_integrate_batch", "gmq_last_batch_info", "gmq_eval_rule_gk", "gmq_gk_table")
 
 KEEP_PARTITION = 1
 BATCH_HOST_LOOP = 2
+RULE_GENZ_MALIK = 0
+RULE_GAUSS_KRONROD = 1
+GK_MAX_DIM = 6
 
 
 class BatchInfo(C.Structure):
@@ -79,6 +83,15 @@ class BatchInfo(C.Structure):
 
 ERR_TOO_LARGE = -6
 NOALLOC_MAX_N = 1 << 23
+
+
+def gk_table():
+    """The library's 1-D Gauss-Kronrod tables (45 floats: nodes, K15 and G7
+    weights)."""
+    import numpy as np
+    out = np.zeros(45)
+    _check("gmq_gk_table", lib().gmq_gk_table(out.ctypes.data_as(_dp)))
+    return out
 
 
 class GmqError(RuntimeError):
@@ -128,6 +141,8 @@ def lib():
         "gmq_integrate_batch": [vp, i32, C.POINTER(Problem), _dp, C.POINTER(Options), i64,
                                 C.POINTER(Result)],
         "gmq_last_batch_info": [vp, C.POINTER(BatchInfo)],
+        "gmq_eval_rule_gk": [vp, C.POINTER(Problem), i64, vp, vp, i64, vp, vp, vp, vp],
+        "gmq_gk_table": [_dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -286,10 +301,10 @@ class Context:
     def integrate(self, family, a=None, u=None, rel_tol=1e-6, lo=None, hi=None, abs_tol=1e-16,
                   max_regions=1 << 22, init_splits=0, max_iters=0, precision=FP64,
                   classifier=VOLUME_SHARE, lanes=0, dim=None, check=True,
-                  keep_partition=False) -> IntegrateResult:
+                  keep_partition=False, rule=RULE_GENZ_MALIK) -> IntegrateResult:
         p = _ProblemHandle(family, a, u, lo, hi, dim)
         o = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, precision, classifier,
-                    lanes, KEEP_PARTITION if keep_partition else 0)
+                    lanes, KEEP_PARTITION if keep_partition else 0, rule)
         r = Result()
         self._last_dim = p.s.dim
         code = lib().gmq_integrate(self.h, C.byref(p.s), C.byref(o), C.byref(r))
@@ -418,6 +433,25 @@ class Context:
             self.h, C.byref(p.s), precision, lanes, n, _dptr(center), _dptr(halfw),
             ld, _dptr(i7), _dptr(err), _dptr(vf), _dptr(ax)))
         return i7, err, vf, ax
+
+    def eval_rule_gk(self, family, a, u, center, halfw, lo=None, hi=None):
+        """The tensor-product Gauss-Kronrod rule; arguments and results as
+        for eval_rule (I_K in place of I7)."""
+        torch = self.torch
+        center = self._dev(center, torch.float64)
+        halfw = self._dev(halfw, torch.float64)
+        d, n = center.shape
+        ld = self._ld(center, halfw)
+        p = _ProblemHandle(family, a, u, lo, hi, d)
+        dev = center.device
+        ik = torch.empty(n, dtype=torch.float64, device=dev)
+        err = torch.empty(n, dtype=torch.float64, device=dev)
+        vf = torch.empty(n, dtype=torch.float64, device=dev)
+        ax = torch.empty(n, dtype=torch.uint8, device=dev)
+        _check("gmq_eval_rule_gk", lib().gmq_eval_rule_gk(
+            self.h, C.byref(p.s), n, _dptr(center), _dptr(halfw), ld, _dptr(ik), _dptr(err),
+            _dptr(vf), _dptr(ax)))
+        return ik, err, vf, ax
 
     def classify_split(self, center, halfw, i7, err, volfrac, axis, budget, rel_tol=0.0,
                        classifier=VOLUME_SHARE, cap_out=None):
