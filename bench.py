@@ -47,6 +47,9 @@ def parse():
                     help="profiling probe: classify + split on 2^22 random d=8 regions")
     ap.add_argument("--probe-batch", action="store_true",
                     help="profiling probe: the d=8 tol 1e-6 problems as one batch, FP64 and mixed")
+    ap.add_argument("--probe-gk", default=None,
+                    help="profiling probe: family codes; the Gauss-Kronrod rule kernel on 2^13 "
+                         "random d=4 regions, three launches per family")
     ap.add_argument("--host-loop", action="store_true",
                     help="with --probe-batch: the host-driven sweep loop instead of the graph")
     ap.add_argument("--kernel-sweep", action="store_true",
@@ -474,6 +477,52 @@ def probe_batch(args):
     ctx.close()
 
 
+def probe_gk(args):
+    """The Gauss-Kronrod rule kernel alone on 2^13 random sub-boxes of
+    [0,1]^4 (15^4 nodes each), three launches per family, for ncu captures;
+    prints the event-timed rate."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    n, d = 1 << 13, 4
+    g = torch.Generator(device="cuda").manual_seed(5)
+    lo = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.9
+    w = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.05 + 1e-3
+    c = (lo + 0.5 * w).contiguous()
+    h = (0.5 * w).contiguous()
+    ctx = gmq.Context(0)
+    ctx.profile(True)
+    for fam in (int(x) for x in args.probe_gk.split(",")):
+        a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM.get(fam, 2.0))
+        ctx.profile_reset()
+        for _ in range(3):
+            ctx.eval_rule_gk(fam, a, u, c, h)
+        p = ctx.profile_read()["rule"]
+        ms = p["ms"] / p["launches"]
+        print(f"gk family {fam} d {d}: {ms:.3f} ms/launch, {n / ms * 1e3:.4g} regions/s, "
+              f"{n * 15 ** d / ms * 1e3:.4g} node-evals/s", flush=True)
+    ctx.close()
+
+
+def _closed(fam, a, u):
+    """Closed forms on [0,1]^d: Gaussian erf product, oscillatory
+    Re[e^{i 2 pi u1} prod (e^{i a} - 1) / (i a)], C0 exp product."""
+    import cmath
+    import math
+    from paper_2511_01573_gb300 import genz_inputs as G
+    if fam == G.GAUSSIAN:
+        return _closed_gauss(a, u)[0]
+    if fam == G.C0:
+        return math.prod((2.0 - math.exp(-ai * ui) - math.exp(-ai * (1.0 - ui))) / ai
+                         for ai, ui in zip(a, u))
+    if fam == G.OSCILLATORY:
+        z = cmath.exp(2j * math.pi * u[0])
+        for ai in a:
+            z *= (cmath.exp(1j * ai) - 1.0) / (1j * ai)
+        return z.real
+    raise ValueError(fam)
+
+
 def _closed_gauss(a, u):
     import math
     g = [math.sqrt(math.pi) / (2 * ai) * (math.erf(ai * (1 - ui)) + math.erf(ai * ui))
@@ -558,6 +607,25 @@ def all_configs(args):
                               "max_rel_diff_vs_fp64": max(
                                   abs(m.integral - f.integral) / abs(f.integral)
                                   for m, f in zip(resm, res) if f.integral != 0.0)}}
+    # the tensor-product Gauss-Kronrod rule against Genz-Malik, d = 2..6
+    gk_rows = []
+    for fam in (G.GAUSSIAN, G.OSCILLATORY, G.C0):
+        for d in (2, 3, 4, 5, 6):
+            a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM[fam])
+            for tol in ((1e-6, 1e-9) if d <= 4 else (1e-6,)):
+                row = {"family": G.FAMILY_NAMES[fam], "d": d, "tol": tol}
+                for name, rule, cap in (("gm", gmq.RULE_GENZ_MALIK, 1 << 22),
+                                        ("gk", gmq.RULE_GAUSS_KRONROD, 1 << 18)):
+                    r, t = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=cap,
+                                                       rule=rule))
+                    row[name] = {"s": t, "regions": r.regions_evaluated,
+                                 "function_evals": r.function_evals, "status": r.status,
+                                 "integral": r.integral}
+                ref = _closed(fam, a, u)
+                for name in ("gm", "gk"):
+                    row[name]["rel_err_vs_closed_form"] = abs(row[name]["integral"] - ref) / abs(ref)
+                gk_rows.append(row)
+    rep["gauss_kronrod_vs_genz_malik"] = gk_rows
     # gradients of the d = 6 Gaussian over frozen partitions
     sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
     errs, tf, tg = [], 0.0, 0.0
@@ -589,6 +657,8 @@ def main():
         return kernel_sweep(args)
     if args.probe_batch:
         return probe_batch(args)
+    if args.probe_gk:
+        return probe_gk(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch
