@@ -15,6 +15,8 @@
 // two: a tile of 1024 regions is a complete subtree, the last block to
 // finish sums the tile results with the same tree.  No floating-point
 // atomics: the result does not depend on scheduling.
+#include <cstdint>
+
 #include "gmq_common.cuh"
 #include "sweep_kernels.cuh"
 
@@ -39,55 +41,113 @@ __device__ double tree_sum_global(const double* v, int64_t count, double* scratc
   return block_tree_sum(tid < nt ? tile_sums[tid] : 0.0, scratch);
 }
 
-// Exclusive scan of in[0..count) (int) into out (long long) by one block;
-// returns the total.
-__device__ long long block_exclusive_scan(const int* in, long long* out, int64_t count,
-                                          long long* wsum) {
+// The same trees with a quarter of the threads: kQuad threads, thread t
+// holding the 4 consecutive values 4t .. 4t + 3 of a tile.  Its
+// ((v0 + v1) + (v2 + v3)) are the first two levels of the tile's pairwise
+// tree and block_tree_sum adds the rest, so a tile sum is bit-identical to
+// the kTile-thread form.
+constexpr int kQuad = kTile / 4;
+
+__device__ __forceinline__ double tile_sum4(const double* v, int64_t base, int64_t count,
+                                            double* scratch) {
+  const int64_t i = base + 4 * (int64_t)threadIdx.x;
+  const double a = i < count ? v[i] : 0.0, b = i + 1 < count ? v[i + 1] : 0.0;
+  const double c = i + 2 < count ? v[i + 2] : 0.0, d = i + 3 < count ? v[i + 3] : 0.0;
+  return block_tree_sum((a + b) + (c + d), scratch);
+}
+
+// tree_sum_global for blocks of kQuad threads; the partials were written by
+// other blocks of this launch (read through L2).
+__device__ double tree_sum_global4(const double* v, int64_t count, double* scratch,
+                                   double* tile_sums) {
+  if (count <= kTile) {
+    const int64_t i = 4 * (int64_t)threadIdx.x;
+    double q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = i + k < count ? __ldcg(v + i + k) : 0.0;
+    return block_tree_sum((q[0] + q[1]) + (q[2] + q[3]), scratch);
+  }
+  const int64_t nt = (count + kTile - 1) / kTile;  // <= kTile by construction
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t i = t * kTile + 4 * (int64_t)threadIdx.x;
+    double q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = i + k < count ? __ldcg(v + i + k) : 0.0;
+    const double s = block_tree_sum((q[0] + q[1]) + (q[2] + q[3]), scratch);
+    if (threadIdx.x == 0) tile_sums[t] = s;
+  }
+  __syncthreads();
+  return tile_sum4(tile_sums, 0, nt, scratch);
+}
+
+// Exclusive scan of in[0..count) (int) into out (long long) by one block of
+// any multiple of 32 threads; returns the total.
+__device__ long long block_exclusive_scan_any(const int* in, long long* out, int64_t count,
+                                              long long* wsum) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = blockDim.x >> 5;
   long long carry = 0;
-  for (int64_t base = 0; base < count; base += kTile) {
+  for (int64_t base = 0; base < count; base += blockDim.x) {
     const int64_t i = base + tid;
-    long long v = i < count ? (long long)in[i] : 0;
-    // inclusive warp scan
+    const long long v = i < count ? (long long)__ldcg(in + i) : 0;
     long long x = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      long long y = __shfl_up_sync(0xffffffffu, x, off);
+      const long long y = __shfl_up_sync(0xffffffffu, x, off);
       if (lane >= off) x += y;
     }
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
     if (warp == 0) {
-      long long w = wsum[lane];
+      long long w = lane < nw ? wsum[lane] : 0;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
-        long long y = __shfl_up_sync(0xffffffffu, w, off);
+        const long long y = __shfl_up_sync(0xffffffffu, w, off);
         if (lane >= off) w += y;
       }
-      wsum[lane] = w;  // inclusive over warps
+      if (lane < nw) wsum[lane] = w;
     }
     __syncthreads();
     const long long before = (warp > 0 ? wsum[warp - 1] : 0) + (x - v);
     if (i < count) out[i] = carry + before;
-    const long long tot = wsum[31];
+    const long long tot = wsum[nw - 1];
     __syncthreads();
     carry += tot;
   }
   return carry;
 }
 
+// 4 consecutive doubles v[i .. i + 3] (0 past n): two 16-byte vector loads
+// when all four exist and v + i is 16-byte aligned (caller arrays of the
+// step-level calls need only be 8-byte aligned), scalar loads otherwise.
+__device__ __forceinline__ void load4(const double* v, int64_t i, int64_t n, double q[4]) {
+  if (i + 3 < n && (reinterpret_cast<uintptr_t>(v + i) & 15u) == 0) {
+    const double2 x = *reinterpret_cast<const double2*>(v + i);
+    const double2 y = *reinterpret_cast<const double2*>(v + i + 2);
+    q[0] = x.x;
+    q[1] = x.y;
+    q[2] = y.x;
+    q[3] = y.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = i + k < n ? v[i + k] : 0.0;
+  }
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kTile) k_sum_status(const SweepArgs S) {
+__global__ void __launch_bounds__(kQuad) k_sum_status(const SweepArgs S) {
   __shared__ double scratch[33];
   __shared__ double tile_sums[kTile];
   __shared__ int is_last;
   if (S.st->flags & kDone) return;
-  const int64_t r = (int64_t)blockIdx.x * kTile + threadIdx.x;
-  const double a = r < S.n ? S.i7[r] : 0.0;
-  const double b = r < S.n ? S.err[r] : 0.0;
-  const double ta = block_tree_sum(a, scratch);
-  const double tb = block_tree_sum(b, scratch);
+  // a tile of kTile regions per block, 4 consecutive regions per thread
+  const int64_t r = (int64_t)blockIdx.x * kTile + 4 * (int64_t)threadIdx.x;
+  double a[4], b[4];
+  load4(S.i7, r, S.n, a);
+  load4(S.err, r, S.n, b);
+  const double ta = block_tree_sum((a[0] + a[1]) + (a[2] + a[3]), scratch);
+  const double tb = block_tree_sum((b[0] + b[1]) + (b[2] + b[3]), scratch);
   if (threadIdx.x == 0) {
     S.blk_a[blockIdx.x] = ta;
     S.blk_b[blockIdx.x] = tb;
@@ -98,8 +158,8 @@ __global__ void __launch_bounds__(kTile) k_sum_status(const SweepArgs S) {
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const double A = tree_sum_global(S.blk_a, gridDim.x, scratch, tile_sums);
-  const double B = tree_sum_global(S.blk_b, gridDim.x, scratch, tile_sums);
+  const double A = tree_sum_global4(S.blk_a, gridDim.x, scratch, tile_sums);
+  const double B = tree_sum_global4(S.blk_b, gridDim.x, scratch, tile_sums);
   if (threadIdx.x == 0) {
     DevStatus* st = S.st;
     st->ticket_sum = 0u;
@@ -120,35 +180,65 @@ __global__ void __launch_bounds__(kTile) k_sum_status(const SweepArgs S) {
   }
 }
 
-__global__ void __launch_bounds__(kTile) k_classify(const SweepArgs S) {
+__global__ void __launch_bounds__(kQuad) k_classify(const SweepArgs S) {
   __shared__ double scratch[33];
   __shared__ double tile_sums[kTile];
   __shared__ long long wsum[32];
+  __shared__ int wcnt[kQuad / 32];
   __shared__ int is_last;
   if (S.st->flags & kDone) return;
-  const int64_t r = (int64_t)blockIdx.x * kTile + threadIdx.x;
+  // a tile of kTile regions per block, 4 consecutive regions per thread
+  const int64_t r = (int64_t)blockIdx.x * kTile + 4 * (int64_t)threadIdx.x;
   const double budget = S.budget_ptr ? *S.budget_ptr : S.budget_val;
-  int split = 0;
-  double ri = 0.0, re = 0.0;
-  if (r < S.n) {
-    const double i7 = S.i7[r];
-    const double e = S.err[r];
-    const uint8_t ax = S.axis[r];
-    const double thr = (S.classifier == GMQ_LOCAL_REL) ? __dmul_rn(S.rel_tol, fabs(i7))
-                                                       : __dmul_rn(budget, S.volfrac[r]);
-    const double guard = __dmul_rn(S.guard, fabs(i7));
-    const bool retire = (e <= thr) || (e <= guard) || (ax & 0x80);
-    split = retire ? 0 : 1;
-    if (retire) {
-      ri = i7;
-      re = e;
-    }
-    S.flags[r] = (uint8_t)split;
+  double i7[4], e[4], vf[4] = {0.0, 0.0, 0.0, 0.0};
+  load4(S.i7, r, S.n, i7);
+  load4(S.err, r, S.n, e);
+  if (S.classifier != GMQ_LOCAL_REL) load4(S.volfrac, r, S.n, vf);
+  uint8_t ax[4] = {0, 0, 0, 0};
+  if (r + 3 < S.n && (reinterpret_cast<uintptr_t>(S.axis + r) & 3u) == 0) {
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(S.axis + r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ax[k] = (uint8_t)(w >> (8 * k));
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ax[k] = r + k < S.n ? S.axis[r + k] : 0;
   }
-  const int cnt = __syncthreads_count(split);
-  const double ta = block_tree_sum(ri, scratch);
-  const double tb = block_tree_sum(re, scratch);
+  int split = 0;
+  double ri[4], re[4];
+  uint8_t fl[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ri[k] = 0.0;
+    re[k] = 0.0;
+    fl[k] = 0;
+    if (r + k < S.n) {
+      const double thr = (S.classifier == GMQ_LOCAL_REL) ? __dmul_rn(S.rel_tol, fabs(i7[k]))
+                                                         : __dmul_rn(budget, vf[k]);
+      const double guard = __dmul_rn(S.guard, fabs(i7[k]));
+      const bool retire = (e[k] <= thr) || (e[k] <= guard) || (ax[k] & 0x80);
+      fl[k] = retire ? 0 : 1;
+      split += fl[k];
+      if (retire) {
+        ri[k] = i7[k];
+        re[k] = e[k];
+      }
+    }
+  }
+  if (r + 3 < S.n && (reinterpret_cast<uintptr_t>(S.flags + r) & 3u) == 0) {
+    *reinterpret_cast<uint32_t*>(S.flags + r) =
+        (uint32_t)fl[0] | ((uint32_t)fl[1] << 8) | ((uint32_t)fl[2] << 16) | ((uint32_t)fl[3] << 24);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (r + k < S.n) S.flags[r + k] = fl[k];
+  }
+  const int wsplit = __reduce_add_sync(0xffffffffu, split);
+  if ((threadIdx.x & 31) == 0) wcnt[threadIdx.x >> 5] = wsplit;
+  const double ta = block_tree_sum((ri[0] + ri[1]) + (ri[2] + ri[3]), scratch);  // syncs
+  const double tb = block_tree_sum((re[0] + re[1]) + (re[2] + re[3]), scratch);
   if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int w = 0; w < kQuad / 32; ++w) cnt += wcnt[w];
     S.blk_count[blockIdx.x] = cnt;
     S.blk_a[blockIdx.x] = ta;
     S.blk_b[blockIdx.x] = tb;
@@ -159,9 +249,9 @@ __global__ void __launch_bounds__(kTile) k_classify(const SweepArgs S) {
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const long long total = block_exclusive_scan(S.blk_count, S.blk_off, gridDim.x, wsum);
-  const double A = tree_sum_global(S.blk_a, gridDim.x, scratch, tile_sums);
-  const double B = tree_sum_global(S.blk_b, gridDim.x, scratch, tile_sums);
+  const long long total = block_exclusive_scan_any(S.blk_count, S.blk_off, gridDim.x, wsum);
+  const double A = tree_sum_global4(S.blk_a, gridDim.x, scratch, tile_sums);
+  const double B = tree_sum_global4(S.blk_b, gridDim.x, scratch, tile_sums);
   if (threadIdx.x == 0) {
     DevStatus* st = S.st;
     st->ticket_cls = 0u;
@@ -217,19 +307,32 @@ __global__ void __launch_bounds__(kTile) k_split(const SweepArgs S) {
   }
   const long long ns = S.st->n_split;
   const int ax = S.axis[r] & 0x7f;
-  for (int k = 0; k < S.d; ++k) {
-    const double c = S.c[(int64_t)k * S.ld + r];
-    const double h = S.h[(int64_t)k * S.ld + r];
-    double cl = c, cr = c, hc = h;
-    if (k == ax) {
-      hc = __dmul_rn(0.5, h);
-      cl = __dsub_rn(c, hc);
-      cr = __dadd_rn(c, hc);
+  // four axes per step, every load issued before the stores
+  for (int k0 = 0; k0 < S.d; k0 += 4) {
+    double cv[4], hv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (k0 + q < S.d) {
+        cv[q] = S.c[(int64_t)(k0 + q) * S.ld + r];
+        hv[q] = S.h[(int64_t)(k0 + q) * S.ld + r];
+      }
     }
-    S.c_out[(int64_t)k * S.ld_out + pos] = cl;
-    S.h_out[(int64_t)k * S.ld_out + pos] = hc;
-    S.c_out[(int64_t)k * S.ld_out + ns + pos] = cr;
-    S.h_out[(int64_t)k * S.ld_out + ns + pos] = hc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + q;
+      if (k < S.d) {
+        double cl = cv[q], cr = cv[q], hc = hv[q];
+        if (k == ax) {
+          hc = __dmul_rn(0.5, hv[q]);
+          cl = __dsub_rn(cv[q], hc);
+          cr = __dadd_rn(cv[q], hc);
+        }
+        S.c_out[(int64_t)k * S.ld_out + pos] = cl;
+        S.h_out[(int64_t)k * S.ld_out + pos] = hc;
+        S.c_out[(int64_t)k * S.ld_out + ns + pos] = cr;
+        S.h_out[(int64_t)k * S.ld_out + ns + pos] = hc;
+      }
+    }
   }
 }
 
@@ -310,14 +413,14 @@ cudaError_t launch_rows_tree_sum(const double* v, int64_t ldv, int64_t n, int ro
 cudaError_t launch_sum_status(const SweepArgs& S, cudaStream_t s) {
   const int64_t blocks = (S.n + kTile - 1) / kTile;
   if (blocks == 0) return cudaSuccess;
-  k_sum_status<<<(unsigned)blocks, kTile, 0, s>>>(S);
+  k_sum_status<<<(unsigned)blocks, kQuad, 0, s>>>(S);
   return cudaGetLastError();
 }
 
 cudaError_t launch_classify(const SweepArgs& S, cudaStream_t s) {
   const int64_t blocks = (S.n + kTile - 1) / kTile;
   if (blocks == 0) return cudaSuccess;
-  k_classify<<<(unsigned)blocks, kTile, 0, s>>>(S);
+  k_classify<<<(unsigned)blocks, kQuad, 0, s>>>(S);
   return cudaGetLastError();
 }
 
