@@ -220,14 +220,15 @@ def dist_setup():
 
 def _oracle_one(job):
     """One integration by the CPU oracle in a host process, unless the
-    sample's wall-clock deadline has passed.  Returns (regions, done)."""
-    p, deadline = job
+    sample's wall-clock deadline has passed.  Returns (regions, done,
+    integral, status)."""
+    p, deadline, cap = job
     if time.time() > deadline:
-        return 0, 0
+        return 0, 0, 0.0, -1
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
-    r = O.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=ORACLE_CAP)
-    return r.regions_evaluated, 1
+    r = O.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=cap)
+    return r.regions_evaluated, 1, r.integral, r.status
 
 
 def _oracle_load(_):
@@ -263,14 +264,15 @@ class OraclePool:
             self.pool = mp.get_context("spawn").Pool(procs)
             self.pool.map(_oracle_load, range(procs), chunksize=1)
 
-    def run(self, probs, seconds):
+    def run(self, probs, seconds, cap=None):
         t0 = time.perf_counter()
-        jobs = [(p, time.time() + seconds) for p in probs]
+        jobs = [(p, time.time() + seconds, cap or ORACLE_CAP) for p in probs]
         if self.pool:
             outs = self.pool.map(_oracle_one, jobs, chunksize=1)
         else:
             outs = [_oracle_one(j) for j in jobs]
         wall = time.perf_counter() - t0
+        self.last = outs
         return sum(o[0] for o in outs) / wall, sum(o[1] for o in outs), wall
 
     def close(self):
@@ -319,11 +321,20 @@ def cpu_baseline(args, seconds):
     pool = OraclePool(cores)
     v, done, wall = pool.run(probs, seconds)
     pool.close()
+    # time to 1e-6 on the 40 tolerance-1e-6 problems, all cores, pool 2^22
+    from paper_2511_01573_gb300 import genz_inputs as G
+    p6 = G.genz_d8_problems(tols=(1e-6,))
+    pool = OraclePool(cores)
+    _, done6, wall6 = pool.run(p6, 3600.0, cap=1 << 22)
+    conv6 = sum(1 for o in pool.last if o[3] == 0)
+    pool.close()
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{done} of {len(probs)} integrations in tolerance order, one process "
                       f"per core, started within {seconds:.0f} s ({wall:.1f} s), pool 2^16",
             "single_core": {"value": v1, "cores": 1,
-                            "sample": f"first {done1} integrations ({wall1:.1f} s)"}}
+                            "sample": f"first {done1} integrations ({wall1:.1f} s)"},
+            "time_to_1e-6": {"s": wall6, "problems": done6, "converged": conv6,
+                             "cores": cores, "pool": "2^22 per integration"}}
 
 
 def probe_rule(args):
