@@ -345,6 +345,14 @@ gmq_status gmq_eval_rule_gk(gmq_context *ctx, const gmq_problem *prob, int64_t n
  * the Kronrod weights); no device work. */
 gmq_status gmq_gk_table(double *out);
 
+/* The FP64 exponential the built-in integrands use (Tang's table-driven
+ * method; within about one ulp), on n device values: d_y[i] = exp(d_x[i]).
+ * No counterpart in the paper; exposed so that its accuracy can be tested
+ * against the CUDA and host libraries.  Synchronous on the context
+ * stream. */
+gmq_status gmq_math_exp(gmq_context *ctx, int64_t n, const double *d_x,
+                        double *d_y);
+
 /* Classification and bisection of one sweep (paper Sec. 3) given the rule
  * outputs above and the sweep's budget = max(abs_tol, rel_tol |I|).
  * Region r is retired if eps_r <= budget * volfrac_r (GMQ_VOLUME_SHARE) or

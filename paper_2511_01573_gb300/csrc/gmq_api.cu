@@ -1018,6 +1018,29 @@ gmq_status gmq_eval_rule_gk(gmq_context* ctx, const gmq_problem* prob, int64_t n
   return GMQ_OK;
 }
 
+}  // extern "C"
+
+namespace {
+__global__ void k_math_exp(int64_t n, const double* x, double* y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = gm_exp(x[i]);
+}
+}  // namespace
+
+extern "C" {
+
+gmq_status gmq_math_exp(gmq_context* ctx, int64_t n, const double* d_x, double* d_y) {
+  if (!ctx || n < 0 || (n > 0 && (!d_x || !d_y))) return GMQ_ERR_INVALID;
+  if (n == 0) return GMQ_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  k_math_exp<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, d_x, d_y);
+  GMQ_CK(cudaGetLastError());
+  ctx->launches += 1;
+  GMQ_CK(cudaStreamSynchronize(ctx->stream));
+  return GMQ_OK;
+}
+
 gmq_status gmq_gk_table(double* out) {
   if (!out) return GMQ_ERR_INVALID;
   const GkConst& K = gk_const();

@@ -64,7 +64,8 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_status_string", "gmq_launch_count", "gmq_eval_rule", "gmq_classify_split",
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
            "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad",
-           "gmq_integrate_batch", "gmq_last_batch_info", "gmq_eval_rule_gk", "gmq_gk_table")
+           "gmq_integrate_batch", "gmq_last_batch_info", "gmq_eval_rule_gk", "gmq_gk_table",
+           "gmq_math_exp")
 
 KEEP_PARTITION = 1
 BATCH_HOST_LOOP = 2
@@ -143,6 +144,7 @@ def lib():
         "gmq_last_batch_info": [vp, C.POINTER(BatchInfo)],
         "gmq_eval_rule_gk": [vp, C.POINTER(Problem), i64, vp, vp, i64, vp, vp, vp, vp],
         "gmq_gk_table": [_dp],
+        "gmq_math_exp": [vp, i64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -452,6 +454,14 @@ class Context:
             self.h, C.byref(p.s), n, _dptr(center), _dptr(halfw), ld, _dptr(ik), _dptr(err),
             _dptr(vf), _dptr(ax)))
         return ik, err, vf, ax
+
+    def math_exp(self, x):
+        """The library's FP64 exponential on a CUDA float64 tensor."""
+        torch = self.torch
+        x = self._dev(x, torch.float64).contiguous()
+        y = torch.empty_like(x)
+        _check("gmq_math_exp", lib().gmq_math_exp(self.h, x.numel(), _dptr(x), _dptr(y)))
+        return y
 
     def classify_split(self, center, halfw, i7, err, volfrac, axis, budget, rel_tol=0.0,
                        classifier=VOLUME_SHARE, cap_out=None):
