@@ -353,6 +353,13 @@ gmq_status gmq_gk_table(double *out);
 gmq_status gmq_math_exp(gmq_context *ctx, int64_t n, const double *d_x,
                         double *d_y);
 
+/* The FP64 reciprocal the product-peak and corner-peak integrands use (the
+ * hardware approximation refined by two Newton-Raphson steps; within one
+ * ulp), on n device values: d_y[i] = 1 / d_x[i].  Exposed for testing, as
+ * gmq_math_exp. */
+gmq_status gmq_math_rcp(gmq_context *ctx, int64_t n, const double *d_x,
+                        double *d_y);
+
 /* Classification and bisection of one sweep (paper Sec. 3) given the rule
  * outputs above and the sweep's budget = max(abs_tol, rel_tol |I|).
  * Region r is retired if eps_r <= budget * volfrac_r (GMQ_VOLUME_SHARE) or

@@ -1,7 +1,9 @@
 """The library's FP64 exponential (Tang's table-driven method, used by the
-Gaussian, C0 and discontinuous integrands) against the host's libm and
-CUDA's exp: within 2 ulp of both on random arguments over the whole fast
-range and on the edges of the fallback to the library exp."""
+Gaussian, C0 and discontinuous integrands) and reciprocal (Newton-Raphson
+from the hardware approximation, used by the product-peak and corner-peak
+integrands) against the host's arithmetic and CUDA's: within 2 ulp (exp)
+and 1 ulp (reciprocal) on random arguments over the whole fast range and at
+the edges of the fallback to the library routine."""
 import numpy as np
 import pytest
 
@@ -37,3 +39,23 @@ def test_exp_accuracy(gpu_ctx):
     assert np.all(y[x == 0.0] == 1.0)
     nan = gpu_ctx.math_exp(torch.tensor([np.nan], dtype=torch.float64, device="cuda"))
     assert torch.isnan(nan).all()
+
+
+def test_rcp_accuracy(gpu_ctx):
+    rng = np.random.default_rng(1573)
+    mag = np.exp2(rng.uniform(-119.9, 119.9, 1 << 20))
+    x = np.concatenate([
+        mag * np.where(rng.random(mag.size) < 0.5, -1.0, 1.0),
+        rng.uniform(1.0, 2.0, 1 << 18),
+        np.array([1.0, -1.0, 2.0, 0.5, 3.0, 2.0 ** -120, 2.0 ** 120, 2.0 ** -121, 2.0 ** 121,
+                  2.0 ** -1070, 1e300, -1e-300, 0.0, -0.0, np.inf, -np.inf]),
+    ])
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    y = gpu_ctx.math_rcp(xd).cpu().numpy()
+    with np.errstate(divide="ignore", over="ignore"):
+        ref = 1.0 / x  # IEEE division: correctly rounded
+    fast = np.abs(x) >= 2.0 ** -120
+    fast &= np.abs(x) <= 2.0 ** 120
+    assert np.max(_ulps(y[fast], ref[fast])) <= 1.0
+    slow = ~fast
+    assert np.array_equal(y[slow], ref[slow])
