@@ -360,6 +360,12 @@ gmq_status gmq_math_exp(gmq_context *ctx, int64_t n, const double *d_x,
 gmq_status gmq_math_rcp(gmq_context *ctx, int64_t n, const double *d_x,
                         double *d_y);
 
+/* The FP64 cosine the oscillatory integrand uses (table-driven; absolute
+ * error within a few units of 2^-53), on n device values: d_y[i] =
+ * cos(d_x[i]).  Exposed for testing, as gmq_math_exp. */
+gmq_status gmq_math_cos(gmq_context *ctx, int64_t n, const double *d_x,
+                        double *d_y);
+
 /* Classification and bisection of one sweep (paper Sec. 3) given the rule
  * outputs above and the sweep's budget = max(abs_tol, rel_tol |I|).
  * Region r is retired if eps_r <= budget * volfrac_r (GMQ_VOLUME_SHARE) or

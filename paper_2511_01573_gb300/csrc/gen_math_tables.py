@@ -1,0 +1,144 @@
+"""Writes gm_math_tables.cuh: the constants of the library's FP64 exponential
+and cosine (gmq_families.cuh, gm_exp and gm_cos), computed in decimal
+arithmetic with 60 significant digits.
+
+Method: Tang's table-driven exponential (P. T. P. Tang, ACM TOMS 15(2),
+1989).  x = (64 m + j) ln2/64 + r, |r| <= ln2/128, exp(x) = 2^m 2^(j/64)
+exp(r).  The table holds 2^(j/64), j = 0..63, rounded to nearest; ln2/64 is
+split into L1 (36 significant bits, so n L1 is exact for |n| < 2^17) and
+L2 = ln2/64 - L1 rounded; exp(r) - 1 is the Taylor polynomial of degree 5
+(its truncation error r^6/720 is below 3.6e-17 relative).
+
+Cosine, by the same table-driven scheme (J.-M. Muller, Elementary Functions,
+ch. 6): x = n pi/32 + r, |r| <= pi/64, cos(x) = C_j cos(r) - S_j sin(r) with
+j = n mod 64, C_j = cos(j pi/32), S_j = sin(j pi/32); pi/32 is split into
+three parts P1, P2 (33 significant bits each, so n P1 and n P2 are exact for
+|n| < 2^20) and P3.
+
+Run from this directory: python gen_math_tables.py
+"""
+from decimal import Decimal, getcontext
+import math
+
+getcontext().prec = 60
+
+
+def dec_ln2():
+    # ln 2 = sum_{k>=1} 1 / (k 2^k)
+    s, t = Decimal(0), Decimal(1)
+    for k in range(1, 400):
+        t /= 2
+        s += t / k
+    return s
+
+
+def dec_exp(x):
+    s, t, k = Decimal(1), Decimal(1), 0
+    while True:
+        k += 1
+        t = t * x / k
+        if abs(t) < Decimal(10) ** -58:
+            return s + t
+        s += t
+
+
+def dec_pi():
+    # Machin: pi = 16 atan(1/5) - 4 atan(1/239)
+    def atan_inv(q):
+        s, t, k = Decimal(0), Decimal(1) / q, 0
+        while abs(t) > Decimal(10) ** -59:
+            s += t / (2 * k + 1) * (-1) ** k
+            t /= q * q
+            k += 1
+        return s
+    return 16 * atan_inv(5) - 4 * atan_inv(239)
+
+
+def dec_cos_sin(x):
+    c, s, t, k = Decimal(0), Decimal(0), Decimal(1), 0
+    while abs(t) > Decimal(10) ** -58 or k < 4:
+        if k % 4 == 0:
+            c += t
+        elif k % 4 == 1:
+            s += t
+        elif k % 4 == 2:
+            c -= t
+        else:
+            s -= t
+        k += 1
+        t = t * x / k
+    return c, s
+
+
+def split_bits(d: Decimal, bits: int) -> float:
+    m, e = math.frexp(float(d))
+    scale = Decimal(2) ** (bits - e)
+    return float((d * scale).to_integral_value() / scale)
+
+
+def to_double(d: Decimal) -> float:
+    """Round a Decimal to the nearest double (ties to even)."""
+    f = float(d)  # correctly rounded: Python converts via the exact decimal string
+    return f
+
+
+def split36(d: Decimal) -> float:
+    """d rounded to 36 significant bits."""
+    m, e = math.frexp(float(d))
+    scale = Decimal(2) ** (36 - e)
+    return float((d * scale).to_integral_value() / scale)
+
+
+def main():
+    ln2 = dec_ln2()
+    c = ln2 / 64
+    l1 = split36(c)
+    l2 = to_double(c - Decimal(l1))
+    inv = to_double(64 / ln2)
+    tab = [to_double(dec_exp(ln2 * j / 64)) for j in range(64)]
+    pi = dec_pi()
+    q = pi / 32
+    p1 = split_bits(q, 33)
+    p2 = split_bits(q - Decimal(p1), 33)
+    p3 = to_double(q - Decimal(p1) - Decimal(p2))
+    invq = to_double(32 / pi)
+    # cos and sin of j pi/32; the exact zeros (j = 0, 16, 32, 48) come out of
+    # the series as residues below 1e-40 and are set to 0
+    cs = [tuple(Decimal(0) if abs(v) < Decimal(10) ** -40 else v for v in dec_cos_sin(pi * j / 32))
+          for j in range(64)]
+    lines = [
+        "// gm_math_tables.cuh -- generated by gen_math_tables.py (decimal arithmetic, 60",
+        "// digits); constants of gm_exp and gm_cos (gmq_families.cuh).",
+        "#pragma once",
+        "",
+        "namespace gmq {",
+        "",
+        f"constexpr double kExpInvL = {inv!r};  // 64 / ln 2",
+        f"constexpr double kExpL1 = {l1!r};  // ln2/64, 36 significant bits",
+        f"constexpr double kExpL2 = {l2!r};  // ln2/64 - kExpL1",
+        "",
+        "// 2^(j/64), j = 0..63, rounded to nearest",
+        "static __device__ const double kExp2Tab[64] = {",
+    ]
+    for i in range(0, 64, 2):
+        lines.append(f"    {tab[i]!r}, {tab[i + 1]!r},")
+    lines += ["};", "",
+              f"constexpr double kCosInvQ = {invq!r};  // 32 / pi",
+              f"constexpr double kCosP1 = {p1!r};  // pi/32, 33 significant bits",
+              f"constexpr double kCosP2 = {p2!r};  // next 33 bits",
+              f"constexpr double kCosP3 = {p3!r};  // pi/32 - P1 - P2",
+              "",
+              "// cos(j pi/32) and sin(j pi/32), j = 0..63, rounded to nearest",
+              "static __device__ const double kCosTab[64] = {"]
+    for i in range(0, 64, 2):
+        lines.append(f"    {to_double(cs[i][0])!r}, {to_double(cs[i + 1][0])!r},")
+    lines += ["};", "static __device__ const double kSinTab[64] = {"]
+    for i in range(0, 64, 2):
+        lines.append(f"    {to_double(cs[i][1])!r}, {to_double(cs[i + 1][1])!r},")
+    lines += ["};", "", "}  // namespace gmq", ""]
+    with open("gm_math_tables.cuh", "w") as f:
+        f.write("\n".join(lines))
+
+
+if __name__ == "__main__":
+    main()

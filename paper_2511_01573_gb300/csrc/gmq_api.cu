@@ -1029,6 +1029,10 @@ __global__ void k_math_rcp(int64_t n, const double* x, double* y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = gm_rcp(x[i]);
 }
+__global__ void k_math_cos(int64_t n, const double* x, double* y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = gm_cos(x[i]);
+}
 }  // namespace
 
 extern "C" {
@@ -1051,6 +1055,18 @@ gmq_status gmq_math_rcp(gmq_context* ctx, int64_t n, const double* d_x, double* 
   DeviceGuard g(ctx->device);
   if (!g.ok) return GMQ_ERR_CUDA;
   k_math_rcp<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, d_x, d_y);
+  GMQ_CK(cudaGetLastError());
+  ctx->launches += 1;
+  GMQ_CK(cudaStreamSynchronize(ctx->stream));
+  return GMQ_OK;
+}
+
+gmq_status gmq_math_cos(gmq_context* ctx, int64_t n, const double* d_x, double* d_y) {
+  if (!ctx || n < 0 || (n > 0 && (!d_x || !d_y))) return GMQ_ERR_INVALID;
+  if (n == 0) return GMQ_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  k_math_cos<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, d_x, d_y);
   GMQ_CK(cudaGetLastError());
   ctx->launches += 1;
   GMQ_CK(cudaStreamSynchronize(ctx->stream));

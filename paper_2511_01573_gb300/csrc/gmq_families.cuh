@@ -6,7 +6,7 @@
 // Real = double is the FP64 path; Real = float the mixed path's integrand.
 #pragma once
 
-#include "gm_exp_table.cuh"
+#include "gm_math_tables.cuh"
 #include "gmq_common.cuh"
 
 namespace gmq {
@@ -26,8 +26,8 @@ struct SmemParams {
 // (truncation below 3.6e-17), 2^(j/64) comes from a 64-entry table and 2^m
 // is added to the exponent field.  About 10 FP64 instructions against the
 // ~16 the rule kernels measured for the library exp, within about one ulp
-// of the exact value (gm_exp_table.cuh holds the constants, computed in
-// exact arithmetic).  |x| >= 707 (results near or past the overflow and
+// of the exact value (gm_math_tables.cuh holds the constants, computed in
+// 60-digit decimal arithmetic).  |x| >= 707 (results near or past the overflow and
 // subnormal ranges) and NaN go to the library exp.
 __device__ __forceinline__ double gm_exp(double x) {
   if (!(fabs(x) < 707.0)) return exp(x);
@@ -69,7 +69,34 @@ __device__ __forceinline__ double gm_rcp(double x) {
 __device__ __forceinline__ float grcp(float x) { return 1.0f / x; }
 __device__ __forceinline__ double grcp(double x) { return gm_rcp(x); }
 __device__ __forceinline__ float gexp(float x) { return expf(x); }
-__device__ __forceinline__ double gcos(double x) { return cos(x); }
+// FP64 cosine by the same table-driven scheme (J.-M. Muller, Elementary
+// Functions, ch. 6): x = n pi/32 + r with a three-part Cody-Waite reduction
+// (exact for |n| < 2^20), |r| <= pi/64; cos(x) = C_j cos(r) - S_j sin(r),
+// j = n mod 64, with C_j = cos(j pi/32), S_j = sin(j pi/32) from 64-entry
+// tables, cos(r) - 1 and sin(r) by their Taylor polynomials of degree 8 and 7
+// (truncation below 1e-19).  About 16 FP64 instructions; absolute error
+// within a few units of 2^-53.  |x| >= 1e5 and non-finite x: the library cos.
+__device__ __forceinline__ double gm_cos(double x) {
+  if (!(fabs(x) < 1e5)) return cos(x);
+  const double shifter = 6755399441055744.0;  // 1.5 * 2^52
+  const double t = fma(x, kCosInvQ, shifter);
+  const int n = __double2loint(t);            // round(x * 32 / pi)
+  const double nd = __dsub_rn(t, shifter);
+  double r = fma(-nd, kCosP1, x);             // exact
+  r = fma(-nd, kCosP2, r);                    // exact
+  r = fma(-nd, kCosP3, r);
+  const double z = __dmul_rn(r, r);
+  double c = fma(z, 1.0 / 40320.0, -1.0 / 720.0);
+  c = fma(c, z, 1.0 / 24.0);
+  c = fma(c, z, -0.5);
+  const double cm1 = __dmul_rn(c, z);         // cos(r) - 1
+  double sp = fma(z, -1.0 / 5040.0, 1.0 / 120.0);
+  sp = fma(sp, z, -1.0 / 6.0);
+  const double sr = fma(__dmul_rn(r, z), sp, r);  // sin(r)
+  const double C = __ldg(&kCosTab[n & 63]), S = __ldg(&kSinTab[n & 63]);
+  return fma(-S, sr, fma(C, cm1, C));
+}
+__device__ __forceinline__ double gcos(double x) { return gm_cos(x); }
 __device__ __forceinline__ float gcos(float x) { return cosf(x); }
 
 // x^e for a positive integer exponent by binary powering.

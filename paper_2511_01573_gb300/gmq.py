@@ -65,7 +65,7 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
            "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad",
            "gmq_integrate_batch", "gmq_last_batch_info", "gmq_eval_rule_gk", "gmq_gk_table",
-           "gmq_math_exp", "gmq_math_rcp")
+           "gmq_math_exp", "gmq_math_rcp", "gmq_math_cos")
 
 KEEP_PARTITION = 1
 BATCH_HOST_LOOP = 2
@@ -146,6 +146,7 @@ def lib():
         "gmq_gk_table": [_dp],
         "gmq_math_exp": [vp, i64, vp, vp],
         "gmq_math_rcp": [vp, i64, vp, vp],
+        "gmq_math_cos": [vp, i64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -470,6 +471,14 @@ class Context:
         x = self._dev(x, torch.float64).contiguous()
         y = torch.empty_like(x)
         _check("gmq_math_rcp", lib().gmq_math_rcp(self.h, x.numel(), _dptr(x), _dptr(y)))
+        return y
+
+    def math_cos(self, x):
+        """The library's FP64 cosine on a CUDA float64 tensor."""
+        torch = self.torch
+        x = self._dev(x, torch.float64).contiguous()
+        y = torch.empty_like(x)
+        _check("gmq_math_cos", lib().gmq_math_cos(self.h, x.numel(), _dptr(x), _dptr(y)))
         return y
 
     def classify_split(self, center, halfw, i7, err, volfrac, axis, budget, rel_tol=0.0,

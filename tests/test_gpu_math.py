@@ -59,3 +59,28 @@ def test_rcp_accuracy(gpu_ctx):
     assert np.max(_ulps(y[fast], ref[fast])) <= 1.0
     slow = ~fast
     assert np.array_equal(y[slow], ref[slow])
+
+
+def test_cos_accuracy(gpu_ctx):
+    """Absolute error within 4 units of 2^-53 of the correctly rounded value
+    (the table-driven scheme is not relatively accurate next to the zeros of
+    cos, which the quadrature sums do not need), 2 ulp where |cos x| >= 1/2."""
+    rng = np.random.default_rng(7)
+    x = np.concatenate([
+        rng.uniform(-100.0, 100.0, 1 << 20),
+        rng.uniform(0.0, 15.0, 1 << 18),             # the oscillatory family's range
+        rng.uniform(-99999.0, 99999.0, 1 << 16),
+        np.pi / 32 * np.arange(-200, 201) + 1e-12,  # table boundaries
+        np.array([0.0, -0.0, 1e-300, np.pi / 2, np.pi, 1e5, -1e5, 1e6, np.inf, np.nan]),
+    ])
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    y = gpu_ctx.math_cos(xd).cpu().numpy()
+    ref_cuda = torch.cos(xd).cpu().numpy()
+    ref_host = np.cos(x)
+    fast = np.abs(x) < 1e5
+    assert np.max(np.abs(y[fast] - ref_host[fast])) <= 4 * 2.0 ** -53
+    assert np.max(np.abs(y[fast] - ref_cuda[fast])) <= 4 * 2.0 ** -53
+    big = fast & (np.abs(ref_host) >= 0.5)
+    assert np.max(_ulps(y[big], ref_host[big])) <= 2.0
+    slow = ~fast
+    assert np.array_equal(y[slow], ref_cuda[slow], equal_nan=True)
