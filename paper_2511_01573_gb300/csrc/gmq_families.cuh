@@ -27,10 +27,11 @@ struct SmemParams {
 // is added to the exponent field.  About 10 FP64 instructions against the
 // ~16 the rule kernels measured for the library exp, within about one ulp
 // of the exact value (gm_math_tables.cuh holds the constants, computed in
-// 60-digit decimal arithmetic).  |x| >= 707 (results near or past the overflow and
+// 60-digit decimal arithmetic).  |x| >= 512 (which covers the overflow and
 // subnormal ranges) and NaN go to the library exp.
 __device__ __forceinline__ double gm_exp(double x) {
-  if (!(fabs(x) < 707.0)) return exp(x);
+  // |x| < 512, tested on the high word (no FP64 compare)
+  if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40800000u) return exp(x);
   const double shifter = 6755399441055744.0;  // 1.5 * 2^52: low word of t = nearest integer
   const double t = fma(x, kExpInvL, shifter);
   const int n = __double2loint(t);            // round(x * 64 / ln2)
@@ -75,9 +76,11 @@ __device__ __forceinline__ float gexp(float x) { return expf(x); }
 // j = n mod 64, with C_j = cos(j pi/32), S_j = sin(j pi/32) from 64-entry
 // tables, cos(r) - 1 and sin(r) by their Taylor polynomials of degree 8 and 7
 // (truncation below 1e-19).  About 16 FP64 instructions; absolute error
-// within a few units of 2^-53.  |x| >= 1e5 and non-finite x: the library cos.
+// within a few units of 2^-53.  |x| >= 2^16 and non-finite x: the library
+// cos.
 __device__ __forceinline__ double gm_cos(double x) {
-  if (!(fabs(x) < 1e5)) return cos(x);
+  // |x| < 2^16, tested on the high word (no FP64 compare)
+  if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40f00000u) return cos(x);
   const double shifter = 6755399441055744.0;  // 1.5 * 2^52
   const double t = fma(x, kCosInvQ, shifter);
   const int n = __double2loint(t);            // round(x * 32 / pi)
