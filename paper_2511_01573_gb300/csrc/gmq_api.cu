@@ -436,6 +436,18 @@ cudaError_t launch_rule_gk(int fam, const GkArgs& G, cudaStream_t s) {
   }
 }
 
+// Two CUDA events released when the holder goes out of scope.
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
 // Name of the last CUDA error a call of this thread turned into a status.
 thread_local const char* g_last_cuda_error = "cudaSuccess";
 
@@ -1515,9 +1527,10 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     ctx->launches += 1;
     const int modes[3] = {1, 4, 32};
     int best[5];
-    cudaEvent_t e0, e1;
-    GMQ_CK(cudaEventCreate(&e0));
-    GMQ_CK(cudaEventCreate(&e1));
+    EventPair ev;  // destroyed on every return path
+    GMQ_CK(cudaEventCreate(&ev.a));
+    GMQ_CK(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     for (int i = 0; i < nl; ++i) {
       float mbest = 1e30f;
       float ms[3];
@@ -1542,8 +1555,6 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
         if (ms[m] <= 1.05f * mbest) best[i] = m;
       info.tune_n[i] = lens[i];
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     auto between = [&](int i) -> long long {  // geometric middle of lens[i-1], lens[i]
       return (long long)std::llround(std::sqrt((double)lens[i - 1] * (double)lens[i]));
     };
