@@ -119,10 +119,10 @@ typedef struct gmq_options {
   int32_t precision;   /* gmq_precision                                     */
   int32_t classifier;  /* gmq_classifier                                    */
   int32_t lanes;       /* threads per region in the rule kernel: 0 = chosen
-                          per sweep by the library, else 1, 4 or 32.  FP64
-                          results do not depend on it (every class sum is
-                          one fixed tree); mixed-precision results do, at
-                          the level of FP32 rounding                        */
+                          per sweep by the library, else 1, 4, 32 or (FP64
+                          only) 128.  FP64 results do not depend on it
+                          (every class sum is one fixed tree); mixed-
+                          precision results do, at FP32 rounding level      */
   int32_t flags;       /* 0, or GMQ_KEEP_PARTITION                           */
   int32_t rule;        /* gmq_rule (GMQ_RULE_GENZ_MALIK by default)          */
 } gmq_options;
@@ -222,11 +222,12 @@ typedef struct gmq_batch_info {
   int32_t evictions;    /* problems evicted and restarted to make room      */
   int32_t forced_lanes; /* opt->lanes when nonzero, else 0                  */
   int64_t lanes_t1;     /* lists of >= lanes_t1 regions: 1 lane per region  */
-  int64_t lanes_t4;     /* >= lanes_t4: 4 lanes; shorter lists: 32 (a warp)  */
-  int32_t lane_sweeps[3]; /* sweeps run with 1, 4 and 32 lanes per region   */
-  int32_t reserved;
+  int64_t lanes_t4;     /* >= lanes_t4: 4 lanes                             */
+  int64_t lanes_t32;    /* >= lanes_t32: 32 (a warp); shorter lists: 128 (a
+                           128-thread block per region)                     */
+  int32_t lane_sweeps[4]; /* sweeps run with 1, 4, 32 and 128 lanes        */
   int64_t tune_n[5];    /* list lengths the autotuner timed (0 if unused)   */
-  double tune_ms[5][3]; /* rule-kernel time per length and mapping 1/4/32   */
+  double tune_ms[5][4]; /* rule-kernel time per length and mapping 1/4/32/128 */
 } gmq_batch_info;
 
 /* Many independent integrals in one device-resident loop (no counterpart in
@@ -248,10 +249,10 @@ typedef struct gmq_batch_info {
  * GMQ_CAP_REACHED.  The device loop is bounded by 4 x max_iters sweeps.
  * Device memory: about pool_regions x (32 dmax + 60) bytes, dmax the
  * largest dimension.
- * opt->precision GMQ_FP64: lanes per region opt->lanes (1, 4 or 32) for
- * every sweep, or with 0 chosen per sweep from the list length by
+ * opt->precision GMQ_FP64: lanes per region opt->lanes (1, 4, 32 or 128)
+ * for every sweep, or with 0 chosen per sweep from the list length by
  * thresholds an autotuner sets on the first call for each largest dimension
- * (it times the three mappings on copies of the initial list at up to five
+ * (it times the four mappings on copies of the initial list at up to five
  * lengths; cached in the context); the results do not depend on the
  * mapping.  opt->precision GMQ_MIXED: one lane per region (opt->lanes must
  * be 0 or 1), one rule launch per family present per sweep, and every
@@ -320,7 +321,8 @@ gmq_status gmq_profile_read(gmq_context *ctx, int32_t kernel, gmq_kernel_stats *
  * vol_r / vol(Omega) with vol_r = prod_k 2 h_k and vol(Omega) from the
  * problem's lo, hi; d_axis[r] = split axis in bits 0..6, bit 7 set when
  * bisecting along that axis cannot move the centre (round-off guard).
- * precision: gmq_precision; lanes: 0, 1, 4 or 32 as in gmq_options.
+ * precision: gmq_precision; lanes: 0, 1, 4, 32 or (FP64) 128 as in
+ * gmq_options.
  * d_volfrac may be NULL. */
 gmq_status gmq_eval_rule(gmq_context *ctx, const gmq_problem *prob,
                          int32_t precision, int32_t lanes, int64_t n,

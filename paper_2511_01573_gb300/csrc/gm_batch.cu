@@ -8,7 +8,7 @@
 // owns the contiguous segment [off_i, off_i + n_i) of the current list (SoA,
 // dmax rows, plus an int32 owner id per region).  Per sweep:
 //   k_batch_rule      all regions of all integrals, persistent grid; family
-//                     and dimension per region; 1, 4 or 32 lanes per region,
+//                     and dimension per region; 1, 4, 32 or 128 lanes per region,
 //                     chosen per sweep from the list length (the per-region
 //                     work is gm_region64.cuh's, so the choice never changes
 //                     a result)
@@ -164,7 +164,7 @@ __device__ __forceinline__ void batch_rule_lanes(const BatchArgs& B, double* sme
   for (long long tile = blockIdx.x; tile * RPB < n_total; tile += gridDim.x) {
     const long long r = tile * RPB + g;
     if (r >= n_total) break;  // so are the group's later tiles
-    __syncwarp(mask);         // the group is done with the previous region's table
+    group_sync<T>(mask);      // the group is done with the previous region's table
     const BatchItem& it = B.items[rid[r]];
     if (it.paused) continue;  // carried over with last sweep's outputs
     const int d = it.P.d;
@@ -180,7 +180,7 @@ __device__ __forceinline__ void batch_rule_lanes(const BatchArgs& B, double* sme
       col[(long long)kXM5 * dm * RPB] = fma(-B.lam5, hv, cv);
       col[(long long)kXRows * dm * RPB] = hv;
     }
-    __syncwarp(mask);
+    group_sync<T>(mask);
     const unsigned short* pairs = pairs_all + batch_pairs_offset(d);
     RegionSums o;
     double* fv = fvs + g;
@@ -216,14 +216,16 @@ __device__ __forceinline__ void batch_rule_lanes(const BatchArgs& B, double* sme
 }
 
 // Rule evaluation of every region of the current list: persistent grid of
-// kBatchRuleBlock-thread blocks, T = bs->lanes lanes per region (set per
-// sweep by k_batch_advance; the results do not depend on it).
+// kBatchRuleBlock-thread blocks, T = bs->lanes lanes per region (1, 4, 32,
+// or 128 = the block; set per sweep by k_batch_advance; the results do not
+// depend on it).
 __global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule(const BatchArgs B) {
   extern __shared__ __align__(16) double smem[];
   const int dm = B.dmax;
   long long most = batch_rule_doubles(dm, 1);
   if (batch_rule_doubles(dm, 4) > most) most = batch_rule_doubles(dm, 4);
   if (batch_rule_doubles(dm, 32) > most) most = batch_rule_doubles(dm, 32);
+  if (batch_rule_doubles(dm, 128) > most) most = batch_rule_doubles(dm, 128);
   unsigned short* pairs_all = reinterpret_cast<unsigned short*>(smem + most);
   for (int e = 2; e <= dm; ++e) {
     const int np = e * (e - 1) / 2;
@@ -238,7 +240,9 @@ __global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule(const BatchArgs 
   }
   __syncthreads();
   const int lanes = B.bs->lanes;
-  if (lanes == 32)
+  if (lanes == 128)
+    batch_rule_lanes<128>(B, smem, pairs_all);
+  else if (lanes == 32)
     batch_rule_lanes<32>(B, smem, pairs_all);
   else if (lanes == 4)
     batch_rule_lanes<4>(B, smem, pairs_all);
@@ -726,7 +730,7 @@ __global__ void k_batch_tile(const BatchArgs B, long long n0, long long n) {
 __global__ void k_batch_advance(const BatchArgs B) {
   BatchState* bs = B.bs;
   const int used = bs->lanes;
-  bs->lane_sweeps[used == 32 ? 2 : (used == 4 ? 1 : 0)] += 1;
+  bs->lane_sweeps[used == 128 ? 3 : (used == 32 ? 2 : (used == 4 ? 1 : 0))] += 1;
   bs->n_total = bs->n_next;
   bs->n_tiles = bs->n_tiles_next;
   bs->parity ^= 1;
@@ -742,6 +746,7 @@ size_t batch_rule_smem(int dmax) {
   long long most = batch_rule_doubles(dmax, 1);
   if (batch_rule_doubles(dmax, 4) > most) most = batch_rule_doubles(dmax, 4);
   if (batch_rule_doubles(dmax, 32) > most) most = batch_rule_doubles(dmax, 32);
+  if (batch_rule_doubles(dmax, 128) > most) most = batch_rule_doubles(dmax, 128);
   const size_t pairs = sizeof(unsigned short) * (size_t)batch_pairs_offset(dmax + 1);
   return (sizeof(double) * (size_t)most + pairs + 15) & ~(size_t)15;
 }

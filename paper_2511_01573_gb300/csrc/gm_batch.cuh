@@ -50,8 +50,8 @@ struct BatchState {
   int max_sweeps;          // bound of the device loop (pauses add sweeps)
   int pauses;              // integral-sweeps paused for lack of pool space
   int evictions;           // integrals evicted to make room (restarted later)
-  int lanes;               // lanes per region of this sweep's rule kernel (1, 4, 32)
-  int lane_sweeps[3];      // sweeps run with 1, 4 and 32 lanes per region
+  int lanes;               // lanes per region of this sweep's rule kernel (1, 4, 32, 128)
+  int lane_sweeps[4];      // sweeps run with 1, 4, 32 and 128 lanes per region
   long long n_tiles;       // tiles of the current list (kSegTile regions, one integral each)
   long long n_tiles_next;  // tiles of the next list
   long long fam_off[2][8]; // first region of each family in either list; [p][7] = length
@@ -88,9 +88,10 @@ struct BatchArgs {
   cudaGraphConditionalHandle cond;
   int use_cond;
   // lanes per region of the rule kernel: forced_lanes if nonzero, else 1
-  // for lists of at least lanes_t1 regions, 4 from lanes_t4, 32 below
+  // for lists of at least lanes_t1 regions, 4 from lanes_t4, 32 from
+  // lanes_t32, 128 (a block) below
   int forced_lanes;
-  long long lanes_t1, lanes_t4;
+  long long lanes_t1, lanes_t4, lanes_t32;
   // tiles: per-integral tile offsets of both lists (count + 1 entries each)
   // and per-tile partial results
   long long* tile_off[2];
@@ -105,7 +106,7 @@ struct BatchArgs {
 
 __host__ __device__ inline int batch_lanes_for(const BatchArgs& B, long long n) {
   if (B.forced_lanes) return B.forced_lanes;
-  return n >= B.lanes_t1 ? 1 : (n >= B.lanes_t4 ? 4 : 32);
+  return n >= B.lanes_t1 ? 1 : (n >= B.lanes_t4 ? 4 : (n >= B.lanes_t32 ? 32 : 128));
 }
 
 

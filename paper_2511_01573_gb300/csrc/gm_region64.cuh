@@ -1,5 +1,6 @@
 // gm_region64.cuh -- FP64 evaluation of one region by a group of T lanes
-// (T in {1, 4, 32}), shared by the single-integral rule kernel (gm_rule.cuh)
+// (T in {1, 4, 32, 128}: a thread, four lanes, a warp or a 128-thread block
+// per region), shared by the single-integral rule kernel (gm_rule.cuh)
 // and the batched rule kernel (gm_batch.cu): both compute every region with
 // the same operations in the same order.
 //
@@ -12,19 +13,19 @@
 // class's nodes, in the order of their definition (class 2: axis k = 0..d-1,
 // +lambda2 then -lambda2; class 3 likewise with lambda3; class 4: pairs
 // j < k in lexicographic order, sign patterns ++, +-, -+, --; class 5: sign
-// patterns m = 0 .. 2^d - 1, bit j set = -lambda5 on axis j) are cut into 32
-// chunks of c = ceil(n / 32) consecutive nodes (trailing chunks may be short
-// or empty).  A chunk is summed left to right; the chunk sums are combined
-// by the adjacent-pairwise tree over the 32 chunk positions, in which a
-// subtree holding no node passes its sibling through unchanged.  Lane l of
-// a group of T takes the 32/T consecutive chunks that start at chunk
-// (32/T) * bitrev(l) (bitrev over log2 T bits), combines them with the same
-// tree, and the group finishes the tree with an xor butterfly: with that
-// bit-reversed assignment the butterfly's partners at offset T/2, T/4, ...
-// are exactly the tree's sibling subtrees at successive levels, and IEEE
-// addition is commutative, so every lane ends with the same value.  The
+// patterns m = 0 .. 2^d - 1, bit j set = -lambda5 on axis j) are cut into
+// 128 chunks of c = ceil(n / 128) consecutive nodes (trailing chunks may be
+// short or empty).  A chunk is summed left to right; the chunk sums are
+// combined by the adjacent-pairwise tree over the 128 chunk positions, in
+// which a subtree holding no node passes its sibling through unchanged.
+// Lane l of a group of T takes the 128/T consecutive chunks that start at
+// chunk (128/T) * bitrev(l) (bitrev over log2 T bits), combines them with
+// the same tree, and the group finishes the tree with an xor butterfly:
+// with that bit-reversed assignment the butterfly's partners at offset T/2,
+// T/4, ... are exactly the tree's sibling subtrees at successive levels, and
+// IEEE addition is commutative, so every lane ends with the same value.  The
 // sums -- and everything computed from them -- are therefore bit-identical
-// for T = 1, 4 and 32: the lane mapping is a pure launch choice.
+// for T = 1, 4, 32 and 128: the lane mapping is a pure launch choice.
 #pragma once
 
 #include "gmq_common.cuh"
@@ -38,10 +39,16 @@ enum XRow { kXC = 0, kXP2 = 1, kXM2 = 2, kXP3 = 3, kXM3 = 4, kXP5 = 5, kXM5 = 6,
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
 
-// Lanes of this thread's group (T consecutive lanes of one warp).
+// Chunks per class: the width of every class-sum tree, and the largest
+// group of lanes per region (a 128-thread block).
+constexpr int kChunks = 128;
+
+// Lanes of this thread's group within its warp (T consecutive lanes of one
+// warp; for T = 128 the group is the whole block and each warp takes part
+// with all its lanes).
 template <int T>
 __device__ __forceinline__ unsigned group_mask() {
-  if constexpr (T == 32) {
+  if constexpr (T >= 32) {
     return 0xffffffffu;
   } else {
     const unsigned base = (threadIdx.x & 31u) & ~(unsigned)(T - 1);
@@ -49,23 +56,32 @@ __device__ __forceinline__ unsigned group_mask() {
   }
 }
 
-// First of the 32/T chunk positions lane `lane` of a group of T owns.
+// Synchronise the lanes of a group (the block for T = 128).
+template <int T>
+__device__ __forceinline__ void group_sync(unsigned mask) {
+  if constexpr (T > 32)
+    __syncthreads();
+  else
+    __syncwarp(mask);
+}
+
+// First of the kChunks/T chunk positions lane `lane` of a group of T owns.
 template <int T>
 __device__ __forceinline__ int lane_first_chunk(int lane) {
   if constexpr (T == 1) {
     return 0;
   } else {
     constexpr int bits = ilog2c(T);
-    return (32 / T) * (int)(__brev((unsigned)lane) >> (32 - bits));
+    return (kChunks / T) * (int)(__brev((unsigned)lane) >> (32 - bits));
   }
 }
 
-// Adjacent-pairwise tree over at most 32 leaves pushed left to right: a
-// binary counter of complete subtrees (L_j holds 2^j leaves while bit j of
+// Adjacent-pairwise tree over at most 128 leaves pushed left to right: a
+// binary counter of complete subtrees (L[j] holds 2^j leaves while bit j of
 // the leaf count is set).  flush() combines the pending subtrees from the
 // rightmost up, so a missing right part of the tree passes through.
 struct PairTree {
-  double L0 = 0.0, L1 = 0.0, L2 = 0.0, L3 = 0.0, L4 = 0.0, L5 = 0.0;
+  double L0 = 0.0, L1 = 0.0, L2 = 0.0, L3 = 0.0, L4 = 0.0, L5 = 0.0, L6 = 0.0, L7 = 0.0;
   int n = 0;
   __device__ __forceinline__ void push(double x) {
     const int p = n++;
@@ -78,36 +94,63 @@ struct PairTree {
     if (!(p & 8)) { L3 = x; return; }
     x = __dadd_rn(L3, x);
     if (!(p & 16)) { L4 = x; return; }
-    L5 = __dadd_rn(L4, x);
+    x = __dadd_rn(L4, x);
+    if (!(p & 32)) { L5 = x; return; }
+    x = __dadd_rn(L5, x);
+    if (!(p & 64)) { L6 = x; return; }
+    L7 = __dadd_rn(L6, x);
   }
   __device__ __forceinline__ double flush(bool& present) const {
     present = n > 0;
-    if (n >= 32) return L5;
+    if (n >= 128) return L7;
     double x = 0.0;
     bool have = false;
     if (n & 1) { x = L0; have = true; }
     if (n & 2) { x = have ? __dadd_rn(L1, x) : L1; have = true; }
     if (n & 4) { x = have ? __dadd_rn(L2, x) : L2; have = true; }
     if (n & 8) { x = have ? __dadd_rn(L3, x) : L3; have = true; }
-    if (n & 16) { x = have ? __dadd_rn(L4, x) : L4; }
+    if (n & 16) { x = have ? __dadd_rn(L4, x) : L4; have = true; }
+    if (n & 32) { x = have ? __dadd_rn(L5, x) : L5; have = true; }
+    if (n & 64) { x = have ? __dadd_rn(L6, x) : L6; }
     return x;
   }
 };
 
-// The group's xor butterfly over lane partial trees (absent partials pass
-// the other side through); every lane returns the full tree's value.
+// Combine a lane's partial with its butterfly partner's (absent partials
+// pass the other side through); a + b == b + a, so both partners agree.
+__device__ __forceinline__ void tree_combine(double& x, bool& present, double ox, bool op) {
+  if (present && op) {
+    x = __dadd_rn(x, ox);
+  } else if (op) {
+    x = ox;
+    present = true;
+  }
+}
+
+// The group's xor butterfly over lane partial trees; every lane returns the
+// full tree's value.  T = 128: the two levels across warps (offsets 64, 32)
+// go through shared memory, the rest through warp shuffles.
 template <int T>
 __device__ __forceinline__ double lanes_tree(double x, bool present, unsigned mask) {
+  if constexpr (T > 32) {
+    __shared__ double sx[T];
+    __shared__ int sp[T];
+    const int l = threadIdx.x & (T - 1);
 #pragma unroll
-  for (int off = T / 2; off > 0; off >>= 1) {
-    const double ox = __shfl_xor_sync(mask, x, off, T);
-    const int op = __shfl_xor_sync(mask, present ? 1 : 0, off, T);
-    if (present && op) {
-      x = __dadd_rn(x, ox);
-    } else if (op) {
-      x = ox;
-      present = true;
+    for (int off = T / 2; off >= 32; off >>= 1) {
+      __syncthreads();
+      sx[l] = x;
+      sp[l] = present ? 1 : 0;
+      __syncthreads();
+      tree_combine(x, present, sx[l ^ off], sp[l ^ off] != 0);
     }
+  }
+  constexpr int W = T < 32 ? T : 32;
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) {
+    const double ox = __shfl_xor_sync(mask, x, off, W);
+    const int op = __shfl_xor_sync(mask, present ? 1 : 0, off, W);
+    tree_combine(x, present, ox, op != 0);
   }
   return present ? x : 0.0;
 }
@@ -117,10 +160,10 @@ template <int T, class Val>
 __device__ __forceinline__ double class_sum(int n, int lane, unsigned mask, Val val) {
   PairTree t;
   if (n > 0) {
-    const int c = (n + 31) >> 5;
+    const int c = (n + kChunks - 1) / kChunks;
     const int nch = (n + c - 1) / c;
     const int p0 = lane_first_chunk<T>(lane);
-    const int p1 = min(p0 + 32 / T, nch);
+    const int p1 = min(p0 + kChunks / T, nch);
     for (int p = p0; p < p1; ++p) {
       const int q0 = p * c, q1 = min(q0 + c, n);
       double x = 0.0;
@@ -209,7 +252,7 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
           P, d, [&](int j) -> double { return tab(j == k1 ? r1 : kXC, j); });
       fv[(i == 0 ? 4 * d : w * d + k1) * fvs] = v;
     }
-    __syncwarp(mask);
+    group_sync<T>(mask);
     f0 = fv[4 * d * fvs];
     const double two_f0 = __dmul_rn(2.0, f0);
     for (int k = lane; k < d; k += T) {
@@ -221,11 +264,14 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
         kbest = k;
       }
     }
-    // argmax over the lanes: larger D wins, the lower axis on ties
+    // argmax over the lanes: larger D wins, the lower axis on ties (for
+    // T = 128 every axis k < d <= 16 sits in warp 0, which holds the answer
+    // for lane 0, the only lane that uses it)
+    constexpr int W = T < 32 ? T : 32;
 #pragma unroll
-    for (int off = T / 2; off > 0; off >>= 1) {
-      const double od = __shfl_xor_sync(mask, dbest, off, T);
-      const int ok = __shfl_xor_sync(mask, kbest, off, T);
+    for (int off = W / 2; off > 0; off >>= 1) {
+      const double od = __shfl_xor_sync(mask, dbest, off, W);
+      const int ok = __shfl_xor_sync(mask, kbest, off, W);
       if (od > dbest || (od == dbest && ok < kbest)) {
         dbest = od;
         kbest = ok;
@@ -233,7 +279,7 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
     }
     // classes 2 and 3 hold 2d <= 32 nodes: one node per chunk
     PairTree t2, t3;
-    const int p0 = lane_first_chunk<T>(lane), p1 = min(p0 + 32 / T, 2 * d);
+    const int p0 = lane_first_chunk<T>(lane), p1 = min(p0 + kChunks / T, 2 * d);
     for (int p = p0; p < p1; ++p) {
       t2.push(fv[((p & 1) * d + (p >> 1)) * fvs]);
       t3.push(fv[((2 + (p & 1)) * d + (p >> 1)) * fvs]);

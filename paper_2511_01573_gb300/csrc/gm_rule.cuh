@@ -3,7 +3,8 @@
 // fourth-difference split axis on every region of a sweep (paper Sec. 2).
 //
 // Mapping: a block of 128 threads owns RB = 128 / T consecutive regions, T
-// threads ("lanes") per region, T in {1, 4, 32}.  The block
+// threads ("lanes") per region, T in {1, 4, 32} (and 128, a block per
+// region, in FP64).  The block
 //   1. stages the regions' centres and half-widths from the structure-of-
 //      arrays list into shared memory with coalesced loads (consecutive
 //      threads read consecutive regions of one axis) and expands them into a
@@ -437,6 +438,9 @@ cudaError_t launch_rule_real(int T, const RuleArgs& A, cudaStream_t s) {
     case 1: return launch_rule_t<FAM, 1, Real>(A, s);
     case 4: return launch_rule_t<FAM, 4, Real>(A, s);
     case 32: return launch_rule_t<FAM, 32, Real>(A, s);
+    case 128:  // a block per region: FP64 only
+      if constexpr (std::is_same<Real, double>::value) return launch_rule_t<FAM, 128, Real>(A, s);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

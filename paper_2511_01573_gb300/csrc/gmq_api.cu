@@ -71,6 +71,7 @@ struct gmq_context {
   int tuned[GMQ_MAX_DIM + 1] = {};
   long long tuned_t1[GMQ_MAX_DIM + 1] = {};
   long long tuned_t4[GMQ_MAX_DIM + 1] = {};
+  long long tuned_t32[GMQ_MAX_DIM + 1] = {};
   gmq_batch_info last_batch = {};
   cudaStream_t capture_stream = nullptr;  // private stream for graph capture
   // kernel timing (gmq_profile_*)
@@ -227,13 +228,18 @@ int auto_splits(int d, int64_t cap) {
 // Threads per region for a sweep of n regions: one thread per region once
 // there are enough regions to give every SM about eight warps; otherwise
 // split each region's nodes over 4 or 32 lanes.
-int choose_lanes(int req, int64_t n, int d, int sms) {
+// Lanes per region for a sweep of n regions: enough threads to fill the
+// GPU (about 256 per SM), a thread per region when the list alone does;
+// a 128-thread block per region (FP64 only) for very short lists of
+// regions with many nodes.
+int choose_lanes(int req, int64_t n, int d, int sms, int precision) {
   if (req) return req;
   const int64_t nodes = num_nodes(d);
   const int64_t want = (int64_t)sms * 256;
   if (n >= want || nodes < 16) return 1;
   if (n * 4 >= want || nodes < 128) return 4;
-  return 32;
+  if (n * 32 >= want || nodes < 1024 || precision != GMQ_FP64) return 32;
+  return 128;
 }
 
 cudaError_t launch_rule(int fam, int precision, int T, const RuleArgs& A, cudaStream_t s) {
@@ -758,7 +764,9 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
       opt->init_splits < 0 || opt->max_iters < 0 || (opt->flags & ~GMQ_KEEP_PARTITION) ||
       (opt->precision != GMQ_FP64 && opt->precision != GMQ_MIXED) ||
       (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL) ||
-      (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32) ||
+      (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32 &&
+       opt->lanes != 128) ||
+      (opt->lanes == 128 && opt->precision != GMQ_FP64) ||
       (opt->rule != GMQ_RULE_GENZ_MALIK && opt->rule != GMQ_RULE_GAUSS_KRONROD) ||
       (opt->rule == GMQ_RULE_GAUSS_KRONROD &&
        (opt->precision != GMQ_FP64 || d > GMQ_GK_MAX_DIM)))
@@ -821,7 +829,7 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
   gmq_status status = GMQ_OK;
   int iters = 0;
   for (;;) {
-    const int T = choose_lanes(opt->lanes, n, d, ctx->sm_count);
+    const int T = choose_lanes(opt->lanes, n, d, ctx->sm_count, opt->precision);
     RuleArgs A;
     A.c = cA;
     A.h = hA;
@@ -969,7 +977,9 @@ gmq_status gmq_eval_rule(gmq_context* ctx, const gmq_problem* prob, int32_t prec
   if (n < 0 || ld < n || (n > 0 && (!d_center || !d_halfw || !d_integral || !d_error || !d_axis)))
     return GMQ_ERR_INVALID;
   if (precision != GMQ_FP64 && precision != GMQ_MIXED) return GMQ_ERR_INVALID;
-  if (lanes != 0 && lanes != 1 && lanes != 4 && lanes != 32) return GMQ_ERR_INVALID;
+  if (lanes != 0 && lanes != 1 && lanes != 4 && lanes != 32 && lanes != 128)
+    return GMQ_ERR_INVALID;
+  if (lanes == 128 && precision != GMQ_FP64) return GMQ_ERR_INVALID;
   if (n == 0) return GMQ_OK;
   DeviceGuard g(ctx->device);
   if (!g.ok) return GMQ_ERR_CUDA;
@@ -984,7 +994,7 @@ gmq_status gmq_eval_rule(gmq_context* ctx, const gmq_problem* prob, int32_t prec
   A.axis = d_axis;
   A.P = fam_params(prob);
   A.R = rule_const(prob->dim, prob->lo, prob->hi);
-  const int T = choose_lanes(lanes, n, prob->dim, ctx->sm_count);
+  const int T = choose_lanes(lanes, n, prob->dim, ctx->sm_count, precision);
   prof_begin(ctx, kKRule);
   GMQ_CK(launch_rule(prob->family, precision, T, A, ctx->stream));
   prof_end(ctx, kKRule, n);
@@ -1287,7 +1297,8 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   if (!(opt->abs_tol >= 0.0) || cap < 1 || cap > kMaxRegions || opt->init_splits < 0 ||
       opt->max_iters < 0 || (opt->flags & ~GMQ_BATCH_HOST_LOOP) ||
       (opt->precision != GMQ_FP64 && opt->precision != GMQ_MIXED) ||
-      (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32) ||
+      (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32 &&
+       opt->lanes != 128) ||
       (opt->precision == GMQ_MIXED && opt->lanes > 1) || opt->rule != GMQ_RULE_GENZ_MALIK ||
       (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL))
     return GMQ_ERR_INVALID;
@@ -1525,7 +1536,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     }
     GMQ_CK(batch_launch_tile(B, total, lens[nl - 1], strm));
     ctx->launches += 1;
-    const int modes[3] = {1, 4, 32};
+    const int modes[4] = {1, 4, 32, 128};
     int best[5];
     EventPair ev;  // destroyed on every return path
     GMQ_CK(cudaEventCreate(&ev.a));
@@ -1533,8 +1544,8 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     cudaEvent_t e0 = ev.a, e1 = ev.b;
     for (int i = 0; i < nl; ++i) {
       float mbest = 1e30f;
-      float ms[3];
-      for (int m = 0; m < 3; ++m) {
+      float ms[4];
+      for (int m = 0; m < 4; ++m) {
         BatchState t = bs0;
         t.n_total = lens[i];
         t.lanes = modes[m];
@@ -1550,8 +1561,8 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
         mbest = std::min(mbest, ms[m]);
       }
       // the fewest lanes within 5% of the fastest mapping
-      best[i] = 2;
-      for (int m = 2; m >= 0; --m)
+      best[i] = 3;
+      for (int m = 3; m >= 0; --m)
         if (ms[m] <= 1.05f * mbest) best[i] = m;
       info.tune_n[i] = lens[i];
     }
@@ -1566,13 +1577,18 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     int i4 = i1;
     for (int i = i1 - 1; i >= 0 && best[i] <= 1; --i) i4 = i;
     const long long t4 = i4 == i1 ? t1 : (i4 == 0 ? 0 : between(i4));
+    int i32 = i4;
+    for (int i = i4 - 1; i >= 0 && best[i] <= 2; --i) i32 = i;
+    const long long t32 = i32 == i4 ? t4 : (i32 == 0 ? 0 : between(i32));
     ctx->tuned[dmax] = 1;
     ctx->tuned_t1[dmax] = t1;
     ctx->tuned_t4[dmax] = t4;
+    ctx->tuned_t32[dmax] = t32;
     info.autotuned = 1;
   }
   B.lanes_t1 = ctx->tuned_t1[dmax];
   B.lanes_t4 = ctx->tuned_t4[dmax];
+  B.lanes_t32 = ctx->tuned_t32[dmax];
   bs0.lanes = batch_lanes_for(B, bs0.n_total);
   GMQ_CK(cudaMemcpyAsync(B.bs, &bs0, sizeof(BatchState), cudaMemcpyHostToDevice, strm));
   info.rule_block = kBatchRuleBlock;
@@ -1582,6 +1598,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   info.forced_lanes = B.forced_lanes;
   info.lanes_t1 = B.forced_lanes ? 0 : B.lanes_t1;
   info.lanes_t4 = B.forced_lanes ? 0 : B.lanes_t4;
+  info.lanes_t32 = B.forced_lanes ? 0 : B.lanes_t32;
 
   BatchState hs;
   if (!(opt->flags & GMQ_BATCH_HOST_LOOP)) {
@@ -1651,7 +1668,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   info.sweeps = hs.sweep;
   info.pauses = hs.pauses;
   info.evictions = hs.evictions;
-  for (int m = 0; m < 3; ++m) info.lane_sweeps[m] = hs.lane_sweeps[m];
+  for (int m = 0; m < 4; ++m) info.lane_sweeps[m] = hs.lane_sweeps[m];
   ctx->last_batch = info;
   for (int32_t k = 0; k < count; ++k) {
     const BatchItem& it = items[(size_t)k];

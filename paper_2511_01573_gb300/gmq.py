@@ -78,9 +78,9 @@ class BatchInfo(C.Structure):
     _fields_ = [("rule_block", C.c_int32), ("rule_grid", C.c_int32), ("sweeps", C.c_int32),
                 ("used_graph", C.c_int32), ("autotuned", C.c_int32), ("pauses", C.c_int32),
                 ("evictions", C.c_int32), ("forced_lanes", C.c_int32),
-                ("lanes_t1", C.c_int64), ("lanes_t4", C.c_int64),
-                ("lane_sweeps", C.c_int32 * 3), ("reserved", C.c_int32),
-                ("tune_n", C.c_int64 * 5), ("tune_ms", (C.c_double * 3) * 5)]
+                ("lanes_t1", C.c_int64), ("lanes_t4", C.c_int64), ("lanes_t32", C.c_int64),
+                ("lane_sweeps", C.c_int32 * 4),
+                ("tune_n", C.c_int64 * 5), ("tune_ms", (C.c_double * 4) * 5)]
 
 ERR_TOO_LARGE = -6
 NOALLOC_MAX_N = 1 << 23
@@ -323,9 +323,9 @@ class Context:
         """Integrate many problems in one device-resident loop.  problems:
         objects with family, dim, a, u (and optional lo, hi, rel_tol).
         max_regions is each problem's cap, pool_regions the shared pool (0:
-        the library's default); lanes 1, 4 or 32 fixes the rule kernel's
-        lanes per region (0: autotuned per sweep; MIXED runs one lane per
-        region).  Returns one IntegrateResult per problem."""
+        the library's default); lanes 1, 4, 32 or 128 fixes the rule
+        kernel's lanes per region (0: autotuned per sweep; MIXED runs one lane
+        per region).  Returns one IntegrateResult per problem."""
         hs = [_ProblemHandle(p.family, p.a, p.u, getattr(p, "lo", None), getattr(p, "hi", None),
                              p.dim) for p in problems]
         arr = (Problem * len(hs))(*[h.s for h in hs])
@@ -348,6 +348,7 @@ class Context:
                 "autotuned": bool(info.autotuned), "pauses": int(info.pauses),
                 "evictions": int(info.evictions), "forced_lanes": int(info.forced_lanes),
                 "lanes_t1": int(info.lanes_t1), "lanes_t4": int(info.lanes_t4),
+                "lanes_t32": int(info.lanes_t32),
                 "lane_sweeps": list(info.lane_sweeps),
                 "tune": [{"n": int(info.tune_n[i]), "ms": list(info.tune_ms[i])}
                          for i in range(5) if info.tune_n[i] > 0]}

@@ -52,14 +52,14 @@ def test_batch_equals_single_runs(gpu_ctx, host_loop):
     assert info["sweeps"] >= max(r.iterations for r in res)
 
 
-@pytest.mark.parametrize("lanes", [1, 4, 32])
+@pytest.mark.parametrize("lanes", [1, 4, 32, 128])
 def test_batch_forced_lane_mappings(gpu_ctx, lanes):
     probs = _mixed_batch(n=24, seed=13)
     cap = 1 << 20
     res = gpu_ctx.integrate_batch(probs, max_regions=cap, lanes=lanes)
     info = gpu_ctx.last_batch_info()
     assert info["forced_lanes"] == lanes and not info["autotuned"]
-    assert info["lane_sweeps"][{1: 0, 4: 1, 32: 2}[lanes]] == info["sweeps"]
+    assert info["lane_sweeps"][{1: 0, 4: 1, 32: 2, 128: 3}[lanes]] == info["sweeps"]
     for p, r in zip(probs, res):
         s = gpu_ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=cap)
         assert (r.status, r.iterations, r.regions_evaluated) == (s.status, s.iterations,
@@ -138,10 +138,10 @@ def test_batch_autotune_cached_and_limits(gpu_ctx):
     info = gpu_ctx.last_batch_info()
     if info["autotuned"]:
         tune = info["tune"]
-        assert 1 <= len(tune) <= 5 and all(len(t["ms"]) == 3 for t in tune)
-        assert all(t["ms"][m] > 0 for t in tune for m in range(3))
+        assert 1 <= len(tune) <= 5 and all(len(t["ms"]) == 4 for t in tune)
+        assert all(t["ms"][m] > 0 for t in tune for m in range(4))
         assert [t["n"] for t in tune] == sorted(t["n"] for t in tune)
-    assert 0 <= info["lanes_t4"] <= info["lanes_t1"]
+    assert 0 <= info["lanes_t32"] <= info["lanes_t4"] <= info["lanes_t1"]
     again = gpu_ctx.integrate_batch(probs)
     assert not gpu_ctx.last_batch_info()["autotuned"]  # cached per largest dimension
     assert [(r.integral, r.regions_evaluated) for r in again] == [

@@ -70,7 +70,7 @@ def _compare_rule(oracle, gpu_ctx, fam, d, lanes, n=None, seed=3, boxes=None):
 
 @pytest.mark.parametrize("fam", range(7))
 @pytest.mark.parametrize("d", [1, 2, 3, 5, 8])
-@pytest.mark.parametrize("lanes", [1, 4, 32])
+@pytest.mark.parametrize("lanes", [1, 4, 32, 128])
 def test_rule_per_region(oracle, gpu_ctx, fam, d, lanes):
     _compare_rule(oracle, gpu_ctx, fam, d, lanes)
 
@@ -222,12 +222,13 @@ def test_e2e_paper_integrands(oracle, gpu_ctx):
 @pytest.mark.parametrize("fam", range(7))
 @pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6, 8, 12])
 def test_rule_lane_mappings_bit_identical(gpu_ctx, fam, d):
-    """FP64: one thread, four lanes or a warp per region give the same bits
-    (every class sum is one fixed tree over 32 chunks of its nodes)."""
+    """FP64: one thread, four lanes, a warp or a 128-thread block per region
+    give the same bits (every class sum is one fixed tree over 128 chunks of
+    its nodes)."""
     a, u = _params(fam, d, 5)
     n = min(_region_count(d), 300) + 7  # ragged against every tile size
     c, h = G.random_boxes(7 + d, n, d)
-    outs = [gpu_ctx.eval_rule(fam, a, u, _soa(c), _soa(h), lanes=t) for t in (1, 4, 32)]
+    outs = [gpu_ctx.eval_rule(fam, a, u, _soa(c), _soa(h), lanes=t) for t in (1, 4, 32, 128)]
     for o in outs[1:]:
         for x, y in zip(outs[0], o):
             assert torch.equal(x, y), (fam, d)
@@ -236,7 +237,8 @@ def test_rule_lane_mappings_bit_identical(gpu_ctx, fam, d):
 def test_rule_lane_mappings_bit_identical_d16(gpu_ctx):
     a, u = _params(G.GAUSSIAN, 16, 5)
     c, h = G.random_boxes(9, 2, 16)
-    outs = [gpu_ctx.eval_rule(G.GAUSSIAN, a, u, _soa(c), _soa(h), lanes=t) for t in (1, 4, 32)]
+    outs = [gpu_ctx.eval_rule(G.GAUSSIAN, a, u, _soa(c), _soa(h), lanes=t)
+            for t in (1, 4, 32, 128)]
     for o in outs[1:]:
         for x, y in zip(outs[0], o):
             assert torch.equal(x, y)
@@ -246,7 +248,7 @@ def test_e2e_lane_choices_agree(gpu_ctx):
     # FP64 results do not depend on the lane mapping: bit-identical runs
     for fam, d in ((G.C0, 4), (G.OSCILLATORY, 6), (G.CORNER_PEAK, 3)):
         a, u = G.seed_genz(2, fam, d, G.GENZ_TARGET_SUM[fam])
-        rs = [gpu_ctx.integrate(fam, a, u, 1e-6, lanes=t) for t in (1, 4, 32, 0)]
+        rs = [gpu_ctx.integrate(fam, a, u, 1e-6, lanes=t) for t in (1, 4, 32, 128, 0)]
         for r in rs[1:]:
             assert (r.iterations, r.regions_evaluated, r.status) == (
                 rs[0].iterations, rs[0].regions_evaluated, rs[0].status)
@@ -301,3 +303,13 @@ def test_e2e_domain_classifier_and_dimension_edges(oracle, gpu_ctx):
     # absolute tolerance only
     a, u = G.seed_genz(6, G.OSCILLATORY, 3, 6.0)
     _e2e(oracle, gpu_ctx, G.OSCILLATORY, a, u, 0.0, abs_tol=1e-9)
+
+
+def test_block_per_region_is_fp64_only(gpu_ctx):
+    from paper_2511_01573_gb300 import gmq
+    a, u = _params(G.GAUSSIAN, 4)
+    c, h = G.random_boxes(3, 5, 4)
+    with pytest.raises(gmq.GmqError):
+        gpu_ctx.eval_rule(G.GAUSSIAN, a, u, _soa(c), _soa(h), lanes=128, precision=gmq.MIXED)
+    with pytest.raises(gmq.GmqError):
+        gpu_ctx.integrate(G.GAUSSIAN, a, u, 1e-4, lanes=128, precision=gmq.MIXED)
