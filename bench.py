@@ -79,8 +79,8 @@ CAP = 1 << 24
 # (profiles/rule_fp64_d8.md).  The counts are fixed by the integrand and d:
 # the four families take no data-dependent branch.  Family codes: 0
 # oscillatory, 1 product peak, 2 corner peak, 3 Gaussian, 4 C0.
-RULE_FP64_INST_D8 = {0: 10267.0, 1: 11871.0, 2: 8663.0, 3: 14678.0, 4: 11470.0}
-RULE_FP64_FLOPS_D8 = {0: 18330.0, 1: 16726.0, 2: 13518.0, 3: 21137.0, 4: 17929.0}
+RULE_FP64_INST_D8 = {0: 10209.0, 1: 11813.0, 2: 8605.0, 3: 14620.0, 4: 11412.0}
+RULE_FP64_FLOPS_D8 = {0: 18272.0, 1: 16668.0, 2: 13460.0, 3: 21079.0, 4: 17871.0}
 # DRAM bytes per region of the rule kernel in the same capture (128 B read,
 # ~13 B written of 25 B of outputs); traffic per launch scales with regions.
 RULE_DRAM_BYTES_PER_REGION_D8 = 141.7

@@ -166,11 +166,10 @@ __device__ __forceinline__ double class_sum(int n, int lane, unsigned mask, Val 
     const int p1 = min(p0 + kChunks / T, nch);
     for (int p = p0; p < p1; ++p) {
       const int q0 = p * c, q1 = min(q0 + c, n);
-      double x = 0.0;
-      for (int q = q0; q < q1; ++q) {
-        const double v = val(q);
-        x = (q == q0) ? v : __dadd_rn(x, v);
-      }
+      // the chunk's first node starts the sum (no add of a zero: a select
+      // would leave the add in the instruction stream)
+      double x = val(q0);
+      for (int q = q0 + 1; q < q1; ++q) x = __dadd_rn(x, val(q));
       t.push(x);
     }
   }
