@@ -79,11 +79,11 @@ CAP = 1 << 24
 # (profiles/rule_fp64_d8.md).  The counts are fixed by the integrand and d:
 # the four families take no data-dependent branch.  Family codes: 0
 # oscillatory, 1 product peak, 2 corner peak, 3 Gaussian, 4 C0.
-RULE_FP64_INST_D8 = {0: 10209.0, 1: 11813.0, 2: 8605.0, 3: 14620.0, 4: 11412.0}
-RULE_FP64_FLOPS_D8 = {0: 18272.0, 1: 16668.0, 2: 13460.0, 3: 21079.0, 4: 17871.0}
+RULE_FP64_INST_D8 = {0: 9006.0, 1: 11813.0, 2: 7803.0, 3: 14219.0, 4: 11011.0}
+RULE_FP64_FLOPS_D8 = {0: 15866.0, 1: 16668.0, 2: 12658.0, 3: 20277.0, 4: 17069.0}
 # DRAM bytes per region of the rule kernel in the same capture (128 B read,
 # ~13 B written of 25 B of outputs); traffic per launch scales with regions.
-RULE_DRAM_BYTES_PER_REGION_D8 = 141.7
+RULE_DRAM_BYTES_PER_REGION_D8 = 141.1
 
 
 def time_to_tol(ctx, stream, tol):
@@ -673,6 +673,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
     ws, rank, local = dist_setup()
     if ws > 1:
         import torch.distributed as dist
@@ -744,11 +745,11 @@ def main():
     if rank != 0:
         return
     rule = prof["rule"]
-    # FP64 roofline of the rule kernel: FP64 flops per region of each family
-    # at d = 8 (a fixed count: the integrand at 401 nodes plus one
-    # accumulation each and the per-region epilogue) times the regions of
-    # that family in the timed steps, over the rule kernel's event-timed
-    # launches.  Peak: 2 FP64 FMA lanes per clock per SM (1.25 TFLOP/s
+    # FP64 roofline of the rule kernel: FP64 instructions (and flops) per
+    # region of each family at d = 8 (a fixed count: the integrand at 401
+    # nodes plus one accumulation each and the per-region epilogue) times the
+    # regions of that family in the timed steps, over the rule kernel's
+    # event-timed launches.  Peak: 2 FP64 FMA lanes per clock per SM (1.25 TFLOP/s
     # nominal / 2 / 152 SMs / 2.07 GHz) at the measured median SM clock.
     roof = None
     clocks = clk.summary()
@@ -767,7 +768,11 @@ def main():
                 "peak_basis": (f"2 FP64 lanes/clk/SM (1.25 TFLOP/s nominal) x 152 SMs "
                                f"x median {mhz:.0f} MHz"),
                 "flops_view": {"achieved_gflops": flops / avg_s / 1e9,
-                               "peak_gflops": 2 * peak_inst}}
+                               "peak_gflops": 2 * peak_inst},
+                "inst_per_region": {G.FAMILY_NAMES[f]: RULE_FP64_INST_D8[f]
+                                    for f in sorted(timed_fam_regions)},
+                "regions_by_family": {G.FAMILY_NAMES[f]: n // args.steps
+                                      for f, n in sorted(timed_fam_regions.items())}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

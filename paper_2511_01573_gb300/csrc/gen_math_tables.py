@@ -3,17 +3,20 @@ and cosine (gmq_families.cuh, gm_exp and gm_cos), computed in decimal
 arithmetic with 60 significant digits.
 
 Method: Tang's table-driven exponential (P. T. P. Tang, ACM TOMS 15(2),
-1989).  x = (64 m + j) ln2/64 + r, |r| <= ln2/128, exp(x) = 2^m 2^(j/64)
-exp(r).  The table holds 2^(j/64), j = 0..63, rounded to nearest; ln2/64 is
-split into L1 (36 significant bits, so n L1 is exact for |n| < 2^17) and
-L2 = ln2/64 - L1 rounded; exp(r) - 1 is the Taylor polynomial of degree 5
-(its truncation error r^6/720 is below 3.6e-17 relative).
+1989).  x = (256 m + j) ln2/256 + r, |r| <= ln2/512, exp(x) = 2^m
+2^(j/256) exp(r).  The table holds 2^(j/256), j = 0..255, rounded to
+nearest; ln2/256 is split into L1 (36 significant bits) and L2 = ln2/256 -
+L1 rounded; exp(r) - 1 is the Taylor polynomial of degree 4 (its truncation
+error r^5/120 is below 3.8e-17).
 
 Cosine, by the same table-driven scheme (J.-M. Muller, Elementary Functions,
-ch. 6): x = n pi/32 + r, |r| <= pi/64, cos(x) = C_j cos(r) - S_j sin(r) with
-j = n mod 64, C_j = cos(j pi/32), S_j = sin(j pi/32); pi/32 is split into
-three parts P1, P2 (33 significant bits each, so n P1 and n P2 are exact for
-|n| < 2^20) and P3.
+ch. 6): x = n pi/128 + r, |r| <= pi/256, cos(x) = C_j cos(r) - S_j sin(r)
+with j = n mod 256, C_j = cos(j pi/128), S_j = sin(j pi/128); pi/128 is
+split into P1 (33 significant bits) and P2 = pi/128 - P1 rounded.  With
+fused multiply-adds the first step x - n P1 is exact (the result is a
+multiple of the coarser of ulp(x) and P1's last bit, and no larger than
+|x|), and the second leaves an error n |pi/128 - P1 - P2| below 2^-70 for
+|n| < 2^22, so two parts suffice.
 
 Run from this directory: python gen_math_tables.py
 """
@@ -89,23 +92,27 @@ def split36(d: Decimal) -> float:
     return float((d * scale).to_integral_value() / scale)
 
 
+NEXP = 256  # table entries of the exponential (2^(j/NEXP))
+NCOS = 256  # table entries of the cosine (cos, sin of 2 pi j/NCOS)
+
+
 def main():
     ln2 = dec_ln2()
-    c = ln2 / 64
+    c = ln2 / NEXP
     l1 = split36(c)
     l2 = to_double(c - Decimal(l1))
-    inv = to_double(64 / ln2)
-    tab = [to_double(dec_exp(ln2 * j / 64)) for j in range(64)]
+    inv = to_double(NEXP / ln2)
+    tab = [to_double(dec_exp(ln2 * j / NEXP)) for j in range(NEXP)]
     pi = dec_pi()
-    q = pi / 32
+    q = 2 * pi / NCOS
     p1 = split_bits(q, 33)
-    p2 = split_bits(q - Decimal(p1), 33)
-    p3 = to_double(q - Decimal(p1) - Decimal(p2))
-    invq = to_double(32 / pi)
-    # cos and sin of j pi/32; the exact zeros (j = 0, 16, 32, 48) come out of
-    # the series as residues below 1e-40 and are set to 0
-    cs = [tuple(Decimal(0) if abs(v) < Decimal(10) ** -40 else v for v in dec_cos_sin(pi * j / 32))
-          for j in range(64)]
+    p2 = to_double(q - Decimal(p1))
+    invq = to_double(NCOS / (2 * pi))
+    # cos and sin of 2 pi j/NCOS; the exact zeros (j = 0, NCOS/4, NCOS/2,
+    # 3 NCOS/4) come out of the series as residues below 1e-40 and are set to 0
+    cs = [tuple(Decimal(0) if abs(v) < Decimal(10) ** -40 else v
+                for v in dec_cos_sin(2 * pi * j / NCOS))
+          for j in range(NCOS)]
     lines = [
         "// gm_math_tables.cuh -- generated by gen_math_tables.py (decimal arithmetic, 60",
         "// digits); constants of gm_exp and gm_cos (gmq_families.cuh).",
@@ -113,27 +120,28 @@ def main():
         "",
         "namespace gmq {",
         "",
-        f"constexpr double kExpInvL = {inv!r};  // 64 / ln 2",
-        f"constexpr double kExpL1 = {l1!r};  // ln2/64, 36 significant bits",
-        f"constexpr double kExpL2 = {l2!r};  // ln2/64 - kExpL1",
+        f"constexpr int kExpTabBits = {NEXP.bit_length() - 1};  // {NEXP} entries",
+        f"constexpr double kExpInvL = {inv!r};  // {NEXP} / ln 2",
+        f"constexpr double kExpL1 = {l1!r};  // ln2/{NEXP}, 36 significant bits",
+        f"constexpr double kExpL2 = {l2!r};  // ln2/{NEXP} - kExpL1",
         "",
-        "// 2^(j/64), j = 0..63, rounded to nearest",
-        "static __device__ const double kExp2Tab[64] = {",
+        f"// 2^(j/{NEXP}), j = 0..{NEXP - 1}, rounded to nearest",
+        f"static __device__ const double kExp2Tab[{NEXP}] = {{",
     ]
-    for i in range(0, 64, 2):
+    for i in range(0, NEXP, 2):
         lines.append(f"    {tab[i]!r}, {tab[i + 1]!r},")
     lines += ["};", "",
-              f"constexpr double kCosInvQ = {invq!r};  // 32 / pi",
-              f"constexpr double kCosP1 = {p1!r};  // pi/32, 33 significant bits",
-              f"constexpr double kCosP2 = {p2!r};  // next 33 bits",
-              f"constexpr double kCosP3 = {p3!r};  // pi/32 - P1 - P2",
+              f"constexpr int kCosTabBits = {NCOS.bit_length() - 1};  // {NCOS} entries",
+              f"constexpr double kCosInvQ = {invq!r};  // {NCOS // 2} / pi",
+              f"constexpr double kCosP1 = {p1!r};  // pi/{NCOS // 2}, 33 significant bits",
+              f"constexpr double kCosP2 = {p2!r};  // pi/{NCOS // 2} - P1",
               "",
-              "// cos(j pi/32) and sin(j pi/32), j = 0..63, rounded to nearest",
-              "static __device__ const double kCosTab[64] = {"]
-    for i in range(0, 64, 2):
+              f"// cos(j pi/{NCOS // 2}) and sin(j pi/{NCOS // 2}), j = 0..{NCOS - 1}, rounded to nearest",
+              f"static __device__ const double kCosTab[{NCOS}] = {{"]
+    for i in range(0, NCOS, 2):
         lines.append(f"    {to_double(cs[i][0])!r}, {to_double(cs[i + 1][0])!r},")
-    lines += ["};", "static __device__ const double kSinTab[64] = {"]
-    for i in range(0, 64, 2):
+    lines += ["};", f"static __device__ const double kSinTab[{NCOS}] = {{"]
+    for i in range(0, NCOS, 2):
         lines.append(f"    {to_double(cs[i][1])!r}, {to_double(cs[i + 1][1])!r},")
     lines += ["};", "", "}  // namespace gmq", ""]
     with open("gm_math_tables.cuh", "w") as f:

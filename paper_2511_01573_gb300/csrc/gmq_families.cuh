@@ -21,31 +21,30 @@ struct SmemParams {
 };
 
 // FP64 exponential by Tang's table-driven method (P. T. P. Tang, ACM TOMS
-// 15(2), 1989): x = (64 m + j) ln2/64 + r with |r| <= ln2/128, so exp(x) =
-// 2^m 2^(j/64) exp(r); exp(r) - 1 is its Taylor polynomial of degree 5
-// (truncation below 3.6e-17), 2^(j/64) comes from a 64-entry table and 2^m
-// is added to the exponent field.  About 10 FP64 instructions against the
-// ~16 the rule kernels measured for the library exp, within about one ulp
-// of the exact value (gm_math_tables.cuh holds the constants, computed in
-// 60-digit decimal arithmetic).  |x| >= 512 (which covers the overflow and
-// subnormal ranges) and NaN go to the library exp.
+// 15(2), 1989): x = (256 m + j) ln2/256 + r with |r| <= ln2/512, so exp(x) =
+// 2^m 2^(j/256) exp(r); exp(r) - 1 is its Taylor polynomial of degree 4
+// (truncation below 3.8e-17), 2^(j/256) comes from a 256-entry table and 2^m
+// is added to the exponent field.  Nine FP64 instructions (the library exp
+// measured ~16.6 in the rule kernels), within about one ulp of the exact
+// value (gm_math_tables.cuh holds the constants, computed in 60-digit
+// decimal arithmetic).  |x| >= 512 (which covers the overflow and subnormal
+// ranges) and NaN go to the library exp.
 __device__ __forceinline__ double gm_exp(double x) {
   // |x| < 512, tested on the high word (no FP64 compare)
   if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40800000u) return exp(x);
   const double shifter = 6755399441055744.0;  // 1.5 * 2^52: low word of t = nearest integer
   const double t = fma(x, kExpInvL, shifter);
-  const int n = __double2loint(t);            // round(x * 64 / ln2)
+  const int n = __double2loint(t);            // round(x * 256 / ln2)
   const double nd = __dsub_rn(t, shifter);    // the same integer as a double (exact)
-  double r = fma(-nd, kExpL1, x);             // exact: n * kExpL1 has at most 53 bits
+  double r = fma(-nd, kExpL1, x);             // exact (fused: x - n L1 fits 53 bits)
   r = fma(-nd, kExpL2, r);
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(q, r, 1.0 / 6.0);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   q = fma(q, r, 0.5);
   q = fma(q, r, 1.0);
   const double em1 = __dmul_rn(q, r);         // exp(r) - 1
-  const double T = __ldg(&kExp2Tab[n & 63]);
-  const double y = fma(T, em1, T);            // 2^(j/64) exp(r), in [2^(-1/128), 2^(127/128)]
-  const unsigned hi = (unsigned)__double2hiint(y) + ((unsigned)(n >> 6) << 20);
+  const double T = __ldg(&kExp2Tab[n & ((1 << kExpTabBits) - 1)]);
+  const double y = fma(T, em1, T);            // 2^(j/256) exp(r), in [2^(-1/512), 2^(511/512)]
+  const unsigned hi = (unsigned)__double2hiint(y) + ((unsigned)(n >> kExpTabBits) << 20);
   return __hiloint2double((int)hi, __double2loint(y));
 }
 
@@ -71,45 +70,51 @@ __device__ __forceinline__ float grcp(float x) { return 1.0f / x; }
 __device__ __forceinline__ double grcp(double x) { return gm_rcp(x); }
 __device__ __forceinline__ float gexp(float x) { return expf(x); }
 // FP64 cosine by the same table-driven scheme (J.-M. Muller, Elementary
-// Functions, ch. 6): x = n pi/32 + r with a three-part Cody-Waite reduction
-// (exact for |n| < 2^20), |r| <= pi/64; cos(x) = C_j cos(r) - S_j sin(r),
-// j = n mod 64, with C_j = cos(j pi/32), S_j = sin(j pi/32) from 64-entry
-// tables, cos(r) - 1 and sin(r) by their Taylor polynomials of degree 8 and 7
-// (truncation below 1e-19).  About 16 FP64 instructions; absolute error
-// within a few units of 2^-53.  |x| >= 2^16 and non-finite x: the library
-// cos.
+// Functions, ch. 6): x = n pi/128 + r with a two-part Cody-Waite reduction
+// (with fused multiply-adds the first part's step is exact and the second's
+// error is below 2^-70 for |x| < 2^16), |r| <= pi/256; cos(x) = C_j cos(r) -
+// S_j sin(r), j = n mod 256, with C_j = cos(j pi/128), S_j = sin(j pi/128)
+// from 256-entry tables, cos(r) - 1 and sin(r) by their Taylor polynomials of
+// degree 6 and 5 (truncation below 1e-17).  Thirteen FP64 instructions;
+// absolute error within a few units of 2^-53.  |x| >= 2^16 and non-finite x:
+// the library cos.
 __device__ __forceinline__ double gm_cos(double x) {
   // |x| < 2^16, tested on the high word (no FP64 compare)
   if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40f00000u) return cos(x);
   const double shifter = 6755399441055744.0;  // 1.5 * 2^52
   const double t = fma(x, kCosInvQ, shifter);
-  const int n = __double2loint(t);            // round(x * 32 / pi)
+  const int n = __double2loint(t);            // round(x * 128 / pi)
   const double nd = __dsub_rn(t, shifter);
   double r = fma(-nd, kCosP1, x);             // exact
-  r = fma(-nd, kCosP2, r);                    // exact
-  r = fma(-nd, kCosP3, r);
+  r = fma(-nd, kCosP2, r);
   const double z = __dmul_rn(r, r);
-  double c = fma(z, 1.0 / 40320.0, -1.0 / 720.0);
-  c = fma(c, z, 1.0 / 24.0);
+  double c = fma(z, -1.0 / 720.0, 1.0 / 24.0);
   c = fma(c, z, -0.5);
   const double cm1 = __dmul_rn(c, z);         // cos(r) - 1
-  double sp = fma(z, -1.0 / 5040.0, 1.0 / 120.0);
-  sp = fma(sp, z, -1.0 / 6.0);
+  const double sp = fma(z, 1.0 / 120.0, -1.0 / 6.0);
   const double sr = fma(__dmul_rn(r, z), sp, r);  // sin(r)
-  const double C = __ldg(&kCosTab[n & 63]), S = __ldg(&kSinTab[n & 63]);
+  const int j = n & ((1 << kCosTabBits) - 1);
+  const double C = __ldg(&kCosTab[j]), S = __ldg(&kSinTab[j]);
   return fma(-S, sr, fma(C, cm1, C));
 }
 __device__ __forceinline__ double gcos(double x) { return gm_cos(x); }
 __device__ __forceinline__ float gcos(float x) { return cosf(x); }
 
-// x^e for a positive integer exponent by binary powering.
+// x^e for an integer exponent e >= 1 by binary powering: the low zero bits
+// of e square x, the lowest one bit starts the product, each higher bit
+// squares once more and multiplies in the set ones (x^9: three squarings
+// and one product).
 template <class Real>
 __device__ __forceinline__ Real ipow(Real x, int e) {
-  Real r = Real(1);
-  while (e) {
-    if (e & 1) r *= x;
+  if (e < 1) return Real(1);
+  while (!(e & 1)) {
     x *= x;
     e >>= 1;
+  }
+  Real r = x;
+  while (e >>= 1) {
+    x *= x;
+    if (e & 1) r *= x;
   }
   return r;
 }

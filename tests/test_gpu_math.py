@@ -1,9 +1,11 @@
 """The library's FP64 exponential (Tang's table-driven method, used by the
-Gaussian, C0 and discontinuous integrands) and reciprocal (Newton-Raphson
-from the hardware approximation, used by the product-peak and corner-peak
-integrands) against the host's arithmetic and CUDA's: within 2 ulp (exp)
-and 1 ulp (reciprocal) on random arguments over the whole fast range and at
-the edges of the fallback to the library routine."""
+Gaussian, C0 and discontinuous integrands), cosine (table-driven, used by
+the oscillatory integrand) and reciprocal (Newton-Raphson from the hardware
+approximation, used by the product-peak and corner-peak integrands) against
+the host's arithmetic and CUDA's: within 2 ulp (exp), 4 units of 2^-53
+absolute (cos) and 1 ulp (reciprocal) on random arguments over the whole
+fast range, at the reduction boundaries and at the edges of the fallback to
+the library routine."""
 import numpy as np
 import pytest
 
@@ -24,7 +26,7 @@ def test_exp_accuracy(gpu_ctx):
         rng.uniform(-20.0, 0.0, 1 << 18),           # the integrands' usual range
         np.array([0.0, -0.0, 1e-300, -1e-300, 5e-324, 1.0, -1.0, 706.99, -706.99,
                   707.0, -707.0, 708.5, -708.5, 709.7, -745.0, -746.0, 710.0]),
-        np.log(2.0) / 128 * np.arange(-64, 65),      # reduction boundaries
+        np.log(2.0) / 512 * np.arange(-256, 257),    # reduction boundaries
     ])
     xd = torch.tensor(x, dtype=torch.float64, device="cuda")
     y = gpu_ctx.math_exp(xd).cpu().numpy()
@@ -70,7 +72,7 @@ def test_cos_accuracy(gpu_ctx):
         rng.uniform(-100.0, 100.0, 1 << 20),
         rng.uniform(0.0, 15.0, 1 << 18),             # the oscillatory family's range
         rng.uniform(-99999.0, 99999.0, 1 << 16),
-        np.pi / 32 * np.arange(-200, 201) + 1e-12,  # table boundaries
+        np.pi / 256 * np.arange(-800, 801) + 1e-12,  # reduction boundaries
         np.array([0.0, -0.0, 1e-300, np.pi / 2, np.pi, 1e5, -1e5, 1e6, np.inf, np.nan]),
     ])
     xd = torch.tensor(x, dtype=torch.float64, device="cuda")
