@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--probe-gk", default=None,
                     help="profiling probe: family codes; the Gauss-Kronrod rule kernel on 2^13 "
                          "random d=4 regions, three launches per family")
+    ap.add_argument("--probe-grad", default=None,
+                    help="profiling probe: family codes; the adjoint kernel on 2^18 random "
+                         "d=8 regions, three calls per family")
     ap.add_argument("--host-loop", action="store_true",
                     help="with --probe-batch: the host-driven sweep loop instead of the graph")
     ap.add_argument("--kernel-sweep", action="store_true",
@@ -364,6 +367,36 @@ def probe_rule(args):
     ctx.close()
 
 
+def probe_grad(args):
+    """The adjoint kernel (k_rule_grad: f and its 2d parameter derivatives at
+    every node) alone on 2^18 random sub-boxes of [0,1]^8 (17 output rows,
+    about 70 MB of inputs and outputs), three calls per family, for ncu
+    captures; prints the event-timed rate of the kernel and of the row sums."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    n, d = 1 << 18, 8
+    g = torch.Generator(device="cuda").manual_seed(3)
+    lo = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.9
+    w = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.05 + 1e-3
+    c = (lo + 0.5 * w).contiguous()
+    h = (0.5 * w).contiguous()
+    ctx = gmq.Context(0)
+    ctx.profile(True)
+    for fam in (int(x) for x in args.probe_grad.split(",")):
+        a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM.get(fam, 2.0))
+        ctx.profile_reset()
+        for _ in range(3):
+            ctx.rule_grad(fam, a, u, c, h)
+        p = ctx.profile_read()
+        r, s = p["rule"], p["sum"]
+        print(f"grad family {fam} d {d}: {r['launches']} launches, "
+              f"{r['ms'] / r['launches']:.3f} ms/launch, "
+              f"{n * r['launches'] / r['ms'] * 1e3:.4g} regions/s; row sums "
+              f"{s['ms'] / max(s['launches'], 1):.3f} ms/launch", flush=True)
+    ctx.close()
+
+
 def probe_split(args):
     """Classify + split alone on 2^22 random d = 8 regions (three calls):
     HBM-bound kernels.  The budget is the median per-region threshold, so
@@ -670,6 +703,8 @@ def main():
         return probe_batch(args)
     if args.probe_gk:
         return probe_gk(args)
+    if args.probe_grad:
+        return probe_grad(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch

@@ -301,8 +301,9 @@ gmq_status gmq_launch_count(gmq_context *ctx, int64_t *count);
 /* Kernel timing.  While enabled, the context brackets each kernel it
  * launches with CUDA events on its stream and, when the call waits for the
  * stream, adds the measured durations to per-kernel totals.  kernel: 0 rule
- * evaluation, 1 global sums, 2 classify, 3 split, 4 partition.  `regions`
- * counts the regions the launches processed.  Enabling adds two event
+ * evaluation (the Genz-Malik, Gauss-Kronrod and gmq_rule_grad kernels), 1
+ * global sums (also gmq_rule_grad's row sums), 2 classify, 3 split, 4
+ * partition.  `regions` counts the regions the launches processed.  Enabling adds two event
  * records per launch. */
 typedef struct gmq_kernel_stats {
   int64_t launches;

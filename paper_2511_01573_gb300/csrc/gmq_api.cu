@@ -1743,6 +1743,7 @@ gmq_status gmq_rule_grad(gmq_context* ctx, const gmq_problem* prob, int64_t n,
   A.R = rule_const(d, prob->lo, prob->hi);
   cudaStream_t strm = ctx->stream;
   cudaError_t e;
+  prof_begin(ctx, kKRule);
   switch (prob->family) {
     case GMQ_OSCILLATORY: e = launch_rule_grad_family<GMQ_OSCILLATORY>(A, strm); break;
     case GMQ_PRODUCT_PEAK: e = launch_rule_grad_family<GMQ_PRODUCT_PEAK>(A, strm); break;
@@ -1753,14 +1754,18 @@ gmq_status gmq_rule_grad(gmq_context* ctx, const gmq_problem* prob, int64_t n,
     default: e = launch_rule_grad_family<GMQ_POLY_SUMSQ11>(A, strm); break;
   }
   GMQ_CK(e);
+  prof_end(ctx, kKRule, n);
   GMQ_CK(cudaMemsetAsync(b + o_tk, 0, sizeof(unsigned) * (size_t)rows, strm));
+  prof_begin(ctx, kKSum);
   GMQ_CK(launch_rows_tree_sum(A.out, ldo, n, rows, (double*)(b + o_blk), (unsigned*)(b + o_tk),
                               (double*)(b + o_sum), strm));
+  prof_end(ctx, kKSum, n);
   ctx->launches += 2;
   std::vector<double> sums((size_t)rows);
   GMQ_CK(cudaMemcpyAsync(sums.data(), b + o_sum, sizeof(double) * (size_t)rows,
                          cudaMemcpyDeviceToHost, strm));
   GMQ_CK(cudaStreamSynchronize(strm));
+  prof_collect(ctx);
   for (int k = 0; k < 2 * d; ++k) grad[k] = sums[(size_t)k];
   *integral = sums[(size_t)(2 * d)];
   return GMQ_OK;
