@@ -82,13 +82,13 @@ typedef enum gmq_classifier {
   GMQ_LOCAL_REL = 1     /* retire r if eps_r <= rel_tol |I_r|                                    */
 } gmq_classifier;
 
-/* Quadrature rule (paper Sec. 3: the framework accommodates several rules).
+/* Quadrature rule (paper Sec. 3: the method is not tied to one rule).
  * GMQ_RULE_GENZ_MALIK: the degree-7 Genz-Malik rule with its embedded
  * degree-5 rule (Sec. 2), any dim.  GMQ_RULE_GAUSS_KRONROD: the
  * tensor-product Gauss-Kronrod rule, 7-point Gauss / 15-point Kronrod per
  * axis (15^dim nodes per region; the paper names the rule but not its order
- * -- this is the classic pair), FP64 only, dim <= GMQ_GK_MAX_DIM (the paper
- * finds its cost prohibitive from dim 7).  Its error estimate is
+ * -- this is the classic pair), FP64 only, dim <= GMQ_GK_MAX_DIM (Sec. 4
+ * reports its cost as too high from dim 7 on).  Its error estimate is
  * |I_K - I_G|; its split axis is the one with the largest directional
  * estimate prod h_k |sum (prod_{j != k} wK)(wK_k - wG_k) f| (G7 along that
  * axis only), or the widest axis when all of those are below 1e-11 of the

@@ -459,8 +459,8 @@ int64_t or_partition(int d, const double *lo, const double *hi, int32_t s,
 /* ------------------------------------------------------------------------ */
 
 /*
- * Reading of the classifier ("discard regions whose contribution to the
- * error is negligible"):
+ * Reading of the classifier (Sec. 3 drops the regions that add only a
+ * negligible amount to the error, without a formula):
  *   classifier 0 (volume share): retire r if err_r <= budget * (vol_r / vol_omega),
  *       budget = max(abs_tol, rel_tol |I|) from this sweep's global estimate;
  *   classifier 1 (local relative): retire r if err_r <= rel_tol |I7_r|.

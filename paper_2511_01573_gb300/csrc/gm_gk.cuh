@@ -1,7 +1,7 @@
-// gm_gk.cuh -- the tensor-product Gauss-Kronrod (7, 15) rule (paper Sec. 3:
-// the framework accommodates several rules, among them a tensor-product
-// Gauss-Kronrod rule; order and split axis are not printed -- the readings
-// here are the classic G7/K15 pair and the directional error estimates).
+// gm_gk.cuh -- the tensor-product Gauss-Kronrod (7, 15) rule (paper Sec. 3
+// names a tensor-product Gauss-Kronrod rule as one of the rules the method
+// can use, without its order or split axis -- the readings here are the
+// classic G7/K15 pair and the directional error estimates).
 //
 // On a region c +- h the rule evaluates f at the 15^d nodes c + h o xi,
 // xi in {K15 nodes}^d, and forms
