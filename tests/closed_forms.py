@@ -12,7 +12,7 @@ from itertools import combinations
 try:
     import mpmath as mp
     mp.mp.dps = 50
-except ImportError:  # the GPU machine has no mpmath
+except ImportError:  # mpmath is optional; without it the forms run in FP64
     mp = None
 
 OSCILLATORY, PRODUCT_PEAK, CORNER_PEAK, GAUSSIAN, C0, DISCONTINUOUS, POLY_SUMSQ11 = range(7)
