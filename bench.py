@@ -293,21 +293,25 @@ def run_reference(args):
     cores = host_cores()
     pool = OraclePool(cores)
     per_step = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
-    vals = []
+    vals, walls = [], []
     sample_desc = ""
     for step in range(args.warmup + args.steps):
         v, done, wall = pool.run(probs, per_step)
         if step >= args.warmup:
             vals.append(v)
+            walls.append(wall)
             sample_desc = (f"{done} of {len(probs)} integrations in tolerance order, "
                            f"{cores} processes, problems started within {per_step:.1f} s "
                            f"({wall:.1f} s), pool 2^16")
     pool.close()
     v = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "genz_d8_4families_seeds1-10_tol1e-3..1e-8_cap2^24"},
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(walls) / len(walls), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"genz_d8_4families_seeds1-{args.seeds}_tol{args.tols}_cap2^24",
+                       "integrations_per_step": len(probs), "parallelism": "replicas1",
+                       "sample": "each step a bounded sample of the integrations"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample_desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
