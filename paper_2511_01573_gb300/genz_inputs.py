@@ -182,6 +182,19 @@ def gaussian_grad_sets(count=1024, dim=6, master_seed=1):
     return [seed_uniform(master_seed * 65536 + i, GAUSSIAN, dim, 0.5, 3.0) for i in range(count)]
 
 
+def random_dyadic_boxes(seed: int, n: int, dim: int):
+    """n random sub-boxes of [0,1]^dim shaped like the regions a refinement
+    leaves (AoS, n x d): per axis the half-width is 2^-j, j uniform in
+    1..12, and the centre is uniform over the positions that keep the box in
+    [0,1].  Vectorised (numpy's PCG64 seeded with `seed`), for lists of
+    millions of regions."""
+    rng = np.random.default_rng(seed)
+    j = rng.integers(1, 13, size=(n, dim)).astype(np.int32)
+    h = np.ldexp(1.0, -j)
+    c = h + (1.0 - 2.0 * h) * rng.random((n, dim))
+    return c, h
+
+
 def random_boxes(seed: int, n: int, dim: int, lo=0.0, hi=1.0):
     """n random sub-boxes of [lo,hi]^dim: centres and half-widths (AoS, n x d)."""
     g = SplitMix64(stream_state(seed, 255, dim))

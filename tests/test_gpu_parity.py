@@ -87,6 +87,37 @@ def test_rule_max_dim(oracle, gpu_ctx):
         _compare_rule(oracle, gpu_ctx, G.GAUSSIAN, 16, lanes, n=1)
 
 
+def test_rule_full_size_sampled(oracle, gpu_ctx):
+    """A d = 8 sweep of the benchmark's size (2^22 + 17 regions, dyadic
+    widths as refinement leaves them) in the launch configuration the
+    library picks for such a list (lanes = 0: one thread per region): a
+    sample of about a thousand regions, including both ends and the
+    128-region block edges, against the oracle with the per-region
+    tolerances above."""
+    n, d = (1 << 22) + 17, 8
+    c, h = G.random_dyadic_boxes(2511, n, d)
+    cd, hd = _soa(c), _soa(h)
+    rng = np.random.default_rng(8)
+    edges = [0, 1, 127, 128, 129, n // 2, n - 18, n - 17, n - 2, n - 1]
+    idx = np.unique(np.concatenate([edges, rng.integers(0, n, 1024)]))
+    for fam in G.GENZ_D8_FAMILIES:
+        a, u = _params(fam, d)
+        i7, err, vf, ax = gpu_ctx.eval_rule(fam, a, u, cd, hd, lanes=0)
+        i7 = i7.cpu().numpy()[idx]
+        err = err.cpu().numpy()[idx]
+        vf = vf.cpu().numpy()[idx]
+        ax = ax.cpu().numpy().astype(np.int32)[idx]
+        o = oracle.rule_regions(fam, a, u, np.ascontiguousarray(c[idx]),
+                                np.ascontiguousarray(h[idx]))
+        scale = o["i7abs"]
+        assert np.all(np.abs(i7 - o["i7"]) <= 1e-12 * scale), fam
+        assert np.all(np.abs(err - o["err"]) <= 1e-12 * scale), fam
+        assert np.array_equal(vf, o["vol"])
+        tie = o["axis_tie"].astype(bool)
+        assert np.array_equal((ax & 0x7F)[~tie], o["axis"][~tie]), fam
+        assert np.array_equal((ax >> 7)[~tie], o["split_bad"][~tie])
+
+
 def test_rule_auto_lanes_and_ragged(oracle, gpu_ctx):
     # tile edges: n = 1, RB - 1, RB + 1 for every lane count; automatic choice
     for n in (1, 3, 4, 5, 31, 33, 127, 129):
