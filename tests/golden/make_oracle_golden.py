@@ -3,7 +3,8 @@ test functions f1..f7 (paper Sec. 4, the integrand list; f6 as read in the
 paper-readings of this project: zero when any x_i exceeds (3 + i)/10) on
 [0,1]^3 at relative tolerance 1e-6, and the d = 3 product-peak
 configuration (a_j = 5, u_j = 1/2, tolerance 1e-6, cap 1e5).  Calls only
-oracle/; a regression fixture for the oracle, not a pin of it (the pins are
+oracle/; each case keeps the oracle's per-sweep trace (region and split
+counts, near-tie decisions, global estimates).  A regression fixture for the oracle, not a pin of it (the pins are
 in tests/test_oracle_*.py).
 
 Run from the repository root: python tests/golden/make_oracle_golden.py
@@ -34,7 +35,9 @@ def run(p, cap):
     return {"integral": r.integral.hex(), "integral_dec": repr(r.integral),
             "error": r.error.hex(), "regions_evaluated": r.regions_evaluated,
             "function_evals": r.function_evals, "iterations": r.iterations,
-            "status": r.status, "near_ties": r.near_ties}
+            "status": r.status, "near_ties": r.near_ties,
+            "trace": [{"n": t["n"], "n_split": t["n_split"], "near_ties": t["near_ties"],
+                       "I": t["I"], "E": t["E"], "budget": t["budget"]} for t in r.trace]}
 
 
 def main():

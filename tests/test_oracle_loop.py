@@ -202,3 +202,31 @@ def test_status_codes(oracle):
     # corner peak with 1 + a x = 0 at the centre node: pow(0, -2) = inf
     r = oracle.integrate(G.CORNER_PEAK, [-2.0], [0.0], 1e-6, init_splits=1)
     assert r.status == -4
+
+
+def test_classify_near_tie_flag_stays_off_away_from_thresholds(oracle):
+    """Classification decisions well away from their thresholds (a factor
+    two either side, the round-off guard far away) are not near-ties; the
+    same region 1e-14 relative from its threshold is."""
+    i7 = np.array([1.0, 2.0, -3.0, 0.5])
+    vol = np.full(4, 0.25)
+    err = np.array([0.125, 0.5, 0.1, 1.0])  # shares 0.25: retire, split, retire, split
+    r = oracle.classify(i7, err, vol, [0, 0, 0, 0], vol_omega=1.0, budget=1.0)
+    assert list(r["flags"]) == [0, 1, 0, 1] and r["near_ties"] == 0
+    err2 = err.copy()
+    err2[0] = 0.25 * (1 + 1e-14)
+    r = oracle.classify(i7, err2, vol, [0, 0, 0, 0], vol_omega=1.0, budget=1.0)
+    assert r["near_ties"] == 1
+
+
+def test_whole_runs_without_near_ties(oracle):
+    """Asymmetric smooth problems take every decision clear of the near-tie
+    bands: these runs must report no flagged decision in any sweep (their
+    GPU comparisons then check every sweep)."""
+    a, u = G.seed_genz(1, G.C0, 4, 2.0)
+    r = oracle.integrate(G.C0, a, u, 1e-6, max_regions=1 << 20)
+    assert r.status == 0 and r.iterations == 8
+    assert r.near_ties == 0 and all(t["near_ties"] == 0 for t in r.trace)
+    a, u = G.seed_genz(5, G.PRODUCT_PEAK, 5, 25.0)
+    r = oracle.integrate(G.PRODUCT_PEAK, a, u, 1e-5, max_regions=1 << 20)
+    assert r.status == 0 and r.iterations == 7 and r.near_ties == 0

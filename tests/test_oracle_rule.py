@@ -261,3 +261,22 @@ def test_split_guard(oracle):
     assert r.flat and r.axis == 0 and r.split_bad
     r = oracle.rule(c, np.array([0.25, 0.25]), f=lambda x: float(x[0]) ** 4)
     assert not r.split_bad
+
+
+def test_near_tie_flag_stays_off_for_clear_choices(oracle):
+    """The axis near-tie flag must not fire when the choice is clear: a
+    parity test skips flagged axes, so a flag that over-fires would hide
+    mismatches.  Fourth differences in ratio 2:1 (x_0^4 against x_1^4 / 2),
+    and a clearly non-flat exponential, are not near-ties."""
+    c, h = [0.4, 0.55, 0.5], [0.3, 0.3, 0.2]  # equal widths on axes 0 and 1
+    r = oracle.rule(c, h, f=lambda x: x[0] ** 4 + 0.5 * x[1] ** 4 + x[2])
+    assert r.axis == 0 and not r.axis_tie and not r.flat
+    assert r.D[0] > 1.9 * r.D[1] and r.D[2] <= 1e-15 * r.D[0]
+    r = oracle.rule(c, h, f=lambda x: math.exp(0.3 * x[0] + 2.0 * x[1] - x[2]))
+    assert r.axis == 1 and not r.axis_tie
+    # runner-up 1e-9 below the best (far outside the 1e-12 band): no flag;
+    # 1e-14 below: flagged
+    r = oracle.rule([0.5, 0.5], [0.5, 0.5], f=lambda x: x[0] ** 4 + (1 - 1e-9) * x[1] ** 4)
+    assert r.axis == 0 and not r.axis_tie
+    r = oracle.rule([0.5, 0.5], [0.5, 0.5], f=lambda x: x[0] ** 4 + (1 - 1e-14) * x[1] ** 4)
+    assert r.axis == 0 and r.axis_tie
