@@ -79,13 +79,33 @@ CAP = 1 << 24
 # FP64 work of the rule kernel per region at d = 8 (401 nodes), per family:
 # FP64 thread-instructions (sm__thread_inst_executed_pipe_fp64_pred_on) and
 # flops (FMA = 2), from the ncu counters of a launch over 2^20 regions
-# (profiles/rule_fp64_d8.md).  The counts are fixed by the integrand and d:
-# the four families take no data-dependent branch.  Family codes: 0
-# oscillatory, 1 product peak, 2 corner peak, 3 Gaussian, 4 C0.
+# (bench.py --probe-rule under ncu).  The counts are fixed by the integrand,
+# d and the compiled kernel: the four families take no data-dependent
+# branch.  They hold for the kernel sources whose fingerprint is
+# RULE_COUNTS_SHA16; when those sources change the counts must be taken
+# again (tests/test_bench_counts.py fails until they are), and until then
+# the roofline reports no fraction.  Family codes: 0 oscillatory, 1 product
+# peak, 2 corner peak, 3 Gaussian, 4 C0.
 RULE_FP64_INST_D8 = {0: 9006.0, 1: 11813.0, 2: 7803.0, 3: 14219.0, 4: 11011.0}
 RULE_FP64_FLOPS_D8 = {0: 15866.0, 1: 16668.0, 2: 12658.0, 3: 20277.0, 4: 17069.0}
-# DRAM bytes per region of the rule kernel in the same capture (128 B read,
-# ~13 B written of 25 B of outputs); traffic per launch scales with regions.
+RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
+                       "gm_math_tables.cuh", "gmq_common.cuh")
+RULE_COUNTS_SHA16 = "4c0281fcc3e7753d"
+
+
+def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
+    """First 16 hex digits of the SHA-256 of the FP64 rule kernel's sources
+    (file name, then contents, in the order given)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2511_01573_gb300", "csrc")
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 RULE_DRAM_BYTES_PER_REGION_D8 = 141.1
 
 
@@ -770,11 +790,27 @@ def main():
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read()
     timed_fam_regions = dict(fam_regions)
-    # e2e: host wall clock through the public call (one step)
+    # measured FP64 FMA issue rate of this GPU (the roofline's peak): the
+    # probe kernel after a warm-up launch, clocks sampled meanwhile
+    with ClockSampler(dev) as pclk:
+        ctx.probe_fma_rate(gmq.FP64, iters=2000)
+        probe64 = max(ctx.probe_fma_rate(gmq.FP64)[0] for _ in range(3))
+    probe_clocks = pclk.summary()
+    # e2e: host wall clock through the public call (one step), with the
+    # per-launch timing events off; its device time (events around the whole
+    # step) against the timed steps' shows what those events cost
+    ctx.profile(False)
+    flush.fill_(1)
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
+    e0.record(stream)
     e2e_regions, e2e_sweeps = step()
+    e1.record(stream)
     e2e_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    unprofiled_ms = e0.elapsed_time(e1)
     tt = time_to_tol(ctx, stream, 1e-6) if not args.no_time_to_tol else None
 
     ms_step = total_ms / args.steps
@@ -788,26 +824,35 @@ def main():
     # region of each family at d = 8 (a fixed count: the integrand at 401
     # nodes plus one accumulation each and the per-region epilogue) times the
     # regions of that family in the timed steps, over the rule kernel's
-    # event-timed launches.  Peak: 2 FP64 FMA lanes per clock per SM (1.25 TFLOP/s
-    # nominal / 2 / 152 SMs / 2.07 GHz) at the measured median SM clock.
+    # event-timed launches.  Peak: the measured FP64 FMA issue rate (probe
+    # kernel, same process); beside it the nominal 2 FP64 lanes per clock per
+    # SM (1.25 TFLOP/s / 2 / 152 SMs / 2.07 GHz) at the median SM clock.
     roof = None
     clocks = clk.summary()
+    counts_current = rule_source_fingerprint() == RULE_COUNTS_SHA16
     if rule["launches"] and all(f in RULE_FP64_INST_D8 for f in timed_fam_regions):
         n_launch = rule["launches"]
         avg_s = rule["ms"] / 1000.0 / n_launch
         inst = sum(RULE_FP64_INST_D8[f] * n for f, n in timed_fam_regions.items()) / n_launch
         flops = sum(RULE_FP64_FLOPS_D8[f] * n for f, n in timed_fam_regions.items()) / n_launch
         mhz = clocks.get("sm_mhz") or 2070.0
-        peak_inst = 2 * 152 * mhz * 1e6 / 1e9  # G FP64 lane-inst/s
+        peak_nominal = 2 * 152 * mhz * 1e6 / 1e9  # G FP64 lane-inst/s
+        peak = probe64 / 1e9
         ach = inst / avg_s / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": peak_inst,
-                "unit": "G FP64 lane-inst/s", "frac": ach / peak_inst,
-                "traffic": RULE_DRAM_BYTES_PER_REGION_D8 * rule["regions"] / n_launch,
+        roof = {"bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "G FP64 lane-inst/s", "frac": ach / peak if counts_current else None,
+                "traffic": (RULE_DRAM_BYTES_PER_REGION_D8 * rule["regions"] / n_launch
+                            if counts_current else None),
                 "kernel": "k_rule64 (FP64 rule evaluation)",
-                "peak_basis": (f"2 FP64 lanes/clk/SM (1.25 TFLOP/s nominal) x 152 SMs "
-                               f"x median {mhz:.0f} MHz"),
+                "peak_basis": ("measured: FP64 FMA probe (gmq_probe_fma_rate, 64 warps/SM, "
+                               "16 independent chains per thread) in this run, median "
+                               f"{probe_clocks.get('sm_mhz')} MHz"),
+                "nominal": {"peak": peak_nominal, "frac": ach / peak_nominal,
+                            "basis": (f"2 FP64 lanes/clk/SM (1.25 TFLOP/s nominal) x 152 SMs "
+                                      f"x median {mhz:.0f} MHz")},
+                "counts_match_source": counts_current,
                 "flops_view": {"achieved_gflops": flops / avg_s / 1e9,
-                               "peak_gflops": 2 * peak_inst},
+                               "peak_gflops_measured": 2 * peak},
                 "inst_per_region": {G.FAMILY_NAMES[f]: RULE_FP64_INST_D8[f]
                                     for f in sorted(timed_fam_regions)},
                 "regions_by_family": {G.FAMILY_NAMES[f]: n // args.steps
@@ -822,6 +867,8 @@ def main():
                    "parallelism": f"replicas{ws}"},
         "gpu_launches": launches,
         "kernels": prof,
+        "unprofiled_step": {"ms": unprofiled_ms, "timed_ms_per_step": total_ms / args.steps,
+                            "note": "the e2e step, per-launch timing events off"},
         "roofline": roof,
         "e2e": {"value": e2e_regions / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": len(probs) * 4 * 8 * 8,

@@ -246,7 +246,8 @@ typedef struct gmq_batch_info {
  * their results unchanged); if nothing can split, the paused problem of
  * highest index is evicted and later restarts from its initial partition
  * (same result again), and a problem that cannot grow even alone stops with
- * GMQ_CAP_REACHED.  The device loop is bounded by 4 x max_iters sweeps.
+ * GMQ_CAP_REACHED.  The device loop is bounded by 4 x max_iters sweeps
+ * (max_iters above 2^28 is rejected with GMQ_ERR_INVALID).
  * Device memory: about pool_regions x (32 dmax + 60) bytes, dmax the
  * largest dimension.
  * opt->precision GMQ_FP64: lanes per region opt->lanes (1, 4, 32 or 128)
@@ -314,6 +315,19 @@ typedef struct gmq_kernel_stats {
 gmq_status gmq_profile_enable(gmq_context *ctx, int32_t on);
 gmq_status gmq_profile_reset(gmq_context *ctx);
 gmq_status gmq_profile_read(gmq_context *ctx, int32_t kernel, gmq_kernel_stats *out);
+
+/* Measurement aid (no counterpart in the paper): the fused multiply-add
+ * issue rate of the context's GPU, measured, as the peak the rule kernels'
+ * rooflines are reported against.  precision GMQ_FP64 times FP64 FMAs,
+ * GMQ_MIXED FP32 FMAs.  One launch of 8 x (SM count) blocks of 256 threads
+ * (64 warps per SM), each thread running `iters` iterations of 16
+ * independent FMA chains (1 <= iters <= 2^32), timed with CUDA events on
+ * the context stream; the call waits for it.  *lane_fma_per_s receives the
+ * lane FMAs per second (one FMA of one thread = one lane FMA = 2 flops),
+ * *ms the launch's duration.  Its 8 x (SM count) x 256 x 8-byte result
+ * sink is context memory (shared with gmq_rule_grad's working memory). */
+gmq_status gmq_probe_fma_rate(gmq_context *ctx, int32_t precision, int64_t iters,
+                              double *lane_fma_per_s, double *ms);
 
 /* ---- step-level calls on caller device memory (one sweep's pieces) ---- */
 
@@ -426,16 +440,20 @@ gmq_status gmq_partition(gmq_context *ctx, int32_t dim, const double *lo,
  *
  * Working memory: a file-scope static device array of about 64 KiB (the
  * last-block ticket and one partial sum per 1024-value tile), which every
- * device that loads the library keeps until the process exits.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture.  All calls
- * share the one array, and each call clears the ticket it needs on its own
- * stream, so calls whose work overlaps on the GPU (different streams, or
- * several host threads) race and must be serialised by the caller.
+ * device that loads the library keeps until the process exits.  Every call
+ * looks up the array's device address on `device` (cudaGetSymbolAddress,
+ * which allocates nothing); the first lookup on a device may load the
+ * library's device code there, so make the first call on a device before
+ * any stream capture.  All calls share the one array, and each call clears
+ * the ticket it needs on its own stream, so calls whose work overlaps on the
+ * GPU (different streams, or several host threads) race and must be
+ * serialised by the caller.
  *
  * Errors: GMQ_ERR_TOO_LARGE if n > GMQ_NOALLOC_MAX_N (nothing is enqueued);
- * GMQ_ERR_INVALID for a negative n, a NULL pointer or a bad device;
- * GMQ_ERR_CUDA if the address lookup, the memset or the launch fails.  The
+ * GMQ_ERR_INVALID for a negative n, a NULL pointer, a bad device, or d_v /
+ * d_sum not in that device's memory; GMQ_ERR_CUDA if the address lookup,
+ * the memset or the launch fails (the CUDA error is cleared before the
+ * call returns).  The
  * call makes no cudaMalloc, cudaFree or other allocating call. */
 gmq_status gmq_tree_sum_noalloc(int32_t device, int64_t n, const double *d_v,
                                 double *d_sum, void *cuda_stream);

@@ -32,6 +32,7 @@ def _units():
     units = [(os.path.join(CSRC, "gmq_api.cu"), "gmq_api.o", []),
              (os.path.join(CSRC, "sweep_kernels.cu"), "sweep_kernels.o", []),
              (os.path.join(CSRC, "noalloc_sum.cu"), "noalloc_sum.o", []),
+             (os.path.join(CSRC, "fma_probe.cu"), "fma_probe.o", []),
              (os.path.join(CSRC, "gm_batch.cu"), "gm_batch.o", [])]
     for fam in range(NUM_FAMILIES):
         units.append((os.path.join(CSRC, "gm_rule_inst.cu"), f"gm_rule_f{fam}.o",

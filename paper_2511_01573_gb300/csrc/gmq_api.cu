@@ -1233,6 +1233,43 @@ gmq_status gmq_partition(gmq_context* ctx, int32_t dim, const double* lo, const 
   return GMQ_OK;
 }
 
+gmq_status gmq_probe_fma_rate(gmq_context* ctx, int32_t precision, int64_t iters,
+                              double* lane_fma_per_s, double* ms) {
+  if (!ctx || !lane_fma_per_s || !ms || iters < 1 || iters > ((int64_t)1 << 32) ||
+      (precision != GMQ_FP64 && precision != GMQ_MIXED))
+    return GMQ_ERR_INVALID;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return GMQ_ERR_CUDA;
+  const int blocks = ctx->sm_count * 8;  // 64 warps per SM
+  const size_t sink = sizeof(double) * (size_t)blocks * kProbeBlock;
+  if (ctx->gscratch_bytes < sink) {
+    if (ctx->gscratch) cudaFree(ctx->gscratch);
+    ctx->gscratch = nullptr;
+    ctx->gscratch_bytes = 0;
+    void* q = nullptr;
+    if (cudaMalloc(&q, sink) != cudaSuccess) {
+      cudaGetLastError();
+      return GMQ_ERR_OOM;
+    }
+    ctx->gscratch = (char*)q;
+    ctx->gscratch_bytes = sink;
+  }
+  EventPair ev;
+  GMQ_CK(cudaEventCreate(&ev.a));
+  GMQ_CK(cudaEventCreate(&ev.b));
+  const int fp64 = precision == GMQ_FP64 ? 1 : 0;
+  GMQ_CK(cudaEventRecord(ev.a, ctx->stream));
+  GMQ_CK(launch_fma_probe(fp64, blocks, iters, ctx->gscratch, ctx->stream));
+  GMQ_CK(cudaEventRecord(ev.b, ctx->stream));
+  ctx->launches += 1;
+  GMQ_CK(cudaEventSynchronize(ev.b));
+  float t = 0.f;
+  GMQ_CK(cudaEventElapsedTime(&t, ev.a, ev.b));
+  *ms = (double)t;
+  *lane_fma_per_s = t > 0.f ? (double)fma_probe_lane_fmas(blocks, iters) / ((double)t * 1e-3) : 0.0;
+  return GMQ_OK;
+}
+
 gmq_status gmq_profile_enable(gmq_context* ctx, int32_t on) {
   if (!ctx) return GMQ_ERR_INVALID;
   if (on && !ctx->ev_made) {
@@ -1295,7 +1332,8 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     return GMQ_ERR_INVALID;
   const int64_t cap = opt->max_regions;  // per problem
   if (!(opt->abs_tol >= 0.0) || cap < 1 || cap > kMaxRegions || opt->init_splits < 0 ||
-      opt->max_iters < 0 || (opt->flags & ~GMQ_BATCH_HOST_LOOP) ||
+      opt->max_iters < 0 || opt->max_iters > (1 << 28) ||  // the loop bound 4 x max_iters is an int
+      (opt->flags & ~GMQ_BATCH_HOST_LOOP) ||
       (opt->precision != GMQ_FP64 && opt->precision != GMQ_MIXED) ||
       (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32 &&
        opt->lanes != 128) ||

@@ -65,7 +65,7 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
            "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad",
            "gmq_integrate_batch", "gmq_last_batch_info", "gmq_eval_rule_gk", "gmq_gk_table",
-           "gmq_math_exp", "gmq_math_rcp", "gmq_math_cos")
+           "gmq_math_exp", "gmq_math_rcp", "gmq_math_cos", "gmq_probe_fma_rate")
 
 KEEP_PARTITION = 1
 BATCH_HOST_LOOP = 2
@@ -147,6 +147,7 @@ def lib():
         "gmq_math_exp": [vp, i64, vp, vp],
         "gmq_math_rcp": [vp, i64, vp, vp],
         "gmq_math_cos": [vp, i64, vp, vp],
+        "gmq_probe_fma_rate": [vp, i32, i64, C.POINTER(dbl), C.POINTER(dbl)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -212,7 +213,11 @@ def tree_sum_noalloc(v, out, stream=None) -> int:
     if v.numel() > 1 and not v.is_contiguous():
         raise ValueError("v must be contiguous")
     dev = v.device.index
+    if out.device != v.device:
+        raise ValueError(f"out is on {out.device}, v on {v.device}")
     s = stream if stream is not None else torch.cuda.current_stream(dev)
+    if s.device != v.device:
+        raise ValueError(f"stream is on {s.device}, v on {v.device}")
     return lib().gmq_tree_sum_noalloc(dev, v.numel(), C.c_void_p(v.data_ptr()),
                                       C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream))
 
@@ -296,6 +301,17 @@ class Context:
             _check("gmq_profile_read", lib().gmq_profile_read(self.h, k, C.byref(s)))
             out[name] = {"launches": int(s.launches), "regions": int(s.regions), "ms": s.ms}
         return out
+
+    def probe_fma_rate(self, precision=FP64, iters=None):
+        """Measured FMA issue rate of this GPU (lane FMAs per second) and the
+        probe launch's milliseconds; FP64 by default, FP32 with MIXED."""
+        if iters is None:
+            iters = 20000 if precision == FP64 else 1_000_000
+        rate = C.c_double()
+        ms = C.c_double()
+        _check("gmq_probe_fma_rate", lib().gmq_probe_fma_rate(self.h, precision, iters,
+                                                              C.byref(rate), C.byref(ms)))
+        return rate.value, ms.value
 
     def launch_count(self) -> int:
         n = C.c_int64()

@@ -160,4 +160,7 @@ def test_batch_autotune_cached_and_limits(gpu_ctx):
         gpu_ctx.integrate_batch(probs, pool_regions=64)
     with pytest.raises(gmq.GmqError):
         gpu_ctx.integrate_batch(probs, lanes=8)
+    with pytest.raises(gmq.GmqError):
+        # the device loop's bound 4 x max_iters must fit an int
+        gpu_ctx.integrate_batch(probs, max_iters=(1 << 28) + 1)
     assert len(again) == len(probs)

@@ -53,3 +53,45 @@ def test_noalloc_sum_limits(gpu_ctx):
     assert _noalloc_sum(gmq, v[:gmq.NOALLOC_MAX_N]) == float(gmq.NOALLOC_MAX_N)
     assert _noalloc_sum(gmq, v[:0]) == 0.0
     assert _noalloc_sum(gmq, v[:1]) == 1.0
+
+
+def test_noalloc_sum_on_a_side_stream_and_another_thread(gpu_ctx):
+    """The call orders its own clear and launch on the stream it is given:
+    on a fresh side stream, with nothing synchronising the default stream,
+    it still gives the bits of gmq_tree_sum; a later call from another host
+    thread (after the first has finished) does too."""
+    import threading
+    from paper_2511_01573_gb300 import gmq
+    rng = np.random.default_rng(7)
+    v = torch.tensor(rng.standard_normal(2_000_003), device="cuda")
+    want = gpu_ctx.tree_sum(v)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    assert gmq.tree_sum_noalloc(v, out, stream=side) == gmq.OK
+    side.synchronize()
+    assert float(out.item()) == want
+    res = {}
+
+    def worker():
+        o = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        res["code"] = gmq.tree_sum_noalloc(v, o, stream=side)
+        side.synchronize()
+        res["sum"] = float(o.item())
+
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert res["code"] == gmq.OK and res["sum"] == want
+
+
+def test_noalloc_sum_rejects_host_memory(gpu_ctx):
+    """Pointers that are not device memory of the given device are refused
+    before anything is enqueued (a pinned host result buffer here)."""
+    import ctypes
+    from paper_2511_01573_gb300 import gmq
+    v = torch.ones(1000, dtype=torch.float64, device="cuda")
+    host = torch.full((1,), 5.0, dtype=torch.float64).pin_memory()
+    code = gmq.lib().gmq_tree_sum_noalloc(0, v.numel(), ctypes.c_void_p(v.data_ptr()),
+                                          ctypes.c_void_p(host.data_ptr()), None)
+    assert code == gmq.ERR_INVALID and float(host[0]) == 5.0
