@@ -288,6 +288,120 @@ void or_rule_regions(const or_family *fam, int64_t n, const double *c,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Null-rule error estimate (paper Sec. 2 cites Berntsen, Espelid & Genz     */
+/* 1991 without printing it; this is the project's reading of it).          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Four fully symmetric null rules on the rule's own nodes (weights per node
+ * class in null_w, from oracle/null_rules.py): N1 of degree 5, N2 and N3 of
+ * degree 3, N4 of degree 1, mutually orthogonal, each with the norm of the
+ * degree-7 rule's weights.  Their values N_k = vol sum_c null_w[k][c] S_c
+ * are combined per degree, e1 = |N1|, e2 = sqrt(N2^2 + N3^2) (the part of
+ * f's values seen by the degree-3 null space beyond N1, independent of how
+ * that space's basis is chosen), e3 = |N4|.  While f is resolved, each
+ * step down in degree multiplies the null values by a factor well below 1;
+ * r = max(e1 / e2, e2 / e3) measures it (x / 0 = infinity for x > 0, 0 / 0
+ * = 0).  With K = 10:
+ *   r >= 1  (not yet asymptotic):  est = K max(e1, e2, e3)
+ *   r < 1   (asymptotic):          est = K r e1
+ * The top null rule (degree 5) is one degree step (x h^2) below the basic
+ * rule (degree 7), so the asymptotic estimate extrapolates e1 by exactly
+ * one observed decay factor.  (The heuristic's strongly asymptotic branch,
+ * K r^2 e1 / r_c below r_c = 1/2, was tried and dropped: on 168 seeded Genz
+ * problems it missed the requested tolerance 27 times, against 9 for the
+ * form above and 7 for the embedded estimate.)  The estimate jumps at
+ * r = 1; est_alt is the value on the other side of that boundary (K e1
+ * below it, K max(e) above).  noise is a bound on how far two correct FP64
+ * implementations' e_k may lie apart (class sums added in different orders:
+ * 1e-12 of the weighted magnitude of the class sums), band the resulting
+ * bound on est (the estimate's slope in the e_k is at most 30, so 50
+ * noise), and regime_tie says whether the e_k's noise reaches across r = 1.
+ */
+static const double kBegK = 10.0;
+
+static double beg_ratio(double x, double y) {
+  if (y > 0.0) return x / y;
+  return x > 0.0 ? INFINITY : 0.0;
+}
+
+static double beg_combine(const double e[3], double r) {
+  if (r >= 1.0) return kBegK * fmax(e[0], fmax(e[1], e[2]));
+  return kBegK * r * e[0];
+}
+
+void or_null_estimate(const or_rule_out *rule, const double *null_w, or_null_out *out) {
+  int k, c;
+  double mag = 0.0, dn, lo[3], hi[3], r_lo, r_hi;
+  for (k = 0; k < 4; ++k) {
+    double t = 0.0;
+    for (c = 0; c < 5; ++c) t = t + null_w[k * 5 + c] * rule->s[c];
+    out->nul[k] = rule->vol * t;
+  }
+  out->e[0] = fabs(out->nul[0]);
+  out->e[1] = sqrt(out->nul[1] * out->nul[1] + out->nul[2] * out->nul[2]);
+  out->e[2] = fabs(out->nul[3]);
+  out->r = fmax(beg_ratio(out->e[0], out->e[1]), beg_ratio(out->e[1], out->e[2]));
+  out->est = beg_combine(out->e, out->r);
+  out->regime = out->r >= 1.0 ? 0 : 1;
+  out->est_alt = out->regime == 0 ? kBegK * out->e[0]
+                                  : kBegK * fmax(out->e[0], fmax(out->e[1], out->e[2]));
+  for (c = 0; c < 5; ++c) {
+    double m = 0.0;
+    for (k = 0; k < 4; ++k) m = fmax(m, fabs(null_w[k * 5 + c]));
+    mag = mag + m * rule->sabs[c];
+  }
+  out->noise = 1e-12 * rule->vol * mag;
+  out->band = 50.0 * out->noise;
+  dn = 1.5 * out->noise; /* e2 combines two null values */
+  for (k = 0; k < 3; ++k) {
+    lo[k] = fmax(out->e[k] - dn, 0.0);
+    hi[k] = out->e[k] + dn;
+  }
+  r_lo = fmax(beg_ratio(lo[0], hi[1]), beg_ratio(lo[1], hi[2]));
+  r_hi = fmax(beg_ratio(hi[0], lo[1]), beg_ratio(hi[1], lo[2]));
+  out->regime_tie = (r_lo < 1.0) && (r_hi >= 1.0);
+}
+
+void or_rule_regions_est(const or_family *fam, int64_t n, const double *c,
+                         const double *h, const double *null_w, double *i7,
+                         double *err, double *vol, int32_t *axis,
+                         int32_t *axis_tie, int32_t *split_bad, double *scale,
+                         double *err_band, double *err_alt) {
+  int64_t r;
+  int d = fam->d;
+  double w7[5], w5[5];
+  or_weights(d, w7, w5);
+  for (r = 0; r < n; ++r) {
+    or_rule_out o;
+    double e = 0.0, band = 0.0, alt = 0.0;
+    or_rule(d, c + r * d, h + r * d, or_family_eval, fam, NULL, &o);
+    if (null_w) {
+      or_null_out q;
+      or_null_estimate(&o, null_w, &q);
+      e = q.est;
+      alt = q.regime_tie ? q.est_alt : q.est;
+      band = q.band + (q.regime_tie ? fabs(q.est - q.est_alt) : 0.0);
+    } else {
+      e = o.err;
+      alt = o.err;
+    }
+    if (i7) i7[r] = o.i7;
+    if (err) err[r] = e;
+    if (vol) vol[r] = o.vol;
+    if (axis) axis[r] = o.axis;
+    if (axis_tie) axis_tie[r] = o.axis_tie;
+    if (split_bad) split_bad[r] = o.split_bad;
+    if (scale)
+      scale[r] = o.vol * (fabs(w7[0]) * o.sabs[0] + fabs(w7[1]) * o.sabs[1] +
+                          fabs(w7[2]) * o.sabs[2] + fabs(w7[3]) * o.sabs[3] +
+                          fabs(w7[4]) * o.sabs[4]);
+    if (err_band) err_band[r] = band;
+    if (err_alt) err_alt[r] = alt;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Tensor-product Gauss-Kronrod (7, 15) rule (paper Sec. 3).                */
 /* ------------------------------------------------------------------------ */
 
@@ -473,11 +587,12 @@ int64_t or_partition(int d, const double *lo, const double *hi, int32_t s,
  * over the class, or |I7_r| when no scale is given): these are the
  * decisions two correct FP64 implementations may take differently.
  */
-int64_t or_classify(int d, int64_t n, const double *i7, const double *err,
-                    const double *vol, const int32_t *split_bad,
-                    const double *scale, double vol_omega, double budget,
-                    double rel_tol, int32_t classifier, uint8_t *flags,
-                    double *ret_i, double *ret_e, int64_t *near_ties) {
+int64_t or_classify_band(int d, int64_t n, const double *i7, const double *err,
+                         const double *vol, const int32_t *split_bad,
+                         const double *scale, const double *err_band,
+                         double vol_omega, double budget, double rel_tol,
+                         int32_t classifier, uint8_t *flags, double *ret_i,
+                         double *ret_e, int64_t *near_ties) {
   const double u = ldexp(1.0, -53);
   double *vi = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double *ve = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -492,7 +607,10 @@ int64_t or_classify(int d, int64_t n, const double *i7, const double *err,
       thr = budget * (vol[r] / vol_omega);
     g = 50.0 * u * fabs(i7[r]);
     retire = (err[r] <= thr) || (err[r] <= g) || split_bad[r];
-    b = 1e-13 * (scale ? scale[r] : fabs(i7[r])) + 1e-12 * err[r];
+    if (err_band)
+      b = err_band[r] + 1e-12 * err[r];
+    else
+      b = 1e-13 * (scale ? scale[r] : fabs(i7[r])) + 1e-12 * err[r];
     bt = 1e-12 * thr;
     loose = (err[r] - b <= thr + bt) || (err[r] - b <= g) || split_bad[r];
     tight = (err[r] + b <= thr - bt) || (err[r] + b <= g) || split_bad[r];
@@ -508,6 +626,16 @@ int64_t or_classify(int d, int64_t n, const double *i7, const double *err,
   free(vi);
   free(ve);
   return nsplit;
+}
+
+int64_t or_classify(int d, int64_t n, const double *i7, const double *err,
+                    const double *vol, const int32_t *split_bad,
+                    const double *scale, double vol_omega, double budget,
+                    double rel_tol, int32_t classifier, uint8_t *flags,
+                    double *ret_i, double *ret_e, int64_t *near_ties) {
+  return or_classify_band(d, n, i7, err, vol, split_bad, scale, NULL, vol_omega,
+                          budget, rel_tol, classifier, flags, ret_i, ret_e,
+                          near_ties);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -583,8 +711,9 @@ static int32_t integrate_impl(const or_family *fam, const double *lo,
   int32_t s, iters = 0, max_iters = opt->max_iters > 0 ? opt->max_iters : 1000;
   int64_t n, r, ties_total = 0;
   double vol_omega = 1.0, I_ret = 0.0, E_ret = 0.0;
-  double *c, *h, *c2, *h2, *i7, *err, *vol, *scl;
+  double *c, *h, *c2, *h2, *i7, *err, *vol, *scl, *eband;
   int32_t *axis, *bad, *atie;
+  const int null_est = opt->estimator == 1;
   uint8_t *flags;
   int32_t status = 0;
   int k;
@@ -595,7 +724,9 @@ static int32_t integrate_impl(const or_family *fam, const double *lo,
   memset(res, 0, sizeof(*res));
   if (d < 1 || d > 20 || cap < 1 || !(opt->rel_tol >= 0.0) ||
       !(opt->abs_tol >= 0.0) || (opt->rule != 0 && opt->rule != 1) ||
-      (opt->rule == 1 && (!opt->gk || d > 6))) {
+      (opt->rule == 1 && (!opt->gk || d > 6)) ||
+      (opt->estimator != 0 && opt->estimator != 1) ||
+      (opt->estimator == 1 && (opt->rule != 0 || !opt->null_w))) {
     res->status = -1;
     return -1;
   }
@@ -622,12 +753,13 @@ static int32_t integrate_impl(const or_family *fam, const double *lo,
   err = (double *)malloc(sizeof(double) * (size_t)cap);
   vol = (double *)malloc(sizeof(double) * (size_t)cap);
   scl = (double *)malloc(sizeof(double) * (size_t)cap);
+  eband = (double *)malloc(sizeof(double) * (size_t)cap);
   axis = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
   bad = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
   atie = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
   flags = (uint8_t *)malloc((size_t)cap);
-  if (!c || !h || !c2 || !h2 || !i7 || !err || !vol || !scl || !axis || !bad ||
-      !atie || !flags) {
+  if (!c || !h || !c2 || !h2 || !i7 || !err || !vol || !scl || !eband || !axis ||
+      !bad || !atie || !flags) {
     status = -2;
     goto done;
   }
@@ -642,7 +774,8 @@ static int32_t integrate_impl(const or_family *fam, const double *lo,
       or_rule_gk_regions(fam, n, c, h, opt->gk, i7, NULL, err, vol, axis, atie, bad, scl);
       res->function_evals += n * or_gk_nodes(d);
     } else {
-      or_rule_regions(fam, n, c, h, i7, NULL, err, vol, axis, atie, bad, scl);
+      or_rule_regions_est(fam, n, c, h, null_est ? opt->null_w : NULL, i7, err, vol,
+                          axis, atie, bad, scl, eband, NULL);
       res->function_evals += n * or_num_nodes(d);
     }
     res->regions_evaluated += n;
@@ -678,9 +811,9 @@ static int32_t integrate_impl(const or_family *fam, const double *lo,
       break;
     }
     /* classify, retire, count */
-    nsplit = or_classify(d, n, i7, err, vol, bad, scl, vol_omega, budget,
-                         opt->rel_tol, opt->classifier, flags, &ret_i, &ret_e,
-                         &ties);
+    nsplit = or_classify_band(d, n, i7, err, vol, bad, scl, null_est ? eband : NULL,
+                              vol_omega, budget, opt->rel_tol, opt->classifier,
+                              flags, &ret_i, &ret_e, &ties);
     for (r = 0; r < n; ++r)
       if (flags[r] && atie[r]) ties++;
     ties_total += ties;
@@ -729,6 +862,7 @@ done:
   free(err);
   free(vol);
   free(scl);
+  free(eband);
   free(axis);
   free(bad);
   free(atie);

@@ -62,6 +62,8 @@ typedef struct {
   int32_t classifier;  /* 0 = volume share, 1 = local relative */
   int32_t rule;        /* 0 = Genz-Malik, 1 = tensor-product Gauss-Kronrod */
   const double *gk;    /* rule 1: the 45-double table of or_rule_gk        */
+  int32_t estimator;   /* 0 = |I7 - I5|, 1 = null rules (Genz-Malik only)  */
+  const double *null_w; /* estimator 1: the 4 x 5 table of or_null_estimate */
 } or_options;
 
 /* Result of the tensor-product Gauss-Kronrod rule on one region. */
@@ -105,6 +107,35 @@ void or_rule_regions(const or_family *fam, int64_t n, const double *c,
                      double *vol, int32_t *axis, int32_t *axis_tie,
                      int32_t *split_bad, double *i7abs);
 
+/* Null-rule error estimate (Berntsen, Espelid & Genz 1991, the heuristic
+ * the paper's Sec. 2 cites; its form here is a reading, see gm_oracle.c).
+ * null_w: 4 x 5 per-node weights of the null rules N1..N4 per node class
+ * (unit volume, row-major; oracle/null_rules.py); rule: the region's rule
+ * output (class sums, class magnitude sums, volume). */
+typedef struct {
+  double nul[4];    /* N_k = vol * sum_c null_w[k][c] S_c                     */
+  double e[3];      /* |N1|, sqrt(N2^2 + N3^2), |N4|                          */
+  double r;         /* max(e1 / e2, e2 / e3): decay per degree step          */
+  double est;       /* the error estimate                                     */
+  double est_alt;   /* the estimate on the other side of the r = 1 boundary  */
+  double noise;     /* rounding band of each e_k: 1e-12 vol sum_c max_k |null_w[k][c]| A_c */
+  double band;      /* rounding band of est (50 noise)                        */
+  int32_t regime;   /* 0: r >= 1 (not asymptotic), 1: r < 1 (asymptotic)     */
+  int32_t regime_tie; /* the e_k's rounding band reaches across r = 1        */
+} or_null_out;
+
+void or_null_estimate(const or_rule_out *rule, const double *null_w, or_null_out *out);
+
+/* The rule over n regions with the chosen estimator (null_w == NULL: the
+ * embedded |I7 - I5|, else the null-rule estimate), as the loop uses it.
+ * err_band (may be NULL) receives each error value's rounding band: the
+ * half-width within which two correct FP64 implementations may differ. */
+void or_rule_regions_est(const or_family *fam, int64_t n, const double *c,
+                         const double *h, const double *null_w, double *i7,
+                         double *err, double *vol, int32_t *axis,
+                         int32_t *axis_tie, int32_t *split_bad, double *scale,
+                         double *err_band, double *err_alt);
+
 /* Pairwise (binary tree over a zero-padded power of two) sum. */
 /* Tensor-product Gauss-Kronrod (7, 15) rule on one region (the paper's
  * Sec. 3 names the rule, not its order or its split axis; these are
@@ -135,12 +166,19 @@ int64_t or_partition(int d, const double *lo, const double *hi, int32_t s,
 /* Classification of one sweep.  flags[r] = 1 split, 0 retire.  Returns the
  * number of split regions; retired sums and near-tie count via pointers.
  * scale (may be NULL) is the per-region magnitude used for the near-tie
- * band. */
+ * band; err_band (may be NULL) replaces its 1e-13 scale term by the given
+ * per-region band of err. */
 int64_t or_classify(int d, int64_t n, const double *i7, const double *err,
                     const double *vol, const int32_t *split_bad,
                     const double *scale, double vol_omega, double budget,
                     double rel_tol, int32_t classifier, uint8_t *flags,
                     double *ret_i, double *ret_e, int64_t *near_ties);
+int64_t or_classify_band(int d, int64_t n, const double *i7, const double *err,
+                         const double *vol, const int32_t *split_bad,
+                         const double *scale, const double *err_band,
+                         double vol_omega, double budget, double rel_tol,
+                         int32_t classifier, uint8_t *flags, double *ret_i,
+                         double *ret_e, int64_t *near_ties);
 
 /* Bisection + compaction: left children of split regions in input order at
  * [0, n_split), right children at [n_split, 2 n_split). */

@@ -38,7 +38,13 @@ class RuleOut(C.Structure):
 class Options(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_regions", C.c_int64),
                 ("init_splits", C.c_int32), ("max_iters", C.c_int32), ("classifier", C.c_int32),
-                ("rule", C.c_int32), ("gk", _dp)]
+                ("rule", C.c_int32), ("gk", _dp), ("estimator", C.c_int32), ("null_w", _dp)]
+
+
+class NullOut(C.Structure):
+    _fields_ = [("nul", C.c_double * 4), ("e", C.c_double * 3), ("r", C.c_double),
+                ("est", C.c_double), ("est_alt", C.c_double), ("noise", C.c_double),
+                ("band", C.c_double), ("regime", C.c_int32), ("regime_tie", C.c_int32)]
 
 
 class GkOut(C.Structure):
@@ -49,7 +55,19 @@ class GkOut(C.Structure):
 
 RULE_GM = 0
 RULE_GK = 1
+EST_EMBEDDED = 0
+EST_NULL_RULES = 1
 _GK = None
+_NULL = {}
+
+
+def null_table(d: int):
+    """The 4 x 5 null-rule weight table for dimension d (oracle/null_rules.py,
+    exact rational arithmetic, rounded once)."""
+    if d not in _NULL:
+        from oracle.null_rules import null_table as nt
+        _NULL[d] = np.ascontiguousarray(np.array(nt(d), dtype=np.float64))
+    return _NULL[d]
 
 
 def gk_table():
@@ -63,11 +81,14 @@ def gk_table():
     return _GK
 
 
-def _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, rule):
+def _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, rule,
+             estimator=EST_EMBEDDED, d=None):
     gk = gk_table() if rule == RULE_GK else None
+    nw = null_table(d) if estimator == EST_NULL_RULES else None
     o = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, rule,
-                _p(gk) if gk is not None else None)
-    o._keep = gk
+                _p(gk) if gk is not None else None, estimator,
+                _p(nw) if nw is not None else None)
+    o._keep = (gk, nw)
     return o
 
 
@@ -131,6 +152,13 @@ def lib():
                                  C.POINTER(GkOut)]
         L.or_rule_gk_regions.argtypes = [C.POINTER(Family), C.c_int64, _dp, _dp, _dp, _dp, _dp,
                                          _dp, _dp, _i32p, _i32p, _i32p, _dp]
+        L.or_null_estimate.argtypes = [C.POINTER(RuleOut), _dp, C.POINTER(NullOut)]
+        L.or_rule_regions_est.argtypes = [C.POINTER(Family), C.c_int64, _dp, _dp, _dp, _dp, _dp,
+                                          _dp, _i32p, _i32p, _i32p, _dp, _dp, _dp]
+        L.or_classify_band.restype = C.c_int64
+        L.or_classify_band.argtypes = [C.c_int, C.c_int64, _dp, _dp, _dp, _i32p, _dp, _dp,
+                                       C.c_double, C.c_double, C.c_double, C.c_int32, _u8p, _dp,
+                                       _dp, C.POINTER(C.c_int64)]
         L.or_integrate.restype = C.c_int32
         L.or_integrate.argtypes = [C.POINTER(Family), _dp, _dp, C.POINTER(Options),
                                    C.POINTER(Result), C.POINTER(Trace), C.c_int32]
@@ -212,8 +240,40 @@ def rule(c, h, f=None, family=None, a=None, u=None) -> Rule:
         fn = C.cast(lib().or_family_eval, C.c_void_p)
         lib().or_rule(d, _p(c), _p(h), fn, C.cast(C.pointer(fh.s), C.c_void_p), _p(D),
                       C.byref(out))
-    return Rule(out.i7, out.i5, out.err, np.array(out.s[:]), np.array(out.sabs[:]), out.vol,
-                out.f0, out.axis, bool(out.axis_tie), bool(out.flat), bool(out.split_bad), D)
+    r = Rule(out.i7, out.i5, out.err, np.array(out.s[:]), np.array(out.sabs[:]), out.vol,
+             out.f0, out.axis, bool(out.axis_tie), bool(out.flat), bool(out.split_bad), D)
+    r._raw = out
+    return r
+
+
+def null_estimate(rule_result: Rule, d: int):
+    """The null-rule estimate of one region from its rule result (or_rule's
+    class sums and magnitudes).  Returns a dict of the NullOut fields."""
+    q = NullOut()
+    lib().or_null_estimate(C.byref(rule_result._raw), _p(null_table(d)), C.byref(q))
+    return {"nul": np.array(q.nul[:]), "e": np.array(q.e[:]), "r": q.r, "est": q.est,
+            "est_alt": q.est_alt, "noise": q.noise, "band": q.band, "regime": q.regime,
+            "regime_tie": bool(q.regime_tie)}
+
+
+def rule_regions_est(family: int, a, u, c, h, estimator=EST_NULL_RULES):
+    """Rule over n regions with the chosen error estimator, as the loop uses
+    it: dict of i7, err, vol, scale, err_band, err_alt, axis, axis_tie,
+    split_bad."""
+    c = _f64(c)
+    h = _f64(h)
+    n, d = c.shape
+    fh = _FamilyHandle(family, a, u)
+    out = {k: np.zeros(n) for k in ("i7", "err", "vol", "scale", "err_band", "err_alt")}
+    ints = {k: np.zeros(n, dtype=np.int32) for k in ("axis", "axis_tie", "split_bad")}
+    nw = null_table(d) if estimator == EST_NULL_RULES else None
+    lib().or_rule_regions_est(C.byref(fh.s), n, _p(c), _p(h), None if nw is None else _p(nw),
+                              _p(out["i7"]), _p(out["err"]), _p(out["vol"]),
+                              _p(ints["axis"], C.c_int32), _p(ints["axis_tie"], C.c_int32),
+                              _p(ints["split_bad"], C.c_int32), _p(out["scale"]),
+                              _p(out["err_band"]), _p(out["err_alt"]))
+    out.update(ints)
+    return out
 
 
 def rule_regions(family: int, a, u, c, h):
@@ -299,18 +359,20 @@ def partition(lo, hi, s: int):
     return c, h
 
 
-def classify(i7, err, vol, split_bad, vol_omega, budget, rel_tol=0.0, classifier=0, scale=None):
+def classify(i7, err, vol, split_bad, vol_omega, budget, rel_tol=0.0, classifier=0, scale=None,
+             err_band=None):
     i7, err, vol = _f64(i7), _f64(err), _f64(vol)
     sc = None if scale is None else _f64(scale)
+    eb = None if err_band is None else _f64(err_band)
     sb = np.ascontiguousarray(np.asarray(split_bad, dtype=np.int32))
     n = len(i7)
     flags = np.zeros(n, dtype=np.uint8)
     ri, re_ = C.c_double(), C.c_double()
     ties = C.c_int64()
-    ns = lib().or_classify(0, n, _p(i7), _p(err), _p(vol), _p(sb, C.c_int32),
-                           None if sc is None else _p(sc), vol_omega, budget,
-                           rel_tol, classifier, _p(flags, C.c_uint8), C.byref(ri), C.byref(re_),
-                           C.byref(ties))
+    ns = lib().or_classify_band(0, n, _p(i7), _p(err), _p(vol), _p(sb, C.c_int32),
+                                None if sc is None else _p(sc), None if eb is None else _p(eb),
+                                vol_omega, budget, rel_tol, classifier, _p(flags, C.c_uint8),
+                                C.byref(ri), C.byref(re_), C.byref(ties))
     return dict(flags=flags, n_split=int(ns), ret_i=ri.value, ret_e=re_.value,
                 near_ties=int(ties.value))
 
@@ -342,12 +404,14 @@ class IntegrateResult:
 
 def integrate(family: int, a, u, rel_tol: float, lo=None, hi=None, abs_tol: float = 1e-16,
               max_regions: int = 100000, init_splits: int = 0, max_iters: int = 0,
-              classifier: int = 0, max_trace: int = 256, rule: int = RULE_GM) -> IntegrateResult:
+              classifier: int = 0, max_trace: int = 256, rule: int = RULE_GM,
+              estimator: int = EST_EMBEDDED) -> IntegrateResult:
     fh = _FamilyHandle(family, a, u)
     d = len(fh.a)
     lo = _f64(np.zeros(d) if lo is None else lo)
     hi = _f64(np.ones(d) if hi is None else hi)
-    opt = _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, rule)
+    opt = _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, rule,
+                   estimator, d)
     res = Result()
     tr = (Trace * max_trace)()
     lib().or_integrate(C.byref(fh.s), _p(lo), _p(hi), C.byref(opt), C.byref(res), tr, max_trace)
@@ -382,7 +446,8 @@ def rule_grad(family: int, a, u, c, h):
 
 def integrate_partition(family: int, a, u, rel_tol: float, lo=None, hi=None,
                         abs_tol: float = 1e-16, max_regions: int = 100000, max_leaves=None,
-                        init_splits: int = 0, max_iters: int = 0, classifier: int = 0):
+                        init_splits: int = 0, max_iters: int = 0, classifier: int = 0,
+                        estimator: int = EST_EMBEDDED):
     """or_integrate plus the final partition (leaves as n x d arrays)."""
     fh = _FamilyHandle(family, a, u)
     d = len(fh.a)
@@ -392,7 +457,8 @@ def integrate_partition(family: int, a, u, rel_tol: float, lo=None, hi=None,
     co = np.zeros((ml, d))
     ho = np.zeros((ml, d))
     nl = C.c_int64()
-    opt = _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, RULE_GM)
+    opt = _options(rel_tol, abs_tol, max_regions, init_splits, max_iters, classifier, RULE_GM,
+                   estimator, d)
     res = Result()
     _lib_grad().or_integrate_partition(C.byref(fh.s), _p(lo), _p(hi), C.byref(opt), C.byref(res),
                                        _p(co), _p(ho), ml, C.byref(nl))
