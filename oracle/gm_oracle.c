@@ -312,11 +312,14 @@ void or_rule_regions(const or_family *fam, int64_t n, const double *c,
  * problems it missed the requested tolerance 27 times, against 9 for the
  * form above and 7 for the embedded estimate.)  The estimate jumps at
  * r = 1; est_alt is the value on the other side of that boundary (K e1
- * below it, K max(e) above).  noise is a bound on how far two correct FP64
- * implementations' e_k may lie apart (class sums added in different orders:
- * 1e-12 of the weighted magnitude of the class sums), band the resulting
- * bound on est (the estimate's slope in the e_k is at most 30, so 50
- * noise), and regime_tie says whether the e_k's noise reaches across r = 1.
+ * below it, K max(e) above).  noise bounds how far two correct FP64
+ * implementations' null values may lie apart (class sums added in
+ * different orders: 1e-13 of the weighted magnitude of the class sums, the
+ * band the embedded estimate's near-tie flag uses too); band bounds the
+ * resulting spread of est: with every e_k moved by up to 1.5 noise (e2
+ * combines two null values), est = K r e1 stays within [K r_lo e1_lo,
+ * K r_hi e1_hi] (it grows with r and e1) and K max(e) within K max(e) +- 1.5
+ * K noise; regime_tie says whether that spread of r reaches across r = 1.
  */
 static const double kBegK = 10.0;
 
@@ -351,9 +354,8 @@ void or_null_estimate(const or_rule_out *rule, const double *null_w, or_null_out
     for (k = 0; k < 4; ++k) m = fmax(m, fabs(null_w[k * 5 + c]));
     mag = mag + m * rule->sabs[c];
   }
-  out->noise = 1e-12 * rule->vol * mag;
-  out->band = 50.0 * out->noise;
-  dn = 1.5 * out->noise; /* e2 combines two null values */
+  out->noise = 1e-13 * rule->vol * mag;
+  dn = 1.5 * out->noise;
   for (k = 0; k < 3; ++k) {
     lo[k] = fmax(out->e[k] - dn, 0.0);
     hi[k] = out->e[k] + dn;
@@ -361,6 +363,11 @@ void or_null_estimate(const or_rule_out *rule, const double *null_w, or_null_out
   r_lo = fmax(beg_ratio(lo[0], hi[1]), beg_ratio(lo[1], hi[2]));
   r_hi = fmax(beg_ratio(hi[0], lo[1]), beg_ratio(hi[1], lo[2]));
   out->regime_tie = (r_lo < 1.0) && (r_hi >= 1.0);
+  if (out->regime == 0)
+    out->band = kBegK * dn;
+  else
+    out->band = fmax(kBegK * fmin(r_hi, 1.0) * hi[0] - out->est,
+                     out->est - kBegK * r_lo * lo[0]);
 }
 
 void or_rule_regions_est(const or_family *fam, int64_t n, const double *c,

@@ -118,8 +118,8 @@ typedef struct {
   double r;         /* max(e1 / e2, e2 / e3): decay per degree step          */
   double est;       /* the error estimate                                     */
   double est_alt;   /* the estimate on the other side of the r = 1 boundary  */
-  double noise;     /* rounding band of each e_k: 1e-12 vol sum_c max_k |null_w[k][c]| A_c */
-  double band;      /* rounding band of est (50 noise)                        */
+  double noise;     /* rounding band of the null values: 1e-13 vol sum_c max_k |null_w[k][c]| A_c */
+  double band;      /* resulting rounding band of est (interval bound)       */
   int32_t regime;   /* 0: r >= 1 (not asymptotic), 1: r < 1 (asymptotic)     */
   int32_t regime_tie; /* the e_k's rounding band reaches across r = 1        */
 } or_null_out;
