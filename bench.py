@@ -57,6 +57,12 @@ def parse():
                     help="with --probe-batch: the host-driven sweep loop instead of the graph")
     ap.add_argument("--kernel-sweep", action="store_true",
                     help="isolated rule / classify / split rates against the region count")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="the measured FP64 and FP32 issue rates (fused multiply-add, add, "
+                         "multiply chains) with the SM clocks sampled meanwhile")
+    ap.add_argument("--estimators", action="store_true",
+                    help="the d=8 workload with the embedded and the null-rule error estimate: "
+                         "time, regions and true error against the closed forms per tolerance")
     ap.add_argument("--all-configs", action="store_true",
                     help="report the other workloads (d=3, d=12 mixed, batch, gradients)")
     ap.add_argument("--seeds-d12", type=int, default=3)
@@ -90,7 +96,7 @@ RULE_FP64_INST_D8 = {0: 9006.0, 1: 11813.0, 2: 7803.0, 3: 14219.0, 4: 11011.0}
 RULE_FP64_FLOPS_D8 = {0: 15866.0, 1: 16668.0, 2: 12658.0, 3: 20277.0, 4: 17069.0}
 RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
                        "gm_math_tables.cuh", "gmq_common.cuh")
-RULE_COUNTS_SHA16 = "4c0281fcc3e7753d"
+RULE_COUNTS_SHA16 = "1eb3d21db416b97a"
 
 
 def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
@@ -588,6 +594,20 @@ def _closed(fam, a, u):
         for ai in a:
             z *= (cmath.exp(1j * ai) - 1.0) / (1j * ai)
         return z.real
+    if fam == G.CORNER_PEAK:
+        # (1 / (d! prod a)) sum_{S} (-1)^|S| / (1 + sum_{j in S} a_j), in exact
+        # rational arithmetic (the alternating sum cancels badly in FP64)
+        from fractions import Fraction
+        from itertools import combinations
+        fa = [Fraction(x) for x in a]
+        tot = Fraction(0)
+        for k in range(len(fa) + 1):
+            for S in combinations(fa, k):
+                tot += Fraction((-1) ** k) / (1 + sum(S, Fraction(0)))
+        den = Fraction(math.factorial(len(fa)))
+        for x in fa:
+            den *= x
+        return float(tot / den)
     raise ValueError(fam)
 
 
@@ -713,8 +733,86 @@ def all_configs(args):
     ctx.close()
 
 
+def probe_peaks(args):
+    """The issue-rate probe (gmq_probe_fp_rate) for FP64 and FP32, each of
+    fused multiply-add, add and multiply chains, after a warm-up launch;
+    prints one JSON object with lane operations per second, lanes per clock
+    per SM at the sampled median SM clock, and the clocks."""
+    import torch
+    from paper_2511_01573_gb300 import gmq
+    ctx = gmq.Context(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {}
+    with ClockSampler(0) as clk:
+        for prec, name in ((gmq.FP64, "fp64"), (gmq.MIXED, "fp32")):
+            ctx.probe_fp_rate(prec, iters=2000 if prec == gmq.FP64 else 100000)
+            for op in ctx.PROBE_OPS:
+                rate, ms = max(ctx.probe_fp_rate(prec, op) for _ in range(3))
+                out[f"{name}_{op}"] = {"G_lane_ops_per_s": rate / 1e9, "ms": ms}
+    c = clk.summary()
+    mhz = c.get("sm_mhz") or 2070.0
+    for v in out.values():
+        v["lanes_per_clk_per_sm"] = v["G_lane_ops_per_s"] * 1e9 / (sms * mhz * 1e6)
+    print(json.dumps({"probe_peaks": out, "sms": sms, "clocks": c}), flush=True)
+    ctx.close()
+
+
+def estimators(args):
+    """The d = 8 workload (40 problems per tolerance, 1e-3 .. 1e-8) with the
+    embedded error estimate |I7 - I5| and with the null-rule estimate: GPU
+    time (CUDA events), regions, convergence, and the true relative error
+    against the closed forms (the largest, the median, and how many runs
+    stay within their tolerance).  Prints one JSON object."""
+    import statistics
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    stream = torch.cuda.Stream(device=0)
+    ctx = gmq.Context(0, stream=stream)
+    exact = {}
+    rows = []
+    for tol in (1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
+        probs = G.genz_d8_problems(tols=(tol,))
+        for p in probs:
+            key = (p.family, tuple(p.a), tuple(p.u))
+            if key not in exact:
+                exact[key] = _closed(p.family, p.a, p.u)
+        for name, est in (("embedded", gmq.EST_EMBEDDED), ("null_rules", gmq.EST_NULL_RULES)):
+            for p in probs[:4]:
+                ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=CAP, estimator=est)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = [ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=CAP, estimator=est)
+                   for p in probs]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rel = [abs(r.integral - exact[(p.family, tuple(p.a), tuple(p.u))]) /
+                   abs(exact[(p.family, tuple(p.a), tuple(p.u))]) for p, r in zip(probs, res)]
+            by_fam = {}
+            for p, r, e in zip(probs, res, rel):
+                f = by_fam.setdefault(G.FAMILY_NAMES[p.family], {"regions": 0, "max_err_over_tol": 0.0})
+                f["regions"] += r.regions_evaluated
+                f["max_err_over_tol"] = max(f["max_err_over_tol"], e / tol)
+            rows.append({"tol": tol, "estimator": name, "s": e0.elapsed_time(e1) / 1000.0,
+                         "regions": sum(r.regions_evaluated for r in res),
+                         "converged": sum(1 for r in res if r.status == 0),
+                         "within_tol": sum(1 for e in rel if e <= tol),
+                         "max_err_over_tol": max(rel) / tol,
+                         "median_err_over_tol": statistics.median(rel) / tol,
+                         "by_family": by_fam})
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"estimators_d8": rows}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.probe_peaks:
+        return probe_peaks(args)
+    if args.estimators:
+        return estimators(args)
     if args.all_configs:
         return all_configs(args)
     if args.probe_rule:
@@ -790,12 +888,15 @@ def main():
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read()
     timed_fam_regions = dict(fam_regions)
-    # measured FP64 FMA issue rate of this GPU (the roofline's peak): the
-    # probe kernel after a warm-up launch, clocks sampled meanwhile
+    # measured FP64 issue rate of this GPU (the roofline's peak): the probe
+    # kernel's fused multiply-add, add and multiply chains after a warm-up
+    # launch, clocks sampled meanwhile; the pipe's peak is the fastest
     with ClockSampler(dev) as pclk:
-        ctx.probe_fma_rate(gmq.FP64, iters=2000)
-        probe64 = max(ctx.probe_fma_rate(gmq.FP64)[0] for _ in range(3))
+        ctx.probe_fp_rate(gmq.FP64, iters=2000)
+        probe_ops = {op: max(ctx.probe_fp_rate(gmq.FP64, op)[0] for _ in range(2))
+                     for op in ctx.PROBE_OPS}
     probe_clocks = pclk.summary()
+    probe64 = max(probe_ops.values())
     # e2e: host wall clock through the public call (one step), with the
     # per-launch timing events off; its device time (events around the whole
     # step) against the timed steps' shows what those events cost
@@ -844,15 +945,16 @@ def main():
                 "traffic": (RULE_DRAM_BYTES_PER_REGION_D8 * rule["regions"] / n_launch
                             if counts_current else None),
                 "kernel": "k_rule64 (FP64 rule evaluation)",
-                "peak_basis": ("measured: FP64 FMA probe (gmq_probe_fma_rate, 64 warps/SM, "
-                               "16 independent chains per thread) in this run, median "
-                               f"{probe_clocks.get('sm_mhz')} MHz"),
+                "peak_basis": ("measured: fastest FP64 chain of the issue-rate probe "
+                               "(gmq_probe_fp_rate, 64 warps/SM, 16 independent chains per "
+                               f"thread) in this run, median {probe_clocks.get('sm_mhz')} MHz"),
+                "probe_G_lane_ops_per_s": {k: v / 1e9 for k, v in probe_ops.items()},
                 "nominal": {"peak": peak_nominal, "frac": ach / peak_nominal,
                             "basis": (f"2 FP64 lanes/clk/SM (1.25 TFLOP/s nominal) x 152 SMs "
                                       f"x median {mhz:.0f} MHz")},
                 "counts_match_source": counts_current,
                 "flops_view": {"achieved_gflops": flops / avg_s / 1e9,
-                               "peak_gflops_measured": 2 * peak},
+                               "peak_gflops_measured_fma": 2 * probe_ops["fma"] / 1e9},
                 "inst_per_region": {G.FAMILY_NAMES[f]: RULE_FP64_INST_D8[f]
                                     for f in sorted(timed_fam_regions)},
                 "regions_by_family": {G.FAMILY_NAMES[f]: n // args.steps

@@ -100,6 +100,24 @@ typedef enum gmq_rule {
 
 #define GMQ_GK_MAX_DIM 6
 
+/* Local error estimate of the Genz-Malik rule (paper Sec. 2 names the
+ * heuristic of Berntsen, Espelid & Genz 1991 without printing it).
+ * GMQ_EST_EMBEDDED: eps_r = |I7_r - I5_r|, the difference of the degree-7
+ * rule and its embedded degree-5 rule.  GMQ_EST_NULL_RULES: four fully
+ * symmetric null rules on the same nodes (weight sums zero; degrees 5, 3,
+ * 3 and 1; mutually orthogonal, each with the norm of the degree-7
+ * weights), evaluated from the five class sums the rule already forms:
+ * e1 = |N1|, e2 = sqrt(N2^2 + N3^2), e3 = |N4|, r = max(e1/e2, e2/e3) (x/0 =
+ * infinity for x > 0, 0/0 = 0); eps_r = 10 max(e1, e2, e3) if r >= 1 (not
+ * yet asymptotic), else 10 r e1 (e1 extrapolated by one observed decay
+ * step: the degree-5 null rule is one step below the degree-7 rule).  The
+ * form and constants are this library's reading of the heuristic; the node
+ * work is the same, only the per-region epilogue changes. */
+typedef enum gmq_estimator {
+  GMQ_EST_EMBEDDED = 0,
+  GMQ_EST_NULL_RULES = 1
+} gmq_estimator;
+
 typedef struct gmq_problem {
   int32_t dim;       /* 1 <= dim <= GMQ_MAX_DIM                             */
   int32_t family;    /* gmq_family                                          */
@@ -125,6 +143,8 @@ typedef struct gmq_options {
                           precision results do, at FP32 rounding level      */
   int32_t flags;       /* 0, or GMQ_KEEP_PARTITION                           */
   int32_t rule;        /* gmq_rule (GMQ_RULE_GENZ_MALIK by default)          */
+  int32_t estimator;   /* gmq_estimator (GMQ_EST_EMBEDDED by default; the
+                          Gauss-Kronrod rule takes only the embedded one)   */
 } gmq_options;
 
 /* gmq_options.flags: record the final partition of the run (every region
@@ -136,7 +156,7 @@ typedef struct gmq_options {
 
 typedef struct gmq_result {
   double integral;           /* I: retired sums + active regions' I7_r     */
-  double error;              /* eps: the same for |I7_r - I5_r|            */
+  double error;              /* eps: the same for the regions' eps_r       */
   int64_t regions_evaluated; /* rule applications over all sweeps          */
   int64_t function_evals;    /* regions_evaluated * (2^d + 2d^2 + 2d + 1)  */
   int64_t final_active;      /* regions in the last evaluated sweep        */
@@ -316,31 +336,34 @@ gmq_status gmq_profile_enable(gmq_context *ctx, int32_t on);
 gmq_status gmq_profile_reset(gmq_context *ctx);
 gmq_status gmq_profile_read(gmq_context *ctx, int32_t kernel, gmq_kernel_stats *out);
 
-/* Measurement aid (no counterpart in the paper): the fused multiply-add
- * issue rate of the context's GPU, measured, as the peak the rule kernels'
- * rooflines are reported against.  precision GMQ_FP64 times FP64 FMAs,
- * GMQ_MIXED FP32 FMAs.  One launch of 8 x (SM count) blocks of 256 threads
- * (64 warps per SM), each thread running `iters` iterations of 16
- * independent FMA chains (1 <= iters <= 2^32), timed with CUDA events on
- * the context stream; the call waits for it.  *lane_fma_per_s receives the
- * lane FMAs per second (one FMA of one thread = one lane FMA = 2 flops),
- * *ms the launch's duration.  Its 8 x (SM count) x 256 x 8-byte result
- * sink is context memory (shared with gmq_rule_grad's working memory). */
-gmq_status gmq_probe_fma_rate(gmq_context *ctx, int32_t precision, int64_t iters,
-                              double *lane_fma_per_s, double *ms);
+/* Measurement aid (no counterpart in the paper): the floating-point issue
+ * rate of the context's GPU, measured, as the peak the rule kernels'
+ * rooflines are reported against.  precision GMQ_FP64 times FP64
+ * operations, GMQ_MIXED FP32 ones; op 0 times fused multiply-adds, 1 adds,
+ * 2 multiplies.  One launch of 8 x (SM count) blocks of 256 threads (64
+ * warps per SM), each thread running `iters` iterations of 16 independent
+ * chains of the operation (1 <= iters <= 2^32), timed with CUDA events on
+ * the context stream; the call waits for it.  *lane_ops_per_s receives the
+ * lane operations per second (one operation of one thread = one lane
+ * operation; a fused multiply-add counts 2 flops), *ms the launch's
+ * duration.  Its 8 x (SM count) x 256 x 8-byte result sink is context
+ * memory (shared with gmq_rule_grad's working memory). */
+gmq_status gmq_probe_fp_rate(gmq_context *ctx, int32_t precision, int32_t op, int64_t iters,
+                             double *lane_ops_per_s, double *ms);
 
 /* ---- step-level calls on caller device memory (one sweep's pieces) ---- */
 
 /* Rule evaluation (paper Sec. 2) on n regions.  Outputs, each of length n:
- * d_integral[r] = I7_r; d_error[r] = |I7_r - I5_r|; d_volfrac[r] =
+ * d_integral[r] = I7_r; d_error[r] = eps_r, the estimator's value
+ * (gmq_estimator: |I7_r - I5_r| or the null-rule estimate); d_volfrac[r] =
  * vol_r / vol(Omega) with vol_r = prod_k 2 h_k and vol(Omega) from the
  * problem's lo, hi; d_axis[r] = split axis in bits 0..6, bit 7 set when
  * bisecting along that axis cannot move the centre (round-off guard).
  * precision: gmq_precision; lanes: 0, 1, 4, 32 or (FP64) 128 as in
- * gmq_options.
+ * gmq_options; estimator: gmq_estimator.
  * d_volfrac may be NULL. */
 gmq_status gmq_eval_rule(gmq_context *ctx, const gmq_problem *prob,
-                         int32_t precision, int32_t lanes, int64_t n,
+                         int32_t precision, int32_t lanes, int32_t estimator, int64_t n,
                          const double *d_center, const double *d_halfw,
                          int64_t ld, double *d_integral, double *d_error,
                          double *d_volfrac, uint8_t *d_axis);
@@ -361,6 +384,13 @@ gmq_status gmq_eval_rule_gk(gmq_context *ctx, const gmq_problem *prob, int64_t n
  * bisection for the zeros of the Stieltjes polynomial, an 8 x 8 solve for
  * the Kronrod weights); no device work. */
 gmq_status gmq_gk_table(double *out);
+
+/* The library's null-rule table for dimension dim (host memory, 20
+ * doubles; GMQ_EST_NULL_RULES): out[5k + c] is null rule N_{k+1}'s weight
+ * per node of class c (centre, +-lambda2 e_k, +-lambda3 e_k, pairs,
+ * corners), unit volume; rows of degree 5, 3, 3, 1 (for dim 1 the third
+ * row is zero).  Computed on the host; no device work. */
+gmq_status gmq_null_rule_table(int32_t dim, double *out);
 
 /* The FP64 exponential the built-in integrands use (Tang's table-driven
  * method; within about one ulp), on n device values: d_y[i] = exp(d_x[i]).

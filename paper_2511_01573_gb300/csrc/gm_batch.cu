@@ -7,11 +7,12 @@
 // Layout: one region pool holds every integral's active regions; integral i
 // owns the contiguous segment [off_i, off_i + n_i) of the current list (SoA,
 // dmax rows, plus an int32 owner id per region).  Per sweep:
-//   k_batch_rule      all regions of all integrals, persistent grid; family
-//                     and dimension per region; 1, 4, 32 or 128 lanes per region,
-//                     chosen per sweep from the list length (the per-region
-//                     work is gm_region64.cuh's, so the choice never changes
-//                     a result)
+//   k_batch_rule64    one launch per family present (gm_batch_rule64.cuh):
+//                     that family's regions, persistent grid, dimension per
+//                     region; 1, 4, 32 or 128 lanes per region, chosen per
+//                     sweep from the list length (the per-region work is
+//                     gm_region64.cuh's, so the choice never changes a
+//                     result); the mixed form's k_batch_rule_mixed likewise
 //   k_batch_sums      tiles of 4096 regions of one integral each
 //                     (persistent grid): pairwise-tree sums per tile; the
 //                     integral's last tile adds the tile sums and tests the
@@ -37,7 +38,7 @@
 #include <vector>
 
 #include "gm_batch.cuh"
-#include "gm_rule.cuh"
+#include "gm_region64.cuh"
 
 namespace gmq {
 
@@ -130,124 +131,6 @@ __global__ void k_batch_partition(const BatchArgs B) {
     }
     B.rid[0][r] = id;
   }
-}
-
-// Doubles of the rule kernel's per-block coordinate tables for T lanes per
-// region: [kXRows + 1][dmax][128 / T] (coordinate rows and the half-widths)
-// and, for T > 1, the [4 dmax + 1][128 / T] axis-node scratch.
-__host__ __device__ constexpr long long batch_rule_doubles(int dmax, int T) {
-  return (long long)(kXRows + 1) * dmax * (kBatchRuleBlock / T) +
-         (T > 1 ? (long long)(4 * dmax + 1) * (kBatchRuleBlock / T) : 0);
-}
-
-// Pair tables of every dimension 2 .. dmax, one after the other: the table
-// of dimension d starts at entry d (d - 1) (d - 2) / 6.
-__host__ __device__ constexpr int batch_pairs_offset(int d) { return d * (d - 1) * (d - 2) / 6; }
-
-template <int T>
-__device__ __forceinline__ void batch_rule_lanes(const BatchArgs& B, double* smem,
-                                                 const unsigned short* pairs_all) {
-  constexpr int RPB = kBatchRuleBlock / T;  // regions per tile
-  const BatchState* bs = B.bs;
-  const long long n_total = bs->n_total;
-  const int cur = bs->parity;
-  const double* C = B.c[cur];
-  const double* H = B.h[cur];
-  const int32_t* rid = B.rid[cur];
-  const int dm = B.dmax;
-  const int tid = threadIdx.x;
-  const int g = tid / T, lane = tid & (T - 1);
-  const unsigned mask = group_mask<T>();
-  double* tabs = smem;                                      // [kXRows + 1][dm][RPB]
-  double* fvs = smem + (long long)(kXRows + 1) * dm * RPB;  // [4 dm + 1][RPB]
-  auto tab = [&](int row, int k) -> double { return tabs[(row * dm + k) * RPB + g]; };
-  for (long long tile = blockIdx.x; tile * RPB < n_total; tile += gridDim.x) {
-    const long long r = tile * RPB + g;
-    if (r >= n_total) break;  // so are the group's later tiles
-    group_sync<T>(mask);      // the group is done with the previous region's table
-    const BatchItem& it = B.items[rid[r]];
-    if (it.paused) continue;  // carried over with last sweep's outputs
-    const int d = it.P.d;
-    for (int k = lane; k < d; k += T) {
-      const double cv = C[(int64_t)k * B.ld + r], hv = H[(int64_t)k * B.ld + r];
-      double* col = tabs + (long long)k * RPB + g;
-      col[(long long)kXC * dm * RPB] = cv;
-      col[(long long)kXP2 * dm * RPB] = fma(B.lam2, hv, cv);
-      col[(long long)kXM2 * dm * RPB] = fma(-B.lam2, hv, cv);
-      col[(long long)kXP3 * dm * RPB] = fma(B.lam3, hv, cv);
-      col[(long long)kXM3 * dm * RPB] = fma(-B.lam3, hv, cv);
-      col[(long long)kXP5 * dm * RPB] = fma(B.lam5, hv, cv);
-      col[(long long)kXM5 * dm * RPB] = fma(-B.lam5, hv, cv);
-      col[(long long)kXRows * dm * RPB] = hv;
-    }
-    group_sync<T>(mask);
-    const unsigned short* pairs = pairs_all + batch_pairs_offset(d);
-    RegionSums o;
-    double* fv = fvs + g;
-    switch (it.P.family) {
-      case GMQ_OSCILLATORY:
-        region_sums64<GMQ_OSCILLATORY, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
-        break;
-      case GMQ_PRODUCT_PEAK:
-        region_sums64<GMQ_PRODUCT_PEAK, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
-        break;
-      case GMQ_CORNER_PEAK:
-        region_sums64<GMQ_CORNER_PEAK, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
-        break;
-      case GMQ_GAUSSIAN:
-        region_sums64<GMQ_GAUSSIAN, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
-        break;
-      case GMQ_C0:
-        region_sums64<GMQ_C0, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
-        break;
-      case GMQ_DISCONTINUOUS:
-        region_sums64<GMQ_DISCONTINUOUS, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
-        break;
-      default:
-        region_sums64<GMQ_POLY_SUMSQ11, T>(it.P, d, pairs, tab, fv, RPB, B.ratio, o);
-        break;
-    }
-    if (lane == 0)
-      region_finish64(
-          o, d, it.w7, it.w5, it.vol_omega, [&](int k) { return tab(kXC, k); },
-          [&](int k) { return tab(kXRows, k); }, B.i7[cur] + r, B.err[cur] + r, B.vf[cur] + r,
-          B.axis[cur] + r);
-  }
-}
-
-// Rule evaluation of every region of the current list: persistent grid of
-// kBatchRuleBlock-thread blocks, T = bs->lanes lanes per region (1, 4, 32,
-// or 128 = the block; set per sweep by k_batch_advance; the results do not
-// depend on it).
-__global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule(const BatchArgs B) {
-  extern __shared__ __align__(16) double smem[];
-  const int dm = B.dmax;
-  long long most = batch_rule_doubles(dm, 1);
-  if (batch_rule_doubles(dm, 4) > most) most = batch_rule_doubles(dm, 4);
-  if (batch_rule_doubles(dm, 32) > most) most = batch_rule_doubles(dm, 32);
-  if (batch_rule_doubles(dm, 128) > most) most = batch_rule_doubles(dm, 128);
-  unsigned short* pairs_all = reinterpret_cast<unsigned short*>(smem + most);
-  for (int e = 2; e <= dm; ++e) {
-    const int np = e * (e - 1) / 2;
-    for (int p = threadIdx.x; p < np; p += blockDim.x) {
-      int j = 0, rem = p;
-      while (rem >= e - 1 - j) {
-        rem -= e - 1 - j;
-        ++j;
-      }
-      pairs_all[batch_pairs_offset(e) + p] = (unsigned short)((j << 8) | (j + 1 + rem));
-    }
-  }
-  __syncthreads();
-  const int lanes = B.bs->lanes;
-  if (lanes == 128)
-    batch_rule_lanes<128>(B, smem, pairs_all);
-  else if (lanes == 32)
-    batch_rule_lanes<32>(B, smem, pairs_all);
-  else if (lanes == 4)
-    batch_rule_lanes<4>(B, smem, pairs_all);
-  else
-    batch_rule_lanes<1>(B, smem, pairs_all);
 }
 
 // Global sums and convergence test of every integral (persistent grid over
@@ -743,40 +626,12 @@ __global__ void k_batch_advance(const BatchArgs B) {
 }
 
 size_t batch_rule_smem(int dmax) {
-  long long most = batch_rule_doubles(dmax, 1);
-  if (batch_rule_doubles(dmax, 4) > most) most = batch_rule_doubles(dmax, 4);
-  if (batch_rule_doubles(dmax, 32) > most) most = batch_rule_doubles(dmax, 32);
-  if (batch_rule_doubles(dmax, 128) > most) most = batch_rule_doubles(dmax, 128);
   const size_t pairs = sizeof(unsigned short) * (size_t)batch_pairs_offset(dmax + 1);
-  return (sizeof(double) * (size_t)most + pairs + 15) & ~(size_t)15;
-}
-
-int batch_rule_max_blocks(int dmax) {
-  int nb = 0;
-  const size_t smem = batch_rule_smem(dmax);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_batch_rule, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_rule, kBatchRuleBlock, smem) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
-  return nb > 0 ? nb : 1;
+  return (sizeof(double) * (size_t)batch_rule_doubles_max(dmax) + pairs + 15) & ~(size_t)15;
 }
 
 cudaError_t batch_launch_partition(const BatchArgs& B, cudaStream_t s) {
   k_batch_partition<<<B.count, 256, 0, s>>>(B);
-  return cudaGetLastError();
-}
-
-cudaError_t batch_launch_rule(const BatchArgs& B, int grid, cudaStream_t s) {
-  const size_t smem = batch_rule_smem(B.dmax);
-  if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_batch_rule, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_batch_rule<<<grid, kBatchRuleBlock, smem, s>>>(B);
   return cudaGetLastError();
 }
 

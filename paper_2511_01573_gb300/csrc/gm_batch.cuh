@@ -15,6 +15,7 @@ struct BatchItem {
   FamParams P;
   SmemParams<float> Pf;    // the parameters rounded to FP32 (mixed form)
   double w7[5], w5[5];
+  double nw[20];           // null-rule weights (GMQ_EST_NULL_RULES)
   double vol_omega;
   double rel_tol, abs_tol;
   double lo[GMQ_MAX_DIM];
@@ -83,6 +84,7 @@ struct BatchArgs {
   uint8_t* flags;
   int dmax;
   int classifier;
+  int estimator;           // gmq_estimator of every integral of the batch
   double guard;
   double lam2, lam3, lam5, ratio;
   cudaGraphConditionalHandle cond;
@@ -110,14 +112,36 @@ __host__ __device__ inline int batch_lanes_for(const BatchArgs& B, long long n) 
 }
 
 
-// Shared memory of the rule kernel for the largest dimension.
+// Doubles of the FP64 rule kernel's per-block coordinate tables for T lanes
+// per region: [kXRows + 1][dmax][128 / T] (the seven coordinate rows and the
+// half-widths) and, for T > 1, the [4 dmax + 1][128 / T] axis-node scratch;
+// the kernel sizes its shared memory for the largest over T.
+__host__ __device__ constexpr long long batch_rule_doubles(int dmax, int T) {
+  return (long long)(7 + 1) * dmax * (kBatchRuleBlock / T) +
+         (T > 1 ? (long long)(4 * dmax + 1) * (kBatchRuleBlock / T) : 0);
+}
+__host__ __device__ constexpr long long batch_rule_doubles_max(int dmax) {
+  long long m = batch_rule_doubles(dmax, 1);
+  if (batch_rule_doubles(dmax, 4) > m) m = batch_rule_doubles(dmax, 4);
+  if (batch_rule_doubles(dmax, 32) > m) m = batch_rule_doubles(dmax, 32);
+  if (batch_rule_doubles(dmax, 128) > m) m = batch_rule_doubles(dmax, 128);
+  return m;
+}
+
+// Pair tables of every dimension 2 .. dmax, one after the other: the table
+// of dimension d starts at entry d (d - 1) (d - 2) / 6.
+__host__ __device__ constexpr int batch_pairs_offset(int d) { return d * (d - 1) * (d - 2) / 6; }
+
+// Shared memory of the FP64 rule kernel for the largest dimension.
 size_t batch_rule_smem(int dmax);
-// Resident blocks per SM of the rule kernel.
-int batch_rule_max_blocks(int dmax);
 cudaError_t batch_launch_partition(const BatchArgs& B, cudaStream_t s);
-// Rule evaluation of every region of the current list (persistent grid,
-// bs->lanes lanes per region).
-cudaError_t batch_launch_rule(const BatchArgs& B, int grid, cudaStream_t s);
+// FP64 rule evaluation of the current list's regions of family FAM
+// (gm_batch_rule64.cuh; one launch per family present in the batch,
+// persistent grid, bs->lanes lanes per region).
+template <int FAM>
+cudaError_t batch_launch_rule64_family(const BatchArgs& B, int grid, cudaStream_t s);
+template <int FAM>
+int batch_rule64_max_blocks_family(int dmax);
 // Mixed form: rule evaluation of the current list's regions of family FAM
 // (gm_batch_mixed.cuh; one launch per family present in the batch).
 template <int FAM>

@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule_mixed(const Batc
         region_mixed_flat<FAM>(it.Pf, d, pairs_all + d * (d - 1) * (d - 2) / 6, tab, B.ratio, o);
         break;
     }
-    region_finish64(o, d, it.w7, it.w5, it.vol_omega, cval, hval, B.i7[cur] + r,
-                    B.err[cur] + r, B.vf[cur] + r, B.axis[cur] + r);
+    region_finish64(o, d, it.w7, it.w5, B.estimator ? it.nw : nullptr, it.vol_omega, cval, hval,
+                    B.i7[cur] + r, B.err[cur] + r, B.vf[cur] + r, B.axis[cur] + r);
   }
 }
 

@@ -310,13 +310,50 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
   o.kbest = kbest;
 }
 
+// Null-rule error estimate of a region from its class sums (the heuristic
+// of Berntsen, Espelid & Genz 1991 that the paper's Sec. 2 cites; constants
+// and combination as the library reads it).  nw: 4 x 5 per-node weights of
+// four fully symmetric null rules on the rule's node classes (degrees 5,
+// 3, 3, 1, mutually orthogonal, each with the norm of the degree-7
+// weights; unit volume).  N_k = vol sum_c nw[k][c] S_c; e1 = |N1|,
+// e2 = sqrt(N2^2 + N3^2), e3 = |N4|; r = max(e1 / e2, e2 / e3) (x / 0 = inf
+// for x > 0, 0 / 0 = 0) is the decay per degree step.  r >= 1 (not yet
+// asymptotic): 10 max(e); r < 1: 10 r e1, e1 extrapolated by one decay step
+// (the degree-5 null rule is one step below the degree-7 rule).  Every
+// operation is rounded separately, in the order written.
+__device__ __forceinline__ double null_ratio(double x, double y) {
+  if (y > 0.0) return __ddiv_rn(x, y);
+  return x > 0.0 ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
+}
+
+__device__ __forceinline__ double null_rule_estimate(const RegionSums& o, double vol,
+                                                     const double* nw) {
+  const double s[5] = {o.s1, o.s2, o.s3, o.s4, o.s5};
+  double nul[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double t = __dmul_rn(nw[k * 5], s[0]);
+#pragma unroll
+    for (int c = 1; c < 5; ++c) t = __dadd_rn(t, __dmul_rn(nw[k * 5 + c], s[c]));
+    nul[k] = __dmul_rn(vol, t);
+  }
+  const double e1 = fabs(nul[0]);
+  const double e2 = __dsqrt_rn(__dadd_rn(__dmul_rn(nul[1], nul[1]), __dmul_rn(nul[2], nul[2])));
+  const double e3 = fabs(nul[3]);
+  const double r = fmax(null_ratio(e1, e2), null_ratio(e2, e3));
+  if (r >= 1.0) return __dmul_rn(10.0, fmax(e1, fmax(e2, e3)));
+  return __dmul_rn(__dmul_rn(10.0, r), e1);
+}
+
 // Rule values, error estimate, split axis and round-off guard of a region
 // from its class sums (one lane).  cval(k), hval(k): centre and half-width.
+// nw: the null-rule table for the null-rule estimate, or null for the
+// embedded estimate |I7 - I5|.
 template <class CV, class HV>
 __device__ __forceinline__ void region_finish64(const RegionSums& o, int d, const double* w7,
-                                                const double* w5, double vol_omega, CV cval,
-                                                HV hval, double* i7o, double* erro, double* vfo,
-                                                uint8_t* axo) {
+                                                const double* w5, const double* nw,
+                                                double vol_omega, CV cval, HV hval, double* i7o,
+                                                double* erro, double* vfo, uint8_t* axo) {
   double vol = 1.0;
   for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, hval(k)));
   double t7 = __dmul_rn(w7[0], o.s1);
@@ -349,7 +386,7 @@ __device__ __forceinline__ void region_finish64(const RegionSums& o, int d, cons
   const double hh = __dmul_rn(0.5, hval(ax));
   const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
   *i7o = i7;
-  *erro = fabs(__dsub_rn(i7, i5));
+  *erro = nw ? null_rule_estimate(o, vol, nw) : fabs(__dsub_rn(i7, i5));
   if (vfo) *vfo = __ddiv_rn(vol, vol_omega);
   *axo = (uint8_t)(ax | (bad ? 0x80 : 0));
 }

@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_mixed(const RuleArgs A) {
         *P, d, pairs, [&](int row, int j) -> float { return xt[(row * d + j) * RB + g]; },
         A.R.ratio, o);
     region_finish64(
-        o, d, A.R.w7, A.R.w5, A.R.vol_omega, [&](int k) { return cd[k * RB + g]; },
+        o, d, A.R.w7, A.R.w5, A.R.estimator ? A.R.nw : nullptr, A.R.vol_omega,
+        [&](int k) { return cd[k * RB + g]; },
         [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
         A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
     return;
@@ -251,7 +252,8 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_mixed(const RuleArgs A) {
     o.dbest = dbest;
     o.kbest = kbest;
     region_finish64(
-        o, d, A.R.w7, A.R.w5, A.R.vol_omega, [&](int k) { return cd[k * RB + g]; },
+        o, d, A.R.w7, A.R.w5, A.R.estimator ? A.R.nw : nullptr, A.R.vol_omega,
+        [&](int k) { return cd[k * RB + g]; },
         [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
         A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
   }
@@ -317,7 +319,8 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule64(const RuleArgs A) {
   region_sums64<FAM, T>(*P, d, pairs, tab, fv + g, RB, A.R.ratio, o);
   if ((tid & (T - 1)) == 0)
     region_finish64(
-        o, d, A.R.w7, A.R.w5, A.R.vol_omega, [&](int k) { return cd[k * RB + g]; },
+        o, d, A.R.w7, A.R.w5, A.R.estimator ? A.R.nw : nullptr, A.R.vol_omega,
+        [&](int k) { return cd[k * RB + g]; },
         [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
         A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
 }
@@ -370,7 +373,8 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule_mixed_reg(const RuleArgs A)
   region_mixed_walk<FAM, D>(
       *P, [&](int row, int j) -> float { return xt[(row * d + j) * RB + g]; }, A.R.ratio, o);
   region_finish64(
-      o, d, A.R.w7, A.R.w5, A.R.vol_omega, [&](int k) { return cd[k * RB + g]; },
+      o, d, A.R.w7, A.R.w5, A.R.estimator ? A.R.nw : nullptr, A.R.vol_omega,
+      [&](int k) { return cd[k * RB + g]; },
       [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
       A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
 }

@@ -150,7 +150,63 @@ PoolLayout pool_layout(int d, int64_t cap, int flags) {
   return L;
 }
 
-RuleConst rule_const(int d, const double* lo, const double* hi) {
+// Null rules for the null-rule error estimate (Berntsen, Espelid & Genz
+// 1991, cited by the paper's Sec. 2): four fully symmetric null rules on the
+// rule's five node classes, of degrees 5, 3, 3 and 1, mutually orthogonal
+// for <u, v> = sum over nodes u v = sum_c n_c u_c v_c, each with the norm of
+// the degree-7 weights.  Built here from the conditions' side: with g_m the
+// class sums of monomial m divided by the class sizes (g_1, g_{x1^2},
+// g_{x1^4}, g_{x1^2 x2^2}), a rule v annihilates m iff <v, g_m> = 0, so
+//   - N4 spans the degree-1 null rules orthogonal to the degree-3 ones:
+//     g_{x1^2} made orthogonal to g_1;
+//   - N2, N3 span the degree-3 null rules orthogonal to the degree-5 ones:
+//     g_{x1^4}, g_{x1^2 x2^2} made orthogonal to g_1, g_{x1^2} and each
+//     other (d = 1 has no x2 and no pair class: N3 = 0);
+//   - N1 spans the degree-5 null rules: w7 - w5 (the difference of the two
+//     embedded rules, both exact to degree 5).
+// Gram-Schmidt in that order (modified, twice for stability), then each
+// scaled to |w7|.  nw: 4 x 5, row k = N_{k+1}'s weight per node of class c.
+void null_rule_weights(int d, const double* w7, const double* w5, double* nw) {
+  const double l2 = 9.0 / 70.0, l3 = 9.0 / 10.0, l5 = 9.0 / 19.0;  // lambda^2 (lambda4 = lambda3)
+  const double n[5] = {1.0, 2.0 * d, 2.0 * d, 2.0 * d * (d - 1), std::ldexp(1.0, d)};
+  auto dot = [&](const double* u, const double* v) {
+    double t = 0.0;
+    for (int c = 0; c < 5; ++c) t += n[c] * u[c] * v[c];
+    return t;
+  };
+  auto divide = [&](double* g) {
+    for (int c = 0; c < 5; ++c) g[c] = n[c] > 0.0 ? g[c] / n[c] : 0.0;
+  };
+  double g[4][5] = {
+      {1.0, 2.0 * d, 2.0 * d, 2.0 * d * (d - 1), n[4]},
+      {0.0, 2.0 * l2, 2.0 * l3, 4.0 * (d - 1) * l3, n[4] * l5},
+      {0.0, 2.0 * l2 * l2, 2.0 * l3 * l3, 4.0 * (d - 1) * l3 * l3, n[4] * l5 * l5},
+      {0.0, 0.0, 0.0, 4.0 * l3 * l3, n[4] * l5 * l5}};
+  const int ng = d >= 2 ? 4 : 3;
+  for (int m = 0; m < ng; ++m) divide(g[m]);
+  for (int m = 0; m < ng; ++m)
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = 0; q < m; ++q) {
+        const double f = dot(g[m], g[q]) / dot(g[q], g[q]);
+        for (int c = 0; c < 5; ++c) g[m][c] -= f * g[q][c];
+      }
+  const double norm7 = std::sqrt(dot(w7, w7));
+  double rows[4][5] = {};
+  for (int c = 0; c < 5; ++c) rows[0][c] = w7[c] - w5[c];
+  if (d == 1) rows[0][3] = 0.0;
+  for (int c = 0; c < 5; ++c) {
+    rows[1][c] = g[2][c];
+    rows[2][c] = d >= 2 ? g[3][c] : 0.0;
+    rows[3][c] = g[1][c];
+  }
+  for (int k = 0; k < 4; ++k) {
+    const double nn = dot(rows[k], rows[k]);
+    const double f = nn > 0.0 ? norm7 / std::sqrt(nn) : 0.0;
+    for (int c = 0; c < 5; ++c) nw[k * 5 + c] = rows[k][c] * f;
+  }
+}
+
+RuleConst rule_const(int d, const double* lo, const double* hi, int estimator = GMQ_EST_EMBEDDED) {
   RuleConst R;
   const double dd = (double)d;
   R.lam2 = std::sqrt(9.0 / 70.0);
@@ -174,6 +230,9 @@ RuleConst rule_const(int d, const double* lo, const double* hi) {
   }
   R.vol_omega = v;
   R.nodes = num_nodes(d);
+  R.estimator = estimator;
+  for (int k = 0; k < 20; ++k) R.nw[k] = 0.0;
+  if (estimator == GMQ_EST_NULL_RULES) null_rule_weights(d, R.w7, R.w5, R.nw);
   return R;
 }
 
@@ -265,6 +324,32 @@ cudaError_t batch_launch_rule_mixed(int fam, const BatchArgs& B, int grid, cudaS
     case GMQ_DISCONTINUOUS: return batch_launch_rule_mixed_family<GMQ_DISCONTINUOUS>(B, grid, s);
     case GMQ_POLY_SUMSQ11: return batch_launch_rule_mixed_family<GMQ_POLY_SUMSQ11>(B, grid, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t batch_launch_rule64(int fam, const BatchArgs& B, int grid, cudaStream_t s) {
+  switch (fam) {
+    case GMQ_OSCILLATORY: return batch_launch_rule64_family<GMQ_OSCILLATORY>(B, grid, s);
+    case GMQ_PRODUCT_PEAK: return batch_launch_rule64_family<GMQ_PRODUCT_PEAK>(B, grid, s);
+    case GMQ_CORNER_PEAK: return batch_launch_rule64_family<GMQ_CORNER_PEAK>(B, grid, s);
+    case GMQ_GAUSSIAN: return batch_launch_rule64_family<GMQ_GAUSSIAN>(B, grid, s);
+    case GMQ_C0: return batch_launch_rule64_family<GMQ_C0>(B, grid, s);
+    case GMQ_DISCONTINUOUS: return batch_launch_rule64_family<GMQ_DISCONTINUOUS>(B, grid, s);
+    case GMQ_POLY_SUMSQ11: return batch_launch_rule64_family<GMQ_POLY_SUMSQ11>(B, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int batch_rule64_max_blocks(int fam, int dmax) {
+  switch (fam) {
+    case GMQ_OSCILLATORY: return batch_rule64_max_blocks_family<GMQ_OSCILLATORY>(dmax);
+    case GMQ_PRODUCT_PEAK: return batch_rule64_max_blocks_family<GMQ_PRODUCT_PEAK>(dmax);
+    case GMQ_CORNER_PEAK: return batch_rule64_max_blocks_family<GMQ_CORNER_PEAK>(dmax);
+    case GMQ_GAUSSIAN: return batch_rule64_max_blocks_family<GMQ_GAUSSIAN>(dmax);
+    case GMQ_C0: return batch_rule64_max_blocks_family<GMQ_C0>(dmax);
+    case GMQ_DISCONTINUOUS: return batch_rule64_max_blocks_family<GMQ_DISCONTINUOUS>(dmax);
+    case GMQ_POLY_SUMSQ11: return batch_rule64_max_blocks_family<GMQ_POLY_SUMSQ11>(dmax);
+    default: return 1;
   }
 }
 
@@ -769,7 +854,9 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
       (opt->lanes == 128 && opt->precision != GMQ_FP64) ||
       (opt->rule != GMQ_RULE_GENZ_MALIK && opt->rule != GMQ_RULE_GAUSS_KRONROD) ||
       (opt->rule == GMQ_RULE_GAUSS_KRONROD &&
-       (opt->precision != GMQ_FP64 || d > GMQ_GK_MAX_DIM)))
+       (opt->precision != GMQ_FP64 || d > GMQ_GK_MAX_DIM ||
+        opt->estimator != GMQ_EST_EMBEDDED)) ||
+      (opt->estimator != GMQ_EST_EMBEDDED && opt->estimator != GMQ_EST_NULL_RULES))
     return out->status = GMQ_ERR_INVALID, GMQ_ERR_INVALID;
   const bool gk = opt->rule == GMQ_RULE_GAUSS_KRONROD;
   const int s = opt->init_splits > 0 ? opt->init_splits : auto_splits(d, cap);
@@ -797,7 +884,7 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
   cudaStream_t strm = ctx->stream;
 
   const FamParams P = fam_params(prob);
-  const RuleConst R = rule_const(d, prob->lo, prob->hi);
+  const RuleConst R = rule_const(d, prob->lo, prob->hi, opt->estimator);
   int64_t nodes_per_region = R.nodes;
   if (gk) {
     gmq_status gs = ensure_gk(ctx);
@@ -968,7 +1055,8 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
 }
 
 gmq_status gmq_eval_rule(gmq_context* ctx, const gmq_problem* prob, int32_t precision,
-                         int32_t lanes, int64_t n, const double* d_center, const double* d_halfw,
+                         int32_t lanes, int32_t estimator, int64_t n, const double* d_center,
+                         const double* d_halfw,
                          int64_t ld, double* d_integral, double* d_error, double* d_volfrac,
                          uint8_t* d_axis) {
   if (!ctx) return GMQ_ERR_INVALID;
@@ -980,6 +1068,7 @@ gmq_status gmq_eval_rule(gmq_context* ctx, const gmq_problem* prob, int32_t prec
   if (lanes != 0 && lanes != 1 && lanes != 4 && lanes != 32 && lanes != 128)
     return GMQ_ERR_INVALID;
   if (lanes == 128 && precision != GMQ_FP64) return GMQ_ERR_INVALID;
+  if (estimator != GMQ_EST_EMBEDDED && estimator != GMQ_EST_NULL_RULES) return GMQ_ERR_INVALID;
   if (n == 0) return GMQ_OK;
   DeviceGuard g(ctx->device);
   if (!g.ok) return GMQ_ERR_CUDA;
@@ -993,7 +1082,7 @@ gmq_status gmq_eval_rule(gmq_context* ctx, const gmq_problem* prob, int32_t prec
   A.volfrac = d_volfrac;
   A.axis = d_axis;
   A.P = fam_params(prob);
-  A.R = rule_const(prob->dim, prob->lo, prob->hi);
+  A.R = rule_const(prob->dim, prob->lo, prob->hi, estimator);
   const int T = choose_lanes(lanes, n, prob->dim, ctx->sm_count, precision);
   prof_begin(ctx, kKRule);
   GMQ_CK(launch_rule(prob->family, precision, T, A, ctx->stream));
@@ -1092,6 +1181,13 @@ gmq_status gmq_math_cos(gmq_context* ctx, int64_t n, const double* d_x, double* 
   GMQ_CK(cudaGetLastError());
   ctx->launches += 1;
   GMQ_CK(cudaStreamSynchronize(ctx->stream));
+  return GMQ_OK;
+}
+
+gmq_status gmq_null_rule_table(int32_t dim, double* out) {
+  if (!out || dim < 1 || dim > GMQ_MAX_DIM) return GMQ_ERR_INVALID;
+  const RuleConst R = rule_const(dim, nullptr, nullptr, GMQ_EST_NULL_RULES);
+  for (int k = 0; k < 20; ++k) out[k] = R.nw[k];
   return GMQ_OK;
 }
 
@@ -1233,10 +1329,10 @@ gmq_status gmq_partition(gmq_context* ctx, int32_t dim, const double* lo, const 
   return GMQ_OK;
 }
 
-gmq_status gmq_probe_fma_rate(gmq_context* ctx, int32_t precision, int64_t iters,
-                              double* lane_fma_per_s, double* ms) {
-  if (!ctx || !lane_fma_per_s || !ms || iters < 1 || iters > ((int64_t)1 << 32) ||
-      (precision != GMQ_FP64 && precision != GMQ_MIXED))
+gmq_status gmq_probe_fp_rate(gmq_context* ctx, int32_t precision, int32_t op, int64_t iters,
+                             double* lane_ops_per_s, double* ms) {
+  if (!ctx || !lane_ops_per_s || !ms || iters < 1 || iters > ((int64_t)1 << 32) ||
+      (precision != GMQ_FP64 && precision != GMQ_MIXED) || op < 0 || op > 2)
     return GMQ_ERR_INVALID;
   DeviceGuard g(ctx->device);
   if (!g.ok) return GMQ_ERR_CUDA;
@@ -1259,14 +1355,14 @@ gmq_status gmq_probe_fma_rate(gmq_context* ctx, int32_t precision, int64_t iters
   GMQ_CK(cudaEventCreate(&ev.b));
   const int fp64 = precision == GMQ_FP64 ? 1 : 0;
   GMQ_CK(cudaEventRecord(ev.a, ctx->stream));
-  GMQ_CK(launch_fma_probe(fp64, blocks, iters, ctx->gscratch, ctx->stream));
+  GMQ_CK(launch_fma_probe(fp64, op, blocks, iters, ctx->gscratch, ctx->stream));
   GMQ_CK(cudaEventRecord(ev.b, ctx->stream));
   ctx->launches += 1;
   GMQ_CK(cudaEventSynchronize(ev.b));
   float t = 0.f;
   GMQ_CK(cudaEventElapsedTime(&t, ev.a, ev.b));
   *ms = (double)t;
-  *lane_fma_per_s = t > 0.f ? (double)fma_probe_lane_fmas(blocks, iters) / ((double)t * 1e-3) : 0.0;
+  *lane_ops_per_s = t > 0.f ? (double)fma_probe_lane_fmas(blocks, iters) / ((double)t * 1e-3) : 0.0;
   return GMQ_OK;
 }
 
@@ -1338,7 +1434,8 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
       (opt->lanes != 0 && opt->lanes != 1 && opt->lanes != 4 && opt->lanes != 32 &&
        opt->lanes != 128) ||
       (opt->precision == GMQ_MIXED && opt->lanes > 1) || opt->rule != GMQ_RULE_GENZ_MALIK ||
-      (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL))
+      (opt->classifier != GMQ_VOLUME_SHARE && opt->classifier != GMQ_LOCAL_REL) ||
+      (opt->estimator != GMQ_EST_EMBEDDED && opt->estimator != GMQ_EST_NULL_RULES))
     return GMQ_ERR_INVALID;
   std::memset(results, 0, sizeof(gmq_result) * (size_t)count);
   const int max_iters = opt->max_iters > 0 ? opt->max_iters : 1000;
@@ -1381,10 +1478,13 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
     }
     it.Pf.c0 = (float)it.P.c0;
     fam_present[p->family] = true;
-    const RuleConst R = rule_const(d, p->lo, p->hi);
+    const RuleConst R = rule_const(d, p->lo, p->hi, opt->estimator);
     for (int c = 0; c < 5; ++c) {
       it.w7[c] = R.w7[c];
       it.w5[c] = R.w5[c];
+    }
+    for (int c = 0; c < 20; ++c) {
+      it.nw[c] = R.nw[c];
     }
     it.vol_omega = R.vol_omega;
     it.rel_tol = tol;
@@ -1494,6 +1594,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   B.tile_pos = (long long*)(base + o_tp);
   B.tile_grid = 2 * ctx->sm_count;
   B.classifier = opt->classifier;
+  B.estimator = opt->estimator;
   B.guard = mixed ? kGuardMixed : kGuardFp64;
   const RuleConst R0 = rule_const(1, nullptr, nullptr);
   B.lam2 = R0.lam2;
@@ -1542,27 +1643,30 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   // only write rule outputs, which the first sweep overwrites)
   gmq_batch_info info;
   std::memset(&info, 0, sizeof(info));
-  // mixed form: one rule launch per family present, one lane per region
-  int grid = 0;
+  // one rule launch per family present (FP64: lanes per region per sweep;
+  // mixed: one lane per region), each a persistent grid of its own size
   int fam_grid[7] = {};
-  if (mixed) {
-    for (int f = 0; f < 7; ++f)
-      if (fam_present[f]) fam_grid[f] = ctx->sm_count * batch_rule_mixed_max_blocks(f, dmax);
-  } else {
-    grid = ctx->sm_count * batch_rule_max_blocks(dmax);  // also sets the smem limit
-  }
+  for (int f = 0; f < 7; ++f)
+    if (fam_present[f])
+      fam_grid[f] = ctx->sm_count * (mixed ? batch_rule_mixed_max_blocks(f, dmax)
+                                           : batch_rule64_max_blocks(f, dmax));
   auto launch_rule_step = [&](cudaStream_t st) -> cudaError_t {
-    if (!mixed) return batch_launch_rule(B, grid, st);
     for (int f = 0; f < 7; ++f) {
       if (!fam_present[f]) continue;
-      const cudaError_t e = batch_launch_rule_mixed(f, B, fam_grid[f], st);
+      const cudaError_t e = mixed ? batch_launch_rule_mixed(f, B, fam_grid[f], st)
+                                  : batch_launch_rule64(f, B, fam_grid[f], st);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
   int rule_launches = 0;
   for (int f = 0; f < 7; ++f) rule_launches += fam_present[f] ? 1 : 0;
-  if (!mixed) rule_launches = 1;
+  // the family the autotuner times (its kernel over copies of the whole
+  // initial list stands for the rule step: the lanes choice depends on the
+  // list length and the dimension, not on the integrand)
+  int f_tune = 0;
+  while (f_tune < 6 && !fam_present[f_tune]) ++f_tune;
+  const int grid = fam_grid[f_tune];
   B.forced_lanes = mixed ? 1 : opt->lanes;
   if (!mixed && !opt->lanes && !ctx->tuned[dmax]) {
     const int64_t wave = (int64_t)grid * kBatchRuleBlock;  // regions of one T = 1 wave
@@ -1587,10 +1691,11 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
         BatchState t = bs0;
         t.n_total = lens[i];
         t.lanes = modes[m];
+        for (int f = 0; f < 8; ++f) t.fam_off[0][f] = f <= f_tune ? 0 : lens[i];
         GMQ_CK(cudaMemcpyAsync(B.bs, &t, sizeof(BatchState), cudaMemcpyHostToDevice, strm));
-        GMQ_CK(batch_launch_rule(B, grid, strm));  // warm-up
+        GMQ_CK(batch_launch_rule64(f_tune, B, grid, strm));  // warm-up
         GMQ_CK(cudaEventRecord(e0, strm));
-        GMQ_CK(batch_launch_rule(B, grid, strm));
+        GMQ_CK(batch_launch_rule64(f_tune, B, grid, strm));
         GMQ_CK(cudaEventRecord(e1, strm));
         GMQ_CK(cudaEventSynchronize(e1));
         GMQ_CK(cudaEventElapsedTime(&ms[m], e0, e1));
@@ -1630,9 +1735,8 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   bs0.lanes = batch_lanes_for(B, bs0.n_total);
   GMQ_CK(cudaMemcpyAsync(B.bs, &bs0, sizeof(BatchState), cudaMemcpyHostToDevice, strm));
   info.rule_block = kBatchRuleBlock;
-  info.rule_grid = grid;
-  if (mixed)
-    for (int f = 0; f < 7; ++f) info.rule_grid = std::max(info.rule_grid, fam_grid[f]);
+  info.rule_grid = 0;
+  for (int f = 0; f < 7; ++f) info.rule_grid = std::max(info.rule_grid, fam_grid[f]);
   info.forced_lanes = B.forced_lanes;
   info.lanes_t1 = B.forced_lanes ? 0 : B.lanes_t1;
   info.lanes_t4 = B.forced_lanes ? 0 : B.lanes_t4;

@@ -38,6 +38,8 @@ struct RuleConst {
   double ratio;             // lambda2^2 / lambda3^2 = 1/7
   double vol_omega;         // prod_k (hi_k - lo_k)
   int64_t nodes;            // 2^d + 2d^2 + 2d + 1
+  int32_t estimator;        // gmq_estimator
+  double nw[20];            // null-rule weights (GMQ_EST_NULL_RULES), 4 x 5
 };
 
 struct RuleArgs {

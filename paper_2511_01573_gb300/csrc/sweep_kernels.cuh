@@ -27,11 +27,13 @@ cudaError_t launch_tree_sum(const double* v, int64_t n, double* blk, DevStatus* 
 cudaError_t launch_rows_tree_sum(const double* v, int64_t ldv, int64_t n, int rows, double* blk,
                                  unsigned* tickets, double* out, cudaStream_t s);
 
-// FMA throughput probe (fma_probe.cu): `blocks` blocks of kProbeBlock
-// threads; sink holds blocks * kProbeBlock elements (double if fp64, else
-// float).  fma_probe_lane_fmas: the lane FMAs one launch performs.
+// Issue-rate probe (fma_probe.cu): `blocks` blocks of kProbeBlock threads
+// running chains of one operation (op 0 fused multiply-add, 1 add, 2
+// multiply); sink holds blocks * kProbeBlock elements (double if fp64, else
+// float).  fma_probe_lane_fmas: the lane operations one launch performs.
 constexpr int kProbeBlock = 256;
-cudaError_t launch_fma_probe(int fp64, int blocks, int64_t iters, void* sink, cudaStream_t s);
+cudaError_t launch_fma_probe(int fp64, int op, int blocks, int64_t iters, void* sink,
+                             cudaStream_t s);
 int64_t fma_probe_lane_fmas(int blocks, int64_t iters);
 
 }  // namespace gmq

@@ -25,6 +25,7 @@ ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5
  POLY_SUMSQ11) = range(7)
 FP64, MIXED = 0, 1
 VOLUME_SHARE, LOCAL_REL = 0, 1
+EST_EMBEDDED, EST_NULL_RULES = 0, 1
 
 _dp = C.POINTER(C.c_double)
 
@@ -38,7 +39,7 @@ class Options(C.Structure):
     _fields_ = [("rel_tol", C.c_double), ("abs_tol", C.c_double), ("max_regions", C.c_int64),
                 ("init_splits", C.c_int32), ("max_iters", C.c_int32), ("precision", C.c_int32),
                 ("classifier", C.c_int32), ("lanes", C.c_int32), ("flags", C.c_int32),
-                ("rule", C.c_int32)]
+                ("rule", C.c_int32), ("estimator", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -65,7 +66,7 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
            "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad",
            "gmq_integrate_batch", "gmq_last_batch_info", "gmq_eval_rule_gk", "gmq_gk_table",
-           "gmq_math_exp", "gmq_math_rcp", "gmq_math_cos", "gmq_probe_fma_rate")
+           "gmq_math_exp", "gmq_math_rcp", "gmq_math_cos", "gmq_probe_fp_rate", "gmq_null_rule_table")
 
 KEEP_PARTITION = 1
 BATCH_HOST_LOOP = 2
@@ -84,6 +85,14 @@ class BatchInfo(C.Structure):
 
 ERR_TOO_LARGE = -6
 NOALLOC_MAX_N = 1 << 23
+
+
+def null_rule_table(dim: int):
+    """The library's null-rule weights for dimension dim (4 x 5: rows N1..N4,
+    columns the node classes; unit volume)."""
+    out = np.zeros(20)
+    _check("gmq_null_rule_table", lib().gmq_null_rule_table(dim, out.ctypes.data_as(_dp)))
+    return out.reshape(4, 5)
 
 
 def gk_table():
@@ -128,7 +137,8 @@ def lib():
         "gmq_last_trace": [vp, C.POINTER(Sweep), i32, C.POINTER(i32)],
         "gmq_seed_genz": [C.c_uint64, i32, i32, dbl, _dp, _dp],
         "gmq_launch_count": [vp, C.POINTER(i64)],
-        "gmq_eval_rule": [vp, C.POINTER(Problem), i32, i32, i64, vp, vp, i64, vp, vp, vp, vp],
+        "gmq_eval_rule": [vp, C.POINTER(Problem), i32, i32, i32, i64, vp, vp, i64, vp, vp, vp,
+                          vp],
         "gmq_classify_split": [vp, i32, i64, vp, vp, i64, vp, vp, vp, vp, dbl, dbl, i32, vp, vp,
                                i64, i64, vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)],
         "gmq_tree_sum": [vp, i64, vp, C.POINTER(dbl)],
@@ -144,10 +154,11 @@ def lib():
         "gmq_last_batch_info": [vp, C.POINTER(BatchInfo)],
         "gmq_eval_rule_gk": [vp, C.POINTER(Problem), i64, vp, vp, i64, vp, vp, vp, vp],
         "gmq_gk_table": [_dp],
+        "gmq_null_rule_table": [i32, _dp],
         "gmq_math_exp": [vp, i64, vp, vp],
         "gmq_math_rcp": [vp, i64, vp, vp],
         "gmq_math_cos": [vp, i64, vp, vp],
-        "gmq_probe_fma_rate": [vp, i32, i64, C.POINTER(dbl), C.POINTER(dbl)],
+        "gmq_probe_fp_rate": [vp, i32, i32, i64, C.POINTER(dbl), C.POINTER(dbl)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -302,15 +313,18 @@ class Context:
             out[name] = {"launches": int(s.launches), "regions": int(s.regions), "ms": s.ms}
         return out
 
-    def probe_fma_rate(self, precision=FP64, iters=None):
-        """Measured FMA issue rate of this GPU (lane FMAs per second) and the
-        probe launch's milliseconds; FP64 by default, FP32 with MIXED."""
+    PROBE_OPS = ("fma", "add", "mul")
+
+    def probe_fp_rate(self, precision=FP64, op="fma", iters=None):
+        """Measured issue rate of one floating-point operation on this GPU
+        (lane operations per second) and the probe launch's milliseconds;
+        FP64 by default, FP32 with MIXED; op "fma", "add" or "mul"."""
         if iters is None:
             iters = 20000 if precision == FP64 else 1_000_000
         rate = C.c_double()
         ms = C.c_double()
-        _check("gmq_probe_fma_rate", lib().gmq_probe_fma_rate(self.h, precision, iters,
-                                                              C.byref(rate), C.byref(ms)))
+        _check("gmq_probe_fp_rate", lib().gmq_probe_fp_rate(
+            self.h, precision, self.PROBE_OPS.index(op), iters, C.byref(rate), C.byref(ms)))
         return rate.value, ms.value
 
     def launch_count(self) -> int:
@@ -321,10 +335,11 @@ class Context:
     def integrate(self, family, a=None, u=None, rel_tol=1e-6, lo=None, hi=None, abs_tol=1e-16,
                   max_regions=1 << 22, init_splits=0, max_iters=0, precision=FP64,
                   classifier=VOLUME_SHARE, lanes=0, dim=None, check=True,
-                  keep_partition=False, rule=RULE_GENZ_MALIK) -> IntegrateResult:
+                  keep_partition=False, rule=RULE_GENZ_MALIK,
+                  estimator=EST_EMBEDDED) -> IntegrateResult:
         p = _ProblemHandle(family, a, u, lo, hi, dim)
         o = Options(rel_tol, abs_tol, max_regions, init_splits, max_iters, precision, classifier,
-                    lanes, KEEP_PARTITION if keep_partition else 0, rule)
+                    lanes, KEEP_PARTITION if keep_partition else 0, rule, estimator)
         r = Result()
         self._last_dim = p.s.dim
         code = lib().gmq_integrate(self.h, C.byref(p.s), C.byref(o), C.byref(r))
@@ -335,7 +350,7 @@ class Context:
 
     def integrate_batch(self, problems, rel_tols=None, max_regions=1 << 24, abs_tol=1e-16,
                         init_splits=0, max_iters=0, classifier=VOLUME_SHARE, host_loop=False,
-                        pool_regions=0, lanes=0, precision=FP64):
+                        pool_regions=0, lanes=0, precision=FP64, estimator=EST_EMBEDDED):
         """Integrate many problems in one device-resident loop.  problems:
         objects with family, dim, a, u (and optional lo, hi, rel_tol).
         max_regions is each problem's cap, pool_regions the shared pool (0:
@@ -349,7 +364,7 @@ class Context:
             rel_tols = [p.rel_tol for p in problems]
         tols = _f64(rel_tols, len(hs))
         o = Options(0.0, abs_tol, max_regions, init_splits, max_iters, precision, classifier, lanes,
-                    BATCH_HOST_LOOP if host_loop else 0)
+                    BATCH_HOST_LOOP if host_loop else 0, RULE_GENZ_MALIK, estimator)
         res = (Result * len(hs))()
         _check("gmq_integrate_batch", lib().gmq_integrate_batch(self.h, len(hs), arr, _ptr(tols),
                                                                 C.byref(o), pool_regions, res))
@@ -436,7 +451,8 @@ class Context:
             raise ValueError(f"expected a CUDA {dtype} tensor")
         return t
 
-    def eval_rule(self, family, a, u, center, halfw, lo=None, hi=None, precision=FP64, lanes=0):
+    def eval_rule(self, family, a, u, center, halfw, lo=None, hi=None, precision=FP64, lanes=0,
+                  estimator=EST_EMBEDDED):
         """center, halfw: CUDA float64 tensors [dim, n] with unit stride along
         regions.  Returns (I7, err, volfrac, axis) tensors of length n."""
         torch = self.torch
@@ -451,7 +467,7 @@ class Context:
         vf = torch.empty(n, dtype=torch.float64, device=dev)
         ax = torch.empty(n, dtype=torch.uint8, device=dev)
         _check("gmq_eval_rule", lib().gmq_eval_rule(
-            self.h, C.byref(p.s), precision, lanes, n, _dptr(center), _dptr(halfw),
+            self.h, C.byref(p.s), precision, lanes, estimator, n, _dptr(center), _dptr(halfw),
             ld, _dptr(i7), _dptr(err), _dptr(vf), _dptr(ax)))
         return i7, err, vf, ax
 
