@@ -64,10 +64,13 @@ def parse():
                     help="the d=8 workload with the embedded and the null-rule error estimate: "
                          "time, regions and true error against the closed forms per tolerance")
     ap.add_argument("--all-configs", action="store_true",
-                    help="report the other workloads (d=3, d=12 mixed, batch, gradients)")
-    ap.add_argument("--seeds-d12", type=int, default=3)
-    ap.add_argument("--grad-sets", type=int, default=32)
-    ap.add_argument("--batch-count", type=int, default=512)
+                    help="report the other workloads at full size (d=3; d=12 FP64 against "
+                         "mixed; the 4096 batched integrals; the 1024 gradient sets)")
+    ap.add_argument("--seeds-d12", type=int, default=10)
+    ap.add_argument("--grad-sets", type=int, default=1024)
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--gk", action="store_true",
+                    help="with --all-configs: also the Gauss-Kronrod rule against Genz-Malik")
     ap.add_argument("--lanes", type=int, default=1)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -96,7 +99,7 @@ RULE_FP64_INST_D8 = {0: 9006.0, 1: 11813.0, 2: 7803.0, 3: 14219.0, 4: 11011.0}
 RULE_FP64_FLOPS_D8 = {0: 15866.0, 1: 16668.0, 2: 12658.0, 3: 20277.0, 4: 17069.0}
 RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
                        "gm_math_tables.cuh", "gmq_common.cuh")
-RULE_COUNTS_SHA16 = "1eb3d21db416b97a"
+RULE_COUNTS_SHA16 = "ecca76ec2926992e"
 
 
 def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
@@ -623,10 +626,17 @@ def _closed_gauss(a, u):
 
 
 def all_configs(args):
-    """The five workloads beside the benchmark's own: d = 3 product peak,
-    d = 12 FP64 against mixed, the 4096-integral batch, and the d = 6
-    Gaussian gradients.  Prints one JSON object (a report, not the metric)."""
+    """The other workloads beside the benchmark's own, at their full sizes:
+    d = 3 product peak; d = 12 corner peak and Gaussian, FP64 against mixed
+    per tolerance with both errors against the closed forms; the 4096
+    batched integrals (FP64 and mixed, batched against one call per
+    integral, every result against its closed form); the 1024 d = 6
+    Gaussian gradient sets against the closed-form gradients; optionally the
+    Gauss-Kronrod rule against Genz-Malik.  GPU times from CUDA events.
+    Prints one JSON object per workload and a final summary object (a
+    report, not the metric)."""
     import math
+    import statistics
     import torch
     from paper_2511_01573_gb300 import autograd as AG
     from paper_2511_01573_gb300 import genz_inputs as G
@@ -644,79 +654,80 @@ def all_configs(args):
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1) / 1000.0
 
+    def emit(key, val):
+        rep[key] = val
+        print(json.dumps({key: val}), flush=True)
+
     rep = {}
-    # product peak on [0,1]^3, a = 5, u = 1/2, tol 1e-6, cap 1e5
+    # C1: product peak on [0,1]^3, a = 5, u = 1/2, tol 1e-6, cap 1e5
     p = G.product_peak_d3()
+    ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=100000)
     r, t = timed(lambda: ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=100000))
     ex = (10 * math.atan(2.5)) ** 3
-    rep["product_peak_d3"] = {"s": t, "regions": r.regions_evaluated, "sweeps": r.iterations,
-                              "status": r.status, "rel_err_vs_closed_form": abs(r.integral - ex) / ex,
-                              "error_estimate": r.error}
-    # d = 12 corner peak and Gaussian: FP64 against the mixed form
+    emit("product_peak_d3", {"s": t, "regions": r.regions_evaluated, "sweeps": r.iterations,
+                             "status": r.status, "error_estimate": r.error,
+                             "rel_err_vs_closed_form": abs(r.integral - ex) / ex})
+    # C3: d = 12 corner peak and Gaussian, FP64 against the mixed form
     rows = []
     for tol in (1e-4, 1e-5, 1e-6, 1e-7):
         for fam in (G.CORNER_PEAK, G.GAUSSIAN):
-            for s in range(1, args.seeds_d12 + 1):
-                a, u = G.seed_genz(s, fam, 12, G.GENZ_TARGET_SUM[fam])
+            for sd in range(1, args.seeds_d12 + 1):
+                a, u = G.seed_genz(sd, fam, 12, G.GENZ_TARGET_SUM[fam])
+                ex = _closed(fam, a, u)
                 r64, t64 = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=1 << 22))
                 rmx, tmx = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=1 << 22,
                                                        precision=gmq.MIXED))
-                rows.append({"family": G.FAMILY_NAMES[fam], "seed": s, "tol": tol,
+                rows.append({"family": G.FAMILY_NAMES[fam], "seed": sd, "tol": tol,
                              "fp64_s": t64, "mixed_s": tmx, "fp64_regions": r64.regions_evaluated,
                              "mixed_regions": rmx.regions_evaluated, "fp64_status": r64.status,
                              "mixed_status": rmx.status,
+                             "fp64_rel_err": abs(r64.integral - ex) / abs(ex),
+                             "mixed_rel_err": abs(rmx.integral - ex) / abs(ex),
                              "mixed_rel_diff_vs_fp64": abs(rmx.integral - r64.integral)
                              / abs(r64.integral)})
-    rep["d12_fp64_vs_mixed"] = rows
-    # 4096 integrals in one batch against one-by-one calls on a sample
-    # the first args.batch_count of the 4096 problems, batched and one by one
+    emit("d12_fp64_vs_mixed", rows)
+    # C4: the 4096 batched integrals, FP64 and mixed, batched and one by one
     probs = G.batched_problems(count=4096)[: args.batch_count]
     bcap = 1 << 22  # per problem
-    res, tb = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27))
-    info = ctx.last_batch_info()
-    seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap)
-                             for q in probs])
-    same = sum(1 for sr, br in zip(seq, res)
-               if sr.integral == br.integral and sr.regions_evaluated == br.regions_evaluated)
-    st = {}
-    for x in res:
-        st[str(x.status)] = st.get(str(x.status), 0) + 1
-    resm, tbm = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27,
-                                                  precision=gmq.MIXED))
-    infom = ctx.last_batch_info()
-    seqm, tsm = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
-                                             precision=gmq.MIXED) for q in probs])
-    rep["batch"] = {"problems": len(probs), "batched_s": tb, "sequential_s": ts,
-                    "speedup": ts / tb, "regions": sum(x.regions_evaluated for x in res),
-                    "statuses": st, "info": info, "identical_to_single_runs": same,
-                    "mixed": {"batched_s": tbm, "sequential_s": tsm, "speedup": tsm / tbm,
-                              "speedup_vs_fp64_sequential": ts / tbm,
-                              "regions": sum(x.regions_evaluated for x in resm), "info": infom,
-                              "max_rel_diff_vs_fp64": max(
-                                  abs(m.integral - f.integral) / abs(f.integral)
-                                  for m, f in zip(resm, res) if f.integral != 0.0)}}
-    # the tensor-product Gauss-Kronrod rule against Genz-Malik, d = 2..6
-    gk_rows = []
-    for fam in (G.GAUSSIAN, G.OSCILLATORY, G.C0):
-        for d in (2, 3, 4, 5, 6):
-            a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM[fam])
-            for tol in ((1e-6, 1e-9) if d <= 4 else (1e-6,)):
-                row = {"family": G.FAMILY_NAMES[fam], "d": d, "tol": tol}
-                for name, rule, cap in (("gm", gmq.RULE_GENZ_MALIK, 1 << 22),
-                                        ("gk", gmq.RULE_GAUSS_KRONROD, 1 << 18)):
-                    r, t = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=cap,
-                                                       rule=rule))
-                    row[name] = {"s": t, "regions": r.regions_evaluated,
-                                 "function_evals": r.function_evals, "status": r.status,
-                                 "integral": r.integral}
-                ref = _closed(fam, a, u)
-                for name in ("gm", "gk"):
-                    row[name]["rel_err_vs_closed_form"] = abs(row[name]["integral"] - ref) / abs(ref)
-                gk_rows.append(row)
-    rep["gauss_kronrod_vs_genz_malik"] = gk_rows
-    # gradients of the d = 6 Gaussian over frozen partitions
+    exact = [_closed(q.family, q.a, q.u) for q in probs]
+
+    def errs(res):
+        rel = [abs(x.integral - e) / abs(e) / q.rel_tol
+               for x, e, q in zip(res, exact, probs) if x.status == 0]
+        return {"converged": len(rel), "within_tol": sum(1 for v in rel if v <= 1.0),
+                "max_err_over_tol": max(rel) if rel else None,
+                "median_err_over_tol": statistics.median(rel) if rel else None}
+
+    out = {"problems": len(probs)}
+    for name, prec in (("fp64", gmq.FP64), ("mixed", gmq.MIXED)):
+        ctx.integrate_batch(probs[:16], max_regions=bcap, precision=prec)
+        res, tb = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27,
+                                                    precision=prec))
+        info = ctx.last_batch_info()
+        seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
+                                               precision=prec) for q in probs])
+        st = {}
+        for x in res:
+            st[str(x.status)] = st.get(str(x.status), 0) + 1
+        out[name] = {"batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
+                     "regions": sum(x.regions_evaluated for x in res), "statuses": st,
+                     "identical_to_single_runs": sum(
+                         1 for a, b in zip(seq, res)
+                         if a.integral == b.integral and a.regions_evaluated == b.regions_evaluated),
+                     "vs_closed_form": errs(res),
+                     "info": {k: info[k] for k in ("sweeps", "lane_sweeps", "rule_grid", "pauses",
+                                                   "evictions", "lanes_t1", "lanes_t4",
+                                                   "lanes_t32")}}
+        if name == "fp64":
+            fp64_res, fp64_seq_s = res, ts
+    out["mixed"]["speedup_vs_fp64_sequential"] = fp64_seq_s / out["mixed"]["batched_s"]
+    out["mixed"]["max_rel_diff_vs_fp64"] = max(
+        abs(m.integral - f.integral) / abs(f.integral) for m, f in zip(res, fp64_res)
+        if f.integral != 0.0)
+    emit("batch", out)
+    # C5: gradients of the d = 6 Gaussian over frozen partitions, tol 1e-8
     sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
-    errs, tf, tg = [], 0.0, 0.0
+    errs_g, errs_i, tf, tg = [], [], 0.0, 0.0
     for a, u in sets:
         at = torch.tensor(a, requires_grad=True)
         ut = torch.tensor(u, requires_grad=True)
@@ -726,84 +737,35 @@ def all_configs(args):
         tg += t2
         Iex, gex = _closed_gauss(a, u)
         g = list(at.grad.numpy()) + list(ut.grad.numpy())
-        errs.append(max(abs(x - y) for x, y in zip(g, gex)) / max(abs(y) for y in gex))
-    rep["gaussian_d6_gradients"] = {"sets": len(sets), "forward_s": tf, "adjoint_s": tg,
-                                    "max_rel_grad_err_vs_closed_form": max(errs)}
-    print(json.dumps(rep), flush=True)
-    ctx.close()
-
-
-def probe_peaks(args):
-    """The issue-rate probe (gmq_probe_fp_rate) for FP64 and FP32, each of
-    fused multiply-add, add and multiply chains, after a warm-up launch;
-    prints one JSON object with lane operations per second, lanes per clock
-    per SM at the sampled median SM clock, and the clocks."""
-    import torch
-    from paper_2511_01573_gb300 import gmq
-    ctx = gmq.Context(0)
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    out = {}
-    with ClockSampler(0) as clk:
-        for prec, name in ((gmq.FP64, "fp64"), (gmq.MIXED, "fp32")):
-            ctx.probe_fp_rate(prec, iters=2000 if prec == gmq.FP64 else 100000)
-            for op in ctx.PROBE_OPS:
-                rate, ms = max(ctx.probe_fp_rate(prec, op) for _ in range(3))
-                out[f"{name}_{op}"] = {"G_lane_ops_per_s": rate / 1e9, "ms": ms}
-    c = clk.summary()
-    mhz = c.get("sm_mhz") or 2070.0
-    for v in out.values():
-        v["lanes_per_clk_per_sm"] = v["G_lane_ops_per_s"] * 1e9 / (sms * mhz * 1e6)
-    print(json.dumps({"probe_peaks": out, "sms": sms, "clocks": c}), flush=True)
-    ctx.close()
-
-
-def estimators(args):
-    """The d = 8 workload (40 problems per tolerance, 1e-3 .. 1e-8) with the
-    embedded error estimate |I7 - I5| and with the null-rule estimate: GPU
-    time (CUDA events), regions, convergence, and the true relative error
-    against the closed forms (the largest, the median, and how many runs
-    stay within their tolerance).  Prints one JSON object."""
-    import statistics
-    import torch
-    from paper_2511_01573_gb300 import genz_inputs as G
-    from paper_2511_01573_gb300 import gmq
-    stream = torch.cuda.Stream(device=0)
-    ctx = gmq.Context(0, stream=stream)
-    exact = {}
-    rows = []
-    for tol in (1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
-        probs = G.genz_d8_problems(tols=(tol,))
-        for p in probs:
-            key = (p.family, tuple(p.a), tuple(p.u))
-            if key not in exact:
-                exact[key] = _closed(p.family, p.a, p.u)
-        for name, est in (("embedded", gmq.EST_EMBEDDED), ("null_rules", gmq.EST_NULL_RULES)):
-            for p in probs[:4]:
-                ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=CAP, estimator=est)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            res = [ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=CAP, estimator=est)
-                   for p in probs]
-            e1.record(stream)
-            torch.cuda.synchronize()
-            rel = [abs(r.integral - exact[(p.family, tuple(p.a), tuple(p.u))]) /
-                   abs(exact[(p.family, tuple(p.a), tuple(p.u))]) for p, r in zip(probs, res)]
-            by_fam = {}
-            for p, r, e in zip(probs, res, rel):
-                f = by_fam.setdefault(G.FAMILY_NAMES[p.family], {"regions": 0, "max_err_over_tol": 0.0})
-                f["regions"] += r.regions_evaluated
-                f["max_err_over_tol"] = max(f["max_err_over_tol"], e / tol)
-            rows.append({"tol": tol, "estimator": name, "s": e0.elapsed_time(e1) / 1000.0,
-                         "regions": sum(r.regions_evaluated for r in res),
-                         "converged": sum(1 for r in res if r.status == 0),
-                         "within_tol": sum(1 for e in rel if e <= tol),
-                         "max_err_over_tol": max(rel) / tol,
-                         "median_err_over_tol": statistics.median(rel) / tol,
-                         "by_family": by_fam})
-            print(json.dumps(rows[-1]), flush=True)
-    print(json.dumps({"estimators_d8": rows}), flush=True)
+        errs_g.append(max(abs(x - y) for x, y in zip(g, gex)) / max(abs(y) for y in gex))
+        errs_i.append(abs(float(I) - Iex) / abs(Iex))
+    emit("gaussian_d6_gradients", {
+        "sets": len(sets), "forward_s": tf, "adjoint_s": tg,
+        "max_rel_grad_err_vs_closed_form": max(errs_g),
+        "median_rel_grad_err_vs_closed_form": statistics.median(errs_g),
+        "max_rel_integral_err_vs_closed_form": max(errs_i)})
+    if args.gk:
+        # the tensor-product Gauss-Kronrod rule against Genz-Malik, d = 2..6
+        gk_rows = []
+        for fam in (G.GAUSSIAN, G.OSCILLATORY, G.C0):
+            for d in (2, 3, 4, 5, 6):
+                a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM[fam])
+                for tol in ((1e-6, 1e-9) if d <= 4 else (1e-6,)):
+                    row = {"family": G.FAMILY_NAMES[fam], "d": d, "tol": tol}
+                    for name, rule, cap in (("gm", gmq.RULE_GENZ_MALIK, 1 << 22),
+                                            ("gk", gmq.RULE_GAUSS_KRONROD, 1 << 18)):
+                        r, t = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=cap,
+                                                           rule=rule))
+                        row[name] = {"s": t, "regions": r.regions_evaluated,
+                                     "function_evals": r.function_evals, "status": r.status,
+                                     "integral": r.integral}
+                    ref = _closed(fam, a, u)
+                    for name in ("gm", "gk"):
+                        row[name]["rel_err_vs_closed_form"] = (
+                            abs(row[name]["integral"] - ref) / abs(ref))
+                    gk_rows.append(row)
+        emit("gauss_kronrod_vs_genz_malik", gk_rows)
+    print(json.dumps({"all_configs": rep}), flush=True)
     ctx.close()
 
 

@@ -15,11 +15,11 @@
 namespace gmq {
 
 // Shared memory of the batched mixed rule kernel: per thread the region's
-// centre and half-width (FP64) and its FP32 coordinate table, then the pair
-// tables of every dimension 2 .. dmax.
+// FP32 coordinate table, then the pair tables of every dimension 2 .. dmax
+// (the FP64 centres and half-widths the epilogue needs are read again from
+// the list).
 inline size_t batch_rule_mixed_smem(int dmax) {
-  size_t bytes = sizeof(double) * (size_t)2 * dmax * kBatchRuleBlock;
-  bytes += sizeof(float) * (size_t)kXRows * dmax * kBatchRuleBlock;
+  size_t bytes = sizeof(float) * (size_t)kXRows * dmax * kBatchRuleBlock;
   bytes += sizeof(unsigned short) * (size_t)(dmax + 1) * dmax * (dmax - 1) / 6;
   return (bytes + 15) & ~(size_t)15;
 }
@@ -29,9 +29,7 @@ __global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule_mixed(const Batc
   constexpr int RB = kBatchRuleBlock;
   extern __shared__ __align__(16) double smem[];
   const int dm = B.dmax;
-  double* cd = smem;                                    // [dm][RB]
-  double* hd = cd + dm * RB;                            // [dm][RB]
-  float* xt = reinterpret_cast<float*>(hd + dm * RB);  // [kXRows][dm][RB]
+  float* xt = reinterpret_cast<float*>(smem);  // [kXRows][dm][RB]
   unsigned short* pairs_all = reinterpret_cast<unsigned short*>(xt + kXRows * dm * RB);
   for (int e = 2; e <= dm; ++e) {
     const int np = e * (e - 1) / 2;
@@ -52,8 +50,7 @@ __global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule_mixed(const Batc
   const int32_t* rid = B.rid[cur];
   const int tid = threadIdx.x;
   auto tab = [&](int row, int j) -> float { return xt[(row * dm + j) * RB + tid]; };
-  auto cval = [&](int k) { return cd[k * RB + tid]; };
-  auto hval = [&](int k) { return hd[k * RB + tid]; };
+  const float l2 = (float)B.lam2, l3 = (float)B.lam3, l5 = (float)B.lam5;
   // this family's regions: one contiguous range (the batch is in family order)
   const long long r_lo = bs->fam_off[cur][FAM], r_hi = bs->fam_off[cur][FAM + 1];
   for (long long tile = blockIdx.x; r_lo + tile * RB < r_hi; tile += gridDim.x) {
@@ -62,18 +59,11 @@ __global__ void __launch_bounds__(kBatchRuleBlock) k_batch_rule_mixed(const Batc
     const BatchItem& it = B.items[rid[r]];
     if (it.paused) continue;  // carried over with its outputs
     const int d = it.P.d;
-    for (int k = 0; k < d; ++k) {
-      const double cv = C[(int64_t)k * B.ld + r], hv = H[(int64_t)k * B.ld + r];
-      cd[k * RB + tid] = cv;
-      hd[k * RB + tid] = hv;
-      xt[(kXC * dm + k) * RB + tid] = (float)cv;
-      xt[(kXP2 * dm + k) * RB + tid] = (float)fma(B.lam2, hv, cv);
-      xt[(kXM2 * dm + k) * RB + tid] = (float)fma(-B.lam2, hv, cv);
-      xt[(kXP3 * dm + k) * RB + tid] = (float)fma(B.lam3, hv, cv);
-      xt[(kXM3 * dm + k) * RB + tid] = (float)fma(-B.lam3, hv, cv);
-      xt[(kXP5 * dm + k) * RB + tid] = (float)fma(B.lam5, hv, cv);
-      xt[(kXM5 * dm + k) * RB + tid] = (float)fma(-B.lam5, hv, cv);
-    }
+    for (int k = 0; k < d; ++k)
+      mixed_coord_rows(C[(int64_t)k * B.ld + r], H[(int64_t)k * B.ld + r], l2, l3, l5,
+                       xt + k * RB + tid, dm * RB);
+    auto cval = [&](int k) { return C[(int64_t)k * B.ld + r]; };
+    auto hval = [&](int k) { return H[(int64_t)k * B.ld + r]; };
     RegionSums o;
     switch (d) {
       case 3: region_mixed_walk<FAM, 3>(it.Pf, tab, B.ratio, o); break;

@@ -3,11 +3,11 @@
 // mixed kernel, so both compute a region with the same operations in the
 // same order.
 //
-// Mixed form: node coordinates are FP64 values rounded to FP32 (the caller's
-// table), the integrand runs in FP32, and the class sums are FP32 with Knuth
-// TwoSum compensation, converted to FP64 before the weights; the fourth
-// differences and everything after the class sums are FP64
-// (region_finish64).
+// Mixed form: node coordinates are FP32 (the caller's table, built by
+// mixed_coord_rows), the integrand runs in FP32, and the class sums are
+// FP32 with Knuth TwoSum compensation, converted to FP64 before the
+// weights; the fourth differences and everything after the class sums are
+// FP64 (region_finish64).
 #pragma once
 
 #include "gm_region64.cuh"
@@ -15,6 +15,28 @@
 #include "gmq_families.cuh"
 
 namespace gmq {
+
+// The seven FP32 node-coordinate rows of one axis of a region (kXC, kXP2,
+// kXM2, kXP3, kXM3, kXP5, kXM5 at out[row * stride]), formed in FP32 from
+// the centre split into two FP32 parts, c = c_hi + c_lo, and the FP32
+// half-width: x = c_hi + fma(+-lambda, h, c_lo).  The offset c_lo +
+// lambda h is small and nearly exact, so x is c + lambda h rounded once to
+// FP32 up to rare one-ulp differences -- the rounding the FP32 integrand
+// sees in any case -- while the FP64 work per axis is four conversions and
+// one subtraction (the FP64 pipe issues at 1/64 of the FP32 rate).
+__device__ __forceinline__ void mixed_coord_rows(double c, double h, float l2, float l3,
+                                                 float l5, float* out, int stride) {
+  const float c_hi = __double2float_rn(c);
+  const float c_lo = __double2float_rn(__dsub_rn(c, (double)c_hi));
+  const float hf = __double2float_rn(h);
+  out[kXC * stride] = c_hi;
+  out[kXP2 * stride] = __fadd_rn(c_hi, __fmaf_rn(l2, hf, c_lo));
+  out[kXM2 * stride] = __fadd_rn(c_hi, __fmaf_rn(-l2, hf, c_lo));
+  out[kXP3 * stride] = __fadd_rn(c_hi, __fmaf_rn(l3, hf, c_lo));
+  out[kXM3 * stride] = __fadd_rn(c_hi, __fmaf_rn(-l3, hf, c_lo));
+  out[kXP5 * stride] = __fadd_rn(c_hi, __fmaf_rn(l5, hf, c_lo));
+  out[kXM5 * stride] = __fadd_rn(c_hi, __fmaf_rn(-l5, hf, c_lo));
+}
 
 // Integrand parameters in registers (compile-time dimension).
 template <int D>
@@ -34,7 +56,7 @@ __device__ __forceinline__ void region_mixed_flat(const PT& P, int d, const unsi
   const int b5 = b4 + 2 * d * (d - 1);  // first sign-pattern node
   const int N = b5 + (1 << d);
   Acc<float> S1, S2, S3, S4, S5;
-  double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
+  double f0 = 0.0, two_f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
   int kbest = 0;
   for (int i = 0; i < N; ++i) {
     int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
@@ -74,6 +96,7 @@ __device__ __forceinline__ void region_mixed_flat(const PT& P, int d, const unsi
     } else if (kind == 1) {
       S1.add(v);
       f0 = (double)v;
+      two_f0 = __dmul_rn(2.0, f0);
     } else {
       if (kind == 2)
         S2.add(v);
@@ -87,7 +110,6 @@ __device__ __forceinline__ void region_mixed_flat(const PT& P, int d, const unsi
       } else if (w == 2) {
         q2 = vd;
       } else {
-        const double two_f0 = __dmul_rn(2.0, f0);
         const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
         const double t2 = __dsub_rn(__dadd_rn(q2, vd), two_f0);
         const double Dk = fabs(__dsub_rn(t1, __dmul_rn(ratio, t2)));
@@ -109,7 +131,9 @@ __device__ __forceinline__ void region_mixed_flat(const PT& P, int d, const unsi
 }
 
 // Dimension D known at compile time (3 <= D <= 16).  The centre, axis and
-// pair nodes (classes 1-4) are read from the table in definition order; the
+// pair nodes (classes 1-4) are evaluated in definition order from the
+// centre held in registers and the one or two coordinates each node moves,
+// read from the table; the
 // 2^D sign-pattern nodes are walked in Gray-code order over a
 // register-resident node vector: consecutive patterns differ in one
 // coordinate, which moves between c_k + l5 h_k and c_k - l5 h_k by XOR-ing
@@ -134,9 +158,13 @@ __device__ __forceinline__ void region_mixed_walk(const PT& Pf, const Tab& tab, 
   const int b4 = 1 + 4 * d;
   const int b5 = b4 + 2 * d * (d - 1);
   Acc<float> S1, S2, S3, S4, S5;
-  double f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
+  double f0 = 0.0, two_f0 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0, dbest = -1.0;
   int kbest = 0, pj = 0, pk = 1, pc = 0;
-  // classes 1-4 through the table
+  // classes 1-4: the centre in registers, the one or two coordinates a node
+  // moves off the centre from the table
+  float xc[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) xc[j] = tab(kXC, j);
   for (int i = 0; i < b5; ++i) {
     int kind, k1 = -1, r1 = kXC, k2 = -1, r2 = kXC, w = 0;
     if (i == 0) {
@@ -162,14 +190,17 @@ __device__ __forceinline__ void region_mixed_walk(const PT& Pf, const Tab& tab, 
         }
       }
     }
+    const float v1 = k1 >= 0 ? tab(r1, k1) : 0.0f;
+    const float v2 = k2 >= 0 ? tab(r2, k2) : 0.0f;
     const float v = Family<FAM>::template eval<float>(rp, D, [&](int j) -> float {
-      return tab((j == k1) ? r1 : ((j == k2) ? r2 : kXC), j);
+      return (j == k1) ? v1 : ((j == k2) ? v2 : xc[j]);
     });
     if (kind == 4) {
       S4.add(v);
     } else if (kind == 1) {
       S1.add(v);
       f0 = (double)v;
+      two_f0 = __dmul_rn(2.0, f0);
     } else {
       if (kind == 2)
         S2.add(v);
@@ -183,7 +214,6 @@ __device__ __forceinline__ void region_mixed_walk(const PT& Pf, const Tab& tab, 
       } else if (w == 2) {
         q2 = vd;
       } else {
-        const double two_f0 = __dmul_rn(2.0, f0);
         const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
         const double t2 = __dsub_rn(__dadd_rn(q2, vd), two_f0);
         const double Dk = fabs(__dsub_rn(t1, __dmul_rn(ratio, t2)));

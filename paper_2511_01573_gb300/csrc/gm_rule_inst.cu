@@ -7,7 +7,7 @@
 #include "gm_batch_mixed.cuh"
 #include "gm_batch_rule64.cuh"
 #include "gm_gk.cuh"
-#include "gm_rule.cuh"
+#include "gm_rule_mixed.cuh"
 
 #ifndef GMQ_FAM
 #error "compile with -DGMQ_FAM=<family code>"

@@ -16,6 +16,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gm_adjoint.cuh"
 #include "gm_gk.cuh"
 #include "gm_rule.cuh"
@@ -108,6 +110,15 @@ struct DeviceGuard {
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// NVTX range for timeline tools (a no-op unless a tool is attached): one per
+// public call and one per sweep of the single-integral loop.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 int64_t num_nodes(int d) { return ((int64_t)1 << d) + 2 * (int64_t)d * d + 2 * (int64_t)d + 1; }
 
@@ -838,6 +849,7 @@ gmq_status gmq_seed_genz(uint64_t seed, int32_t family, int32_t dim, double targ
 
 gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_options* opt,
                          gmq_result* out) {
+  NvtxRange range("gmq_integrate");
   if (!ctx || !opt || !out) return GMQ_ERR_INVALID;
   std::memset(out, 0, sizeof(*out));
   ctx->trace.clear();
@@ -916,6 +928,10 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
   gmq_status status = GMQ_OK;
   int iters = 0;
   for (;;) {
+    char sweep_name[64];
+    std::snprintf(sweep_name, sizeof(sweep_name), "sweep %d: %lld regions", iters + 1,
+                  (long long)n);
+    NvtxRange sweep_range(sweep_name);
     const int T = choose_lanes(opt->lanes, n, d, ctx->sm_count, opt->precision);
     RuleArgs A;
     A.c = cA;
@@ -1423,6 +1439,7 @@ gmq_status gmq_last_batch_info(gmq_context* ctx, gmq_batch_info* info) {
 gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_problem* probs,
                                const double* rel_tols, const gmq_options* opt,
                                int64_t pool_regions, gmq_result* results) {
+  NvtxRange range("gmq_integrate_batch");
   if (!ctx || !opt || !results || !probs || count < 1 || count > (1 << 20) ||
       pool_regions < 0 || pool_regions > ((int64_t)1 << 31))
     return GMQ_ERR_INVALID;
@@ -1840,6 +1857,7 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
 gmq_status gmq_rule_grad(gmq_context* ctx, const gmq_problem* prob, int64_t n,
                          const double* d_center, const double* d_halfw, int64_t ld,
                          double* integral, double* grad) {
+  NvtxRange range("gmq_rule_grad");
   if (!ctx || !integral || !grad) return GMQ_ERR_INVALID;
   gmq_status vs = validate_problem(prob);
   if (vs != GMQ_OK) return vs;
