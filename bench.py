@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--no-time-to-tol", action="store_true")
     ap.add_argument("--probe-rule", default=None,
                     help="profiling probe: family codes (e.g. 0,1,2,3,4); runs the rule "
-                         "kernel 3 times per family on 2^20 random d=8 regions and exits")
+                         "kernel 3 times per family on 2^20 random regions (--dim, default 8) "
+                         "after a warm-up call, and exits")
     ap.add_argument("--probe-split", action="store_true",
                     help="profiling probe: classify + split on 2^22 random d=8 regions")
     ap.add_argument("--probe-batch", action="store_true",
@@ -72,6 +73,7 @@ def parse():
     ap.add_argument("--gk", action="store_true",
                     help="with --all-configs: also the Gauss-Kronrod rule against Genz-Malik")
     ap.add_argument("--lanes", type=int, default=1)
+    ap.add_argument("--dim", type=int, default=8, help="with --probe-rule: the dimension")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -99,12 +101,26 @@ RULE_FP64_INST_D8 = {0: 9006.0, 1: 11813.0, 2: 7803.0, 3: 14219.0, 4: 11011.0}
 RULE_FP64_FLOPS_D8 = {0: 15866.0, 1: 16668.0, 2: 12658.0, 3: 20277.0, 4: 17069.0}
 RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
                        "gm_math_tables.cuh", "gmq_common.cuh")
-RULE_COUNTS_SHA16 = "ecca76ec2926992e"
+RULE_COUNTS_SHA16 = "078ebf17042d0d86"
+
+
+# FP32 work of the mixed rule kernel (k_rule_mixed_reg, one thread per
+# region) per region at d = 12 (4409 nodes), corner peak and Gaussian (the
+# d = 12 mixed workload): FP32 lane operations, i.e. FP32 thread
+# instructions with each paired instruction (FADD2 / FMUL2 / FFMA2) counted
+# twice (sm__sass_thread_inst_executed_op_fp32_pred_on +
+# sm__sass_thread_inst_executed_ops_fadd2_fmul2_ffma2_pred_on, ncu, 2^20
+# regions; bench.py --probe-rule 2,3 --precision 1 --dim 12).  Tied to the
+# mixed kernel's sources as the FP64 counts are to the FP64 kernel's.
+MIXED_FP32_OPS_D12 = {2: 116237.0, 3: 134179.0}
+MIXED_COUNTS_SOURCES = ("gm_rule_mixed.cuh", "gm_region32.cuh", "gm_region64.cuh",
+                        "gmq_families.cuh", "gm_math_tables.cuh", "gmq_common.cuh")
+MIXED_COUNTS_SHA16 = "690bad1eef3e3b3b"
 
 
 def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
-    """First 16 hex digits of the SHA-256 of the FP64 rule kernel's sources
-    (file name, then contents, in the order given)."""
+    """First 16 hex digits of the SHA-256 of a rule kernel's sources (file
+    name, then contents, in the order given; the FP64 kernel's by default)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2511_01573_gb300", "csrc")
@@ -116,6 +132,58 @@ def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
 
 
 RULE_DRAM_BYTES_PER_REGION_D8 = 141.1
+
+
+def mixed_roofline(ctx, stream, probe32):
+    """Roofline of the mixed rule kernel on the d = 12 mixed workload's
+    families (corner peak, Gaussian): one thread per region (the register
+    walk) over 2^20 random sub-boxes of [0,1]^12, one warm-up call and three
+    event-timed launches per family on the context stream; achieved FP32
+    lane operations per second (MIXED_FP32_OPS_D12 per region) against the
+    measured FP32 issue rate probe32 (lane operations per second)."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    n, d = 1 << 20, 12
+    g = torch.Generator(device="cuda").manual_seed(12)
+    lo = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.9
+    w = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.05 + 1e-3
+    c = (lo + 0.5 * w).contiguous()
+    h = (0.5 * w).contiguous()
+    ops = secs = 0.0
+    per = {}
+    for fam in sorted(MIXED_FP32_OPS_D12):
+        a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM[fam])
+        ctx.eval_rule(fam, a, u, c[:, :256].contiguous(), h[:, :256].contiguous(), lanes=1,
+                      precision=gmq.MIXED)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(3):
+                ctx.eval_rule(fam, a, u, c, h, lanes=1, precision=gmq.MIXED)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        per[G.FAMILY_NAMES[fam]] = {"ms_per_launch": t / 3 * 1000.0, "regions_per_s": 3 * n / t,
+                                    "G_fp32_lane_ops_per_s": 3 * n * MIXED_FP32_OPS_D12[fam] / t / 1e9}
+        ops += 3 * n * MIXED_FP32_OPS_D12[fam]
+        secs += t
+    del c, h, lo, w
+    current = rule_source_fingerprint(MIXED_COUNTS_SOURCES) == MIXED_COUNTS_SHA16
+    ach = ops / secs / 1e9
+    peak = probe32 / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "G FP32 lane-ops/s",
+            "frac": ach / peak if current else None, "traffic": None,
+            "kernel": "k_rule_mixed_reg<FAM, 12> (mixed-precision rule evaluation, d = 12)",
+            "workload": "2^20 random sub-boxes of [0,1]^12, corner peak and Gaussian, "
+                        "three launches each, kernel timed alone",
+            "peak_basis": "measured: FP32 fused multiply-add chains of the issue-rate probe "
+                          "(gmq_probe_fp_rate) in this run",
+            "counts_match_source": current, "fp32_lane_ops_per_region": {
+                G.FAMILY_NAMES[f]: v for f, v in MIXED_FP32_OPS_D12.items()},
+            "by_family": per}
 
 
 def time_to_tol(ctx, stream, tol):
@@ -374,13 +442,14 @@ def cpu_baseline(args, seconds):
 
 
 def probe_rule(args):
-    """The rule kernel alone on 2^20 random sub-boxes of [0,1]^8 (about
-    150 MB of inputs and outputs, more than L2), three launches per family,
-    for ncu captures; prints the event-timed rate."""
+    """The rule kernel alone on 2^20 random sub-boxes of [0,1]^d (d = --dim,
+    default 8: about 150 MB of inputs and outputs, more than L2), one
+    warm-up call then three launches per family, for ncu captures; prints
+    the event-timed rate."""
     import torch
     from paper_2511_01573_gb300 import genz_inputs as G
     from paper_2511_01573_gb300 import gmq
-    n, d = 1 << 20, 8
+    n, d = 1 << 20, args.dim
     g = torch.Generator(device="cuda").manual_seed(1)
     lo = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.9
     w = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.05 + 1e-3
@@ -390,6 +459,9 @@ def probe_rule(args):
     ctx.profile(True)
     for fam in (int(x) for x in args.probe_rule.split(",")):
         a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM.get(fam, 2.0))
+        # warm-up on a few regions (loads the kernel's module) before the timed launches
+        ctx.eval_rule(fam, a, u, c[:, :256].contiguous(), h[:, :256].contiguous(),
+                      lanes=args.lanes, precision=args.precision)
         ctx.profile_reset()
         for _ in range(3):
             ctx.eval_rule(fam, a, u, c, h, lanes=args.lanes, precision=args.precision)
@@ -857,8 +929,10 @@ def main():
         ctx.probe_fp_rate(gmq.FP64, iters=2000)
         probe_ops = {op: max(ctx.probe_fp_rate(gmq.FP64, op)[0] for _ in range(2))
                      for op in ctx.PROBE_OPS}
+        probe32 = max(ctx.probe_fp_rate(gmq.MIXED, "fma")[0] for _ in range(2))
     probe_clocks = pclk.summary()
     probe64 = max(probe_ops.values())
+    roof_mixed = mixed_roofline(ctx, stream, probe32)
     # e2e: host wall clock through the public call (one step), with the
     # per-launch timing events off; its device time (events around the whole
     # step) against the timed steps' shows what those events cost
@@ -934,6 +1008,7 @@ def main():
         "unprofiled_step": {"ms": unprofiled_ms, "timed_ms_per_step": total_ms / args.steps,
                             "note": "the e2e step, per-launch timing events off"},
         "roofline": roof,
+        "roofline_mixed": roof_mixed,
         "e2e": {"value": e2e_regions / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": len(probs) * 4 * 8 * 8,
                 "d2h_bytes_per_step": e2e_sweeps * 80},

@@ -345,6 +345,16 @@ __device__ __forceinline__ double null_rule_estimate(const RegionSums& o, double
   return __dmul_rn(__dmul_rn(10.0, r), e1);
 }
 
+// 2 h, exactly: for normal h one more in the exponent field (integer work,
+// which keeps the FP64 pipe free), the multiplication otherwise (zero,
+// subnormal, or 2 h overflowing).
+__device__ __forceinline__ double twice_exact(double h) {
+  const int hi = __double2hiint(h);
+  const unsigned ex = ((unsigned)hi >> 20) & 0x7ffu;
+  if (ex - 1u < 2045u) return __hiloint2double(hi + (1 << 20), __double2loint(h));
+  return __dmul_rn(2.0, h);
+}
+
 // Rule values, error estimate, split axis and round-off guard of a region
 // from its class sums (one lane).  cval(k), hval(k): centre and half-width.
 // nw: the null-rule table for the null-rule estimate, or null for the
@@ -355,7 +365,7 @@ __device__ __forceinline__ void region_finish64(const RegionSums& o, int d, cons
                                                 double vol_omega, CV cval, HV hval, double* i7o,
                                                 double* erro, double* vfo, uint8_t* axo) {
   double vol = 1.0;
-  for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, __dmul_rn(2.0, hval(k)));
+  for (int k = 0; k < d; ++k) vol = __dmul_rn(vol, twice_exact(hval(k)));
   double t7 = __dmul_rn(w7[0], o.s1);
   t7 = __dadd_rn(t7, __dmul_rn(w7[1], o.s2));
   t7 = __dadd_rn(t7, __dmul_rn(w7[2], o.s3));
@@ -387,7 +397,11 @@ __device__ __forceinline__ void region_finish64(const RegionSums& o, int d, cons
   const bool bad = (hh == 0.0) || (__dsub_rn(cs, hh) == cs) || (__dadd_rn(cs, hh) == cs);
   *i7o = i7;
   *erro = nw ? null_rule_estimate(o, vol, nw) : fabs(__dsub_rn(i7, i5));
-  if (vfo) *vfo = __ddiv_rn(vol, vol_omega);
+  if (vfo) {
+    // vol / vol(Omega); a unit domain (bits of 1.0) divides by one
+    const bool unit = __double_as_longlong(vol_omega) == 0x3ff0000000000000ll;
+    *vfo = unit ? vol : __ddiv_rn(vol, vol_omega);
+  }
   *axo = (uint8_t)(ax | (bad ? 0x80 : 0));
 }
 

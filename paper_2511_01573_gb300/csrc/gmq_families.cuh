@@ -66,7 +66,8 @@ __device__ __forceinline__ double gm_rcp(double x) {
   e = fma(-x, y, 1.0);
   return fma(y, e, y);
 }
-__device__ __forceinline__ float grcp(float x) { return 1.0f / x; }
+// FP32 reciprocal: the correctly rounded 1/x (the bits of 1.0f / x)
+__device__ __forceinline__ float grcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double grcp(double x) { return gm_rcp(x); }
 __device__ __forceinline__ float gexp(float x) { return expf(x); }
 // FP64 cosine by the same table-driven scheme (J.-M. Muller, Elementary
@@ -98,7 +99,68 @@ __device__ __forceinline__ double gm_cos(double x) {
   return fma(-S, sr, fma(C, cm1, C));
 }
 __device__ __forceinline__ double gcos(double x) { return gm_cos(x); }
-__device__ __forceinline__ float gcos(float x) { return cosf(x); }
+
+// FP32 cosine of the mixed form's oscillatory integrand, by Cody and
+// Waite's reduction (W. J. Cody, W. Waite, Software Manual for the
+// Elementary Functions, 1980): x = n pi/2 + r, n the nearest integer to
+// x 2/pi, |r| <= pi/4 (up to one rounding of the quotient), with pi/2 split
+// into three FP32 parts (their sum is pi/2 to 1e-23) subtracted by fused
+// multiply-adds; cos r and sin r by their Taylor polynomials of degree 8
+// and 9 (truncated terms below 3e-8); the quadrant n mod 4 picks cos r,
+// -sin r, -cos r or sin r.  Absolute error a few units of 2^-24 for
+// |x| < 2^15; other x (and NaN) take the library cosf, outside the inlined
+// path.  gm_cosf2: the same steps on two lanes with paired instructions.
+static __device__ __noinline__ float gm_cosf_wide(float x) { return cosf(x); }
+
+constexpr float kPio2A = 0x1.921fb6p+0f, kPio2B = -0x1.777a5cp-25f, kPio2C = -0x1.ee59dap-50f;
+constexpr float kTwoOverPi = 0.636619747f;
+
+__device__ __forceinline__ float cosf_quadrant(float c, float s, int q) {
+  const float v = (q & 1) ? s : c;
+  return ((q + 1) & 2) ? -v : v;
+}
+
+__device__ __forceinline__ float gm_cosf(float x) {
+  if (!(fabsf(x) < 32768.0f)) return gm_cosf_wide(x);
+  const float n = rintf(x * kTwoOverPi);
+  float r = __fmaf_rn(-n, kPio2A, x);
+  r = __fmaf_rn(-n, kPio2B, r);
+  r = __fmaf_rn(-n, kPio2C, r);
+  const float z = r * r;
+  float c = __fmaf_rn(z, 1.0f / 40320.0f, -1.0f / 720.0f);
+  c = __fmaf_rn(c, z, 1.0f / 24.0f);
+  c = __fmaf_rn(c, z, -0.5f);
+  c = __fmaf_rn(c, z, 1.0f);
+  float sp = __fmaf_rn(z, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  sp = __fmaf_rn(sp, z, 1.0f / 120.0f);
+  sp = __fmaf_rn(sp, z, -1.0f / 6.0f);
+  const float s = __fmaf_rn(sp, z * r, r);
+  return cosf_quadrant(c, s, (int)n);
+}
+
+__device__ __forceinline__ float2 gm_cosf2(float2 x) {
+  if (!(fabsf(x.x) < 32768.0f && fabsf(x.y) < 32768.0f))
+    return make_float2(gm_cosf(x.x), gm_cosf(x.y));
+  const float2 n = make_float2(rintf(x.x * kTwoOverPi), rintf(x.y * kTwoOverPi));
+  const float2 mn = make_float2(-n.x, -n.y);
+  float2 r = __ffma2_rn(mn, make_float2(kPio2A, kPio2A), x);
+  r = __ffma2_rn(mn, make_float2(kPio2B, kPio2B), r);
+  r = __ffma2_rn(mn, make_float2(kPio2C, kPio2C), r);
+  const float2 z = __fmul2_rn(r, r);
+  float2 c = __ffma2_rn(z, make_float2(1.0f / 40320.0f, 1.0f / 40320.0f),
+                        make_float2(-1.0f / 720.0f, -1.0f / 720.0f));
+  c = __ffma2_rn(c, z, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
+  c = __ffma2_rn(c, z, make_float2(-0.5f, -0.5f));
+  c = __ffma2_rn(c, z, make_float2(1.0f, 1.0f));
+  float2 sp = __ffma2_rn(z, make_float2(1.0f / 362880.0f, 1.0f / 362880.0f),
+                         make_float2(-1.0f / 5040.0f, -1.0f / 5040.0f));
+  sp = __ffma2_rn(sp, z, make_float2(1.0f / 120.0f, 1.0f / 120.0f));
+  sp = __ffma2_rn(sp, z, make_float2(-1.0f / 6.0f, -1.0f / 6.0f));
+  const float2 s = __ffma2_rn(sp, __fmul2_rn(z, r), r);
+  return make_float2(cosf_quadrant(c.x, s.x, (int)n.x), cosf_quadrant(c.y, s.y, (int)n.y));
+}
+
+__device__ __forceinline__ float gcos(float x) { return gm_cosf(x); }
 
 // x^e for an integer exponent e >= 1 by binary powering: the low zero bits
 // of e square x, the lowest one bit starts the product, each higher bit
@@ -222,6 +284,126 @@ struct Family<GMQ_POLY_SUMSQ11> {
   }
 };
 
+// Two FP32 integrand values at once.  On this GPU a paired FP32 instruction
+// (FADD2 / FMUL2 / FFMA2, the __fadd2_rn / __fmul2_rn / __ffma2_rn
+// intrinsics) does two lanes' adds, multiplies or fused multiply-adds in one
+// issue slot, so the mixed kernels evaluate the integrand at two nodes
+// together: x(j) returns the pair of the two nodes' j-th coordinates.  Each
+// lane runs exactly the scalar eval's operations in the scalar eval's order
+// (every paired operation rounds each lane as the scalar one does; the
+// transcendental and the reciprocal run per lane), so eval2 returns the
+// bits two eval calls would.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 abs2(float2 v) { return make_float2(fabsf(v.x), fabsf(v.y)); }
+
+template <int FAM>
+struct Family2;
+
+template <>
+struct Family2<GMQ_OSCILLATORY> {
+  template <class PT, class X>
+  __device__ __forceinline__ static float2 eval2(const PT& P, int d, X x) {
+    float2 s = bc2(P.c0);
+#pragma unroll
+    for (int j = 0; j < d; ++j) s = __ffma2_rn(bc2(P.a[j]), x(j), s);
+    return gm_cosf2(s);
+  }
+};
+
+template <>
+struct Family2<GMQ_PRODUCT_PEAK> {
+  template <class PT, class X>
+  __device__ __forceinline__ static float2 eval2(const PT& P, int d, X x) {
+    float2 den = bc2(1.0f);
+#pragma unroll
+    for (int j = 0; j < d; ++j) {
+      const float2 t = __fadd2_rn(x(j), bc2(-P.u[j]));
+      den = __fmul2_rn(den, __ffma2_rn(t, t, bc2(P.b[j])));
+    }
+    return make_float2(grcp(den.x), grcp(den.y));
+  }
+};
+
+template <>
+struct Family2<GMQ_CORNER_PEAK> {
+  template <class PT, class X>
+  __device__ __forceinline__ static float2 eval2(const PT& P, int d, X x) {
+    float2 s = bc2(1.0f);
+#pragma unroll
+    for (int j = 0; j < d; ++j) s = __ffma2_rn(bc2(P.a[j]), x(j), s);
+    // s^(d+1) by the binary powering of ipow, both lanes at once
+    int e = d + 1;
+    while (!(e & 1)) {
+      s = __fmul2_rn(s, s);
+      e >>= 1;
+    }
+    float2 r = s;
+    while (e >>= 1) {
+      s = __fmul2_rn(s, s);
+      if (e & 1) r = __fmul2_rn(r, s);
+    }
+    return make_float2(grcp(r.x), grcp(r.y));
+  }
+};
+
+template <>
+struct Family2<GMQ_GAUSSIAN> {
+  template <class PT, class X>
+  __device__ __forceinline__ static float2 eval2(const PT& P, int d, X x) {
+    float2 s = bc2(0.0f);
+#pragma unroll
+    for (int j = 0; j < d; ++j) {
+      const float2 t = __fadd2_rn(x(j), bc2(-P.u[j]));
+      s = __ffma2_rn(bc2(P.b[j]), __fmul2_rn(t, t), s);
+    }
+    return make_float2(gexp(-s.x), gexp(-s.y));
+  }
+};
+
+template <>
+struct Family2<GMQ_C0> {
+  template <class PT, class X>
+  __device__ __forceinline__ static float2 eval2(const PT& P, int d, X x) {
+    float2 s = bc2(0.0f);
+#pragma unroll
+    for (int j = 0; j < d; ++j)
+      s = __ffma2_rn(bc2(P.a[j]), abs2(__fadd2_rn(x(j), bc2(-P.u[j]))), s);
+    return make_float2(gexp(-s.x), gexp(-s.y));
+  }
+};
+
+template <>
+struct Family2<GMQ_DISCONTINUOUS> {
+  template <class PT, class X>
+  __device__ __forceinline__ static float2 eval2(const PT& P, int d, X x) {
+    float2 s = bc2(0.0f);
+    bool zx = false, zy = false;
+#pragma unroll
+    for (int j = 0; j < d; ++j) {
+      const float2 xj = x(j);
+      zx = zx || (xj.x > P.u[j]);
+      zy = zy || (xj.y > P.u[j]);
+      s = __ffma2_rn(bc2(P.a[j]), xj, s);
+    }
+    return make_float2(zx ? 0.0f : gexp(s.x), zy ? 0.0f : gexp(s.y));
+  }
+};
+
+template <>
+struct Family2<GMQ_POLY_SUMSQ11> {
+  template <class PT, class X>
+  __device__ __forceinline__ static float2 eval2(const PT& P, int d, X x) {
+    float2 s = bc2(0.0f);
+#pragma unroll
+    for (int j = 0; j < d; ++j) {
+      const float2 xj = x(j);
+      s = __ffma2_rn(xj, xj, s);
+    }
+    const float2 s2 = __fmul2_rn(s, s), s4 = __fmul2_rn(s2, s2), s8 = __fmul2_rn(s4, s4);
+    return __fmul2_rn(__fmul2_rn(s8, s2), s);
+  }
+};
+
 // Class-sum accumulators: plain FP64 sums, or FP32 sums compensated with
 // Knuth's TwoSum (the rounding error of every addition is carried in c).
 template <class Real>
@@ -234,6 +416,22 @@ struct Acc<double> {
   __device__ __forceinline__ double value() const { return s; }
 };
 
+// An FP32 value as FP64, exactly, assembled from its bit pattern with
+// integer operations (the conversion instruction runs on the FP64 pipe,
+// which on this GPU issues at 1/64 of the FP32 rate): sign, exponent rebased
+// from 127 to 1023, the 23 fraction bits at the top of the 52.  Zero keeps
+// its sign; subnormal, infinite and NaN values take the conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u) {
+    const unsigned hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)f;
+}
+
 template <>
 struct Acc<float> {
   float s = 0.0f, c = 0.0f;
@@ -244,7 +442,7 @@ struct Acc<float> {
     c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, ap), __fsub_rn(v, bp)));
     s = t;
   }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  __device__ __forceinline__ double value() const { return f2d_exact(s) + f2d_exact(c); }
 };
 
 }  // namespace gmq

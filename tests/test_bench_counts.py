@@ -16,3 +16,9 @@ def test_counts_cover_the_benchmark_families():
     from paper_2511_01573_gb300 import genz_inputs as G
     for fam in G.GENZ_D8_FAMILIES:
         assert bench.RULE_FP64_INST_D8[fam] > 401 and bench.RULE_FP64_FLOPS_D8[fam] > 401
+
+
+def test_mixed_counts_belong_to_the_current_kernel_sources():
+    assert (bench.rule_source_fingerprint(bench.MIXED_COUNTS_SOURCES) ==
+            bench.MIXED_COUNTS_SHA16), (
+        "the mixed rule kernel changed since its FP32 operation counts were taken")
