@@ -776,8 +776,11 @@ def all_configs(args):
         res, tb = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27,
                                                     precision=prec))
         info = ctx.last_batch_info()
+        # one call per integral; the mixed batch runs one lane per region, so
+        # the single mixed calls that it reproduces bit for bit do too
+        lanes = 1 if prec == gmq.MIXED else 0
         seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
-                                               precision=prec) for q in probs])
+                                               precision=prec, lanes=lanes) for q in probs])
         st = {}
         for x in res:
             st[str(x.status)] = st.get(str(x.status), 0) + 1
@@ -799,20 +802,28 @@ def all_configs(args):
     emit("batch", out)
     # C5: gradients of the d = 6 Gaussian over frozen partitions, tol 1e-8
     sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
-    errs_g, errs_i, tf, tg = [], [], 0.0, 0.0
+    errs_g, errs_i, tf, tg, retried = [], [], 0.0, 0.0, 0
     for a, u in sets:
         at = torch.tensor(a, requires_grad=True)
         ut = torch.tensor(u, requires_grad=True)
-        I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx, max_regions=1 << 24))
+        try:
+            I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx,
+                                              max_regions=1 << 24))
+        except RuntimeError:
+            # the final partition outgrew 2^24 regions: again with room for 2^26
+            retried += 1
+            I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx,
+                                              max_regions=1 << 26))
         _, t2 = timed(lambda: I.backward())
         tf += t1
         tg += t2
         Iex, gex = _closed_gauss(a, u)
         g = list(at.grad.numpy()) + list(ut.grad.numpy())
         errs_g.append(max(abs(x - y) for x, y in zip(g, gex)) / max(abs(y) for y in gex))
-        errs_i.append(abs(float(I) - Iex) / abs(Iex))
+        errs_i.append(abs(float(I.detach()) - Iex) / abs(Iex))
     emit("gaussian_d6_gradients", {
         "sets": len(sets), "forward_s": tf, "adjoint_s": tg,
+        "sets_needing_2^26_regions": retried,
         "max_rel_grad_err_vs_closed_form": max(errs_g),
         "median_rel_grad_err_vs_closed_form": statistics.median(errs_g),
         "max_rel_integral_err_vs_closed_form": max(errs_i)})

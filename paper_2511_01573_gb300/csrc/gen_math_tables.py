@@ -3,11 +3,11 @@ and cosine (gmq_families.cuh, gm_exp and gm_cos), computed in decimal
 arithmetic with 60 significant digits.
 
 Method: Tang's table-driven exponential (P. T. P. Tang, ACM TOMS 15(2),
-1989).  x = (256 m + j) ln2/256 + r, |r| <= ln2/512, exp(x) = 2^m
-2^(j/256) exp(r).  The table holds 2^(j/256), j = 0..255, rounded to
-nearest; ln2/256 is split into L1 (36 significant bits) and L2 = ln2/256 -
-L1 rounded; exp(r) - 1 is the Taylor polynomial of degree 4 (its truncation
-error r^5/120 is below 3.8e-17).
+1989).  x = (2048 m + j) ln2/2048 + r, |r| <= ln2/4096, exp(x) = 2^m
+2^(j/2048) exp(r).  The table holds 2^(j/2048), j = 0..2047, rounded to
+nearest; ln2/2048 is split into L1 (36 significant bits) and L2 = ln2/2048
+- L1 rounded; exp(r) - 1 is the Taylor polynomial of degree 3 (its
+truncation error r^4/24 is below 3.5e-17).
 
 Cosine, by the same table-driven scheme (J.-M. Muller, Elementary Functions,
 ch. 6): x = n pi/128 + r, |r| <= pi/256, cos(x) = C_j cos(r) - S_j sin(r)
@@ -92,7 +92,7 @@ def split36(d: Decimal) -> float:
     return float((d * scale).to_integral_value() / scale)
 
 
-NEXP = 256  # table entries of the exponential (2^(j/NEXP))
+NEXP = 2048  # table entries of the exponential (2^(j/NEXP))
 NCOS = 256  # table entries of the cosine (cos, sin of 2 pi j/NCOS)
 
 

@@ -21,29 +21,28 @@ struct SmemParams {
 };
 
 // FP64 exponential by Tang's table-driven method (P. T. P. Tang, ACM TOMS
-// 15(2), 1989): x = (256 m + j) ln2/256 + r with |r| <= ln2/512, so exp(x) =
-// 2^m 2^(j/256) exp(r); exp(r) - 1 is its Taylor polynomial of degree 4
-// (truncation below 3.8e-17), 2^(j/256) comes from a 256-entry table and 2^m
-// is added to the exponent field.  Nine FP64 instructions (the library exp
-// measured ~16.6 in the rule kernels), within about one ulp of the exact
-// value (gm_math_tables.cuh holds the constants, computed in 60-digit
-// decimal arithmetic).  |x| >= 512 (which covers the overflow and subnormal
-// ranges) and NaN go to the library exp.
+// 15(2), 1989): x = (2048 m + j) ln2/2048 + r with |r| <= ln2/4096, so
+// exp(x) = 2^m 2^(j/2048) exp(r); exp(r) - 1 is its Taylor polynomial of
+// degree 3 (truncation below 3.5e-17), 2^(j/2048) comes from a 2048-entry
+// table (16 KB) and 2^m is added to the exponent field.  Eight FP64
+// instructions (the library exp measured ~16.6 in the rule kernels), within
+// about one ulp of the exact value (gm_math_tables.cuh holds the constants,
+// computed in 60-digit decimal arithmetic).  |x| >= 512 (which covers the
+// overflow and subnormal ranges) and NaN go to the library exp.
 __device__ __forceinline__ double gm_exp(double x) {
   // |x| < 512, tested on the high word (no FP64 compare)
   if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40800000u) return exp(x);
   const double shifter = 6755399441055744.0;  // 1.5 * 2^52: low word of t = nearest integer
   const double t = fma(x, kExpInvL, shifter);
-  const int n = __double2loint(t);            // round(x * 256 / ln2)
+  const int n = __double2loint(t);            // round(x * 2048 / ln2)
   const double nd = __dsub_rn(t, shifter);    // the same integer as a double (exact)
   double r = fma(-nd, kExpL1, x);             // exact (fused: x - n L1 fits 53 bits)
   r = fma(-nd, kExpL2, r);
-  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
-  q = fma(q, r, 0.5);
+  double q = fma(r, 1.0 / 6.0, 0.5);
   q = fma(q, r, 1.0);
   const double em1 = __dmul_rn(q, r);         // exp(r) - 1
   const double T = __ldg(&kExp2Tab[n & ((1 << kExpTabBits) - 1)]);
-  const double y = fma(T, em1, T);            // 2^(j/256) exp(r), in [2^(-1/512), 2^(511/512)]
+  const double y = fma(T, em1, T);            // 2^(j/2048) exp(r), in [2^(-1/4096), 2^(4095/4096)]
   const unsigned hi = (unsigned)__double2hiint(y) + ((unsigned)(n >> kExpTabBits) << 20);
   return __hiloint2double((int)hi, __double2loint(y));
 }
@@ -51,20 +50,20 @@ __device__ __forceinline__ double gm_exp(double x) {
 __device__ __forceinline__ double gexp(double x) { return gm_exp(x); }
 
 // FP64 reciprocal: the hardware's approximate reciprocal (PTX
-// rcp.approx.ftz.f64, relative error about 2^-23) refined by two
-// Newton-Raphson steps y <- y + y (1 - x y) (P. Markstein, IBM J. Res. Dev.
-// 34(1), 1990), each of which doubles the number of correct bits: within one
-// ulp of 1/x for 2^-120 <= |x| <= 2^120, at four FP64 FMAs.  Other inputs
-// (near the ends of the range, 0, inf, NaN) take the library's division.
+// rcp.approx.ftz.f64, relative error about 2^-23) refined by one third-order
+// step of Householder's iteration for 1/x: with e = 1 - x y (one fused
+// multiply-add, exact up to its final rounding), y (1 + e + e^2) = (1/x)(1 -
+// e^3), so the relative error drops from about 2^-23 to about 2^-69 before
+// the last rounding: within one ulp of 1/x for 2^-120 <= |x| <= 2^120, at
+// three FP64 FMAs (two Newton-Raphson steps take four).  Other inputs (near
+// the ends of the range, 0, inf, NaN) take the library's division.
 __device__ __forceinline__ double gm_rcp(double x) {
   const unsigned ex = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;  // biased exponent
   if (ex - (1023u - 120u) > 240u) return 1.0 / x;
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 // FP32 reciprocal: the correctly rounded 1/x (the bits of 1.0f / x)
 __device__ __forceinline__ float grcp(float x) { return __frcp_rn(x); }
