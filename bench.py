@@ -97,11 +97,11 @@ CAP = 1 << 24
 # again (tests/test_bench_counts.py fails until they are), and until then
 # the roofline reports no fraction.  Family codes: 0 oscillatory, 1 product
 # peak, 2 corner peak, 3 Gaussian, 4 C0.
-RULE_FP64_INST_D8 = {0: 9006.0, 1: 11813.0, 2: 7803.0, 3: 14219.0, 4: 11011.0}
-RULE_FP64_FLOPS_D8 = {0: 15866.0, 1: 16668.0, 2: 12658.0, 3: 20277.0, 4: 17069.0}
+RULE_FP64_INST_D8 = {0: 9006.0, 1: 11412.0, 2: 7402.0, 3: 13818.0, 4: 10610.0}
+RULE_FP64_FLOPS_D8 = {0: 15866.0, 1: 15866.0, 2: 11856.0, 3: 19475.0, 4: 16267.0}
 RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
                        "gm_math_tables.cuh", "gmq_common.cuh")
-RULE_COUNTS_SHA16 = "078ebf17042d0d86"
+RULE_COUNTS_SHA16 = "7a5a60d82580d2da"
 
 
 # FP32 work of the mixed rule kernel (k_rule_mixed_reg, one thread per
@@ -115,7 +115,7 @@ RULE_COUNTS_SHA16 = "078ebf17042d0d86"
 MIXED_FP32_OPS_D12 = {2: 116237.0, 3: 134179.0}
 MIXED_COUNTS_SOURCES = ("gm_rule_mixed.cuh", "gm_region32.cuh", "gm_region64.cuh",
                         "gmq_families.cuh", "gm_math_tables.cuh", "gmq_common.cuh")
-MIXED_COUNTS_SHA16 = "690bad1eef3e3b3b"
+MIXED_COUNTS_SHA16 = "b26bbce2194aedb8"
 
 
 def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
@@ -802,18 +802,26 @@ def all_configs(args):
     emit("batch", out)
     # C5: gradients of the d = 6 Gaussian over frozen partitions, tol 1e-8
     sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
-    errs_g, errs_i, tf, tg, retried = [], [], 0.0, 0.0, 0
+    errs_g, errs_i, tf, tg, t_retry = [], [], 0.0, 0.0, 0.0
+    caps = (1 << 24, 1 << 26, 1 << 28)
+    needed = {c: 0 for c in caps}
     for a, u in sets:
         at = torch.tensor(a, requires_grad=True)
         ut = torch.tensor(u, requires_grad=True)
-        try:
-            I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx,
-                                              max_regions=1 << 24))
-        except RuntimeError:
-            # the final partition outgrew 2^24 regions: again with room for 2^26
-            retried += 1
-            I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx,
-                                              max_regions=1 << 26))
+        # the final partition (retired leaves plus the last list) must fit in
+        # max_regions: sets that outgrow it run again with four times the room
+        for cap in caps:
+            w0 = time.perf_counter()
+            try:
+                I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx,
+                                                  max_regions=cap))
+                break
+            except RuntimeError:
+                torch.cuda.synchronize()
+                t_retry += time.perf_counter() - w0
+                if cap == caps[-1]:
+                    raise
+        needed[cap] += 1
         _, t2 = timed(lambda: I.backward())
         tf += t1
         tg += t2
@@ -823,7 +831,8 @@ def all_configs(args):
         errs_i.append(abs(float(I.detach()) - Iex) / abs(Iex))
     emit("gaussian_d6_gradients", {
         "sets": len(sets), "forward_s": tf, "adjoint_s": tg,
-        "sets_needing_2^26_regions": retried,
+        "attempts_without_room_s": t_retry,
+        "sets_by_partition_room": {f"2^{c.bit_length() - 1}": k for c, k in needed.items()},
         "max_rel_grad_err_vs_closed_form": max(errs_g),
         "median_rel_grad_err_vs_closed_form": statistics.median(errs_g),
         "max_rel_integral_err_vs_closed_form": max(errs_i)})
