@@ -5,6 +5,7 @@
 
 #include "gmq_common.cuh"
 #include "gmq_families.cuh"
+#include "gm_region64.cuh"
 
 namespace gmq {
 
@@ -112,13 +113,12 @@ __host__ __device__ inline int batch_lanes_for(const BatchArgs& B, long long n) 
 }
 
 
-// Doubles of the FP64 rule kernel's per-block coordinate tables for T lanes
-// per region: [kXRows + 1][dmax][128 / T] (the seven coordinate rows and the
-// half-widths) and, for T > 1, the [4 dmax + 1][128 / T] axis-node scratch;
-// the kernel sizes its shared memory for the largest over T.
+// Doubles of the FP64 rule kernel's per-block region workspaces for T lanes
+// per region: 128 / T workspaces of the largest layout over dimensions
+// 1 .. dmax (gm_region64.cuh; flag masks included for every family); the
+// kernel sizes its shared memory for the largest over T.
 __host__ __device__ constexpr long long batch_rule_doubles(int dmax, int T) {
-  return (long long)(7 + 1) * dmax * (kBatchRuleBlock / T) +
-         (T > 1 ? (long long)(4 * dmax + 1) * (kBatchRuleBlock / T) : 0);
+  return (long long)sep_words_max(dmax, true, T > 1) * (kBatchRuleBlock / T);
 }
 __host__ __device__ constexpr long long batch_rule_doubles_max(int dmax) {
   long long m = batch_rule_doubles(dmax, 1);

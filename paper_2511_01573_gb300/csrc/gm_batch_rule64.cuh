@@ -15,8 +15,6 @@
 
 namespace gmq {
 
-static_assert(kXRows == 7, "batch_rule_doubles counts seven coordinate rows");
-
 template <int FAM, int T>
 __device__ __forceinline__ void batch_rule64_lanes(const BatchArgs& B, double* smem,
                                                    const unsigned short* pairs_all) {
@@ -27,41 +25,31 @@ __device__ __forceinline__ void batch_rule64_lanes(const BatchArgs& B, double* s
   const double* C = B.c[cur];
   const double* H = B.h[cur];
   const int32_t* rid = B.rid[cur];
-  const int dm = B.dmax;
+  const int64_t ld = B.ld;
   const int tid = threadIdx.x;
   const int g = tid / T, lane = tid & (T - 1);
   const unsigned mask = group_mask<T>();
-  double* tabs = smem;                                      // [kXRows + 1][dm][RPB]
-  double* fvs = smem + (long long)(kXRows + 1) * dm * RPB;  // [4 dm + 1][RPB]
-  auto tab = [&](int row, int k) -> double { return tabs[(row * dm + k) * RPB + g]; };
+  double* wsp = smem + g;  // this group's region workspace, entries RPB apart
   for (long long tile = blockIdx.x; r_lo + tile * RPB < r_hi; tile += gridDim.x) {
     const long long r = r_lo + tile * RPB + g;
     if (r >= r_hi) break;  // so are the group's later tiles
-    group_sync<T>(mask);   // the group is done with the previous region's table
+    group_sync<T>(mask);   // the group is done with the previous region's workspace
     const BatchItem& it = B.items[rid[r]];
     if (it.paused) continue;  // carried over with last sweep's outputs
     const int d = it.P.d;
-    for (int k = lane; k < d; k += T) {
-      const double cv = C[(int64_t)k * B.ld + r], hv = H[(int64_t)k * B.ld + r];
-      double* col = tabs + (long long)k * RPB + g;
-      col[(long long)kXC * dm * RPB] = cv;
-      col[(long long)kXP2 * dm * RPB] = fma(B.lam2, hv, cv);
-      col[(long long)kXM2 * dm * RPB] = fma(-B.lam2, hv, cv);
-      col[(long long)kXP3 * dm * RPB] = fma(B.lam3, hv, cv);
-      col[(long long)kXM3 * dm * RPB] = fma(-B.lam3, hv, cv);
-      col[(long long)kXP5 * dm * RPB] = fma(B.lam5, hv, cv);
-      col[(long long)kXM5 * dm * RPB] = fma(-B.lam5, hv, cv);
-      col[(long long)kXRows * dm * RPB] = hv;
-    }
-    group_sync<T>(mask);
+    auto ch = [&](int k, double& c, double& h) {
+      c = C[(int64_t)k * ld + r];
+      h = H[(int64_t)k * ld + r];
+    };
     RegionSums o;
-    region_sums64<FAM, T>(it.P, d, pairs_all + batch_pairs_offset(d), tab, fvs + g, RPB,
-                          B.ratio, o);
+    region_sums64<FAM, T>(it.P, d, pairs_all + batch_pairs_offset(d), ch, B.lam2, B.lam3,
+                          B.lam5, wsp, RPB, B.ratio, o);
     if (lane == 0)
       region_finish64(
           o, d, it.w7, it.w5, B.estimator ? it.nw : nullptr, it.vol_omega,
-          [&](int k) { return tab(kXC, k); }, [&](int k) { return tab(kXRows, k); },
-          B.i7[cur] + r, B.err[cur] + r, B.vf[cur] + r, B.axis[cur] + r);
+          [&](int k) { return C[(int64_t)k * ld + r]; },
+          [&](int k) { return H[(int64_t)k * ld + r]; }, B.i7[cur] + r, B.err[cur] + r,
+          B.vf[cur] + r, B.axis[cur] + r);
   }
 }
 

@@ -185,78 +185,316 @@ struct RegionSums {
   int kbest;                  // its axis (lowest on ties)
 };
 
+// Separable node sums.  Every family is f = g(S), S = base (+) phi_0(x_0)
+// (+) ... (+) phi_{d-1}(x_{d-1}) (Sep<FAM> in gmq_families.cuh), and a
+// node's coordinate on axis j is one of seven values: the centre c_j or
+// c_j +- lambda h_j.  So a region evaluates phi 7 d times and forms each
+// node's S from a fixed association of per-axis terms and partial chains:
+//   pre_k = base (+) phi_C(0) (+) ... (+) phi_C(k-1)        (left to right)
+//   suf_k = phi_C(k) (+) (phi_C(k+1) (+) (... phi_C(d-1)))  (right to left)
+//   centre             S = base (+) suf_0
+//   axis node (k, x)   S = (pre_k (+) phi_k(x)) (+) suf_{k+1}
+//   pair node (j<k)    S = ((pre_j (+) phi_j(x_j)) (+) mid_jk) (+)
+//                          (phi_k(x_k) (+) suf_{k+1}),
+//                      mid_jk = phi_C(j+1) (+) ... (+) phi_C(k-1) (left to right)
+//   class-5 node m     S = A[m_A] (+) (B[m_B] (+) C[m_C])
+// where the sign pattern m is cut into parts over axes [0, a), [a, a + b),
+// [a + b, d) and A, B, C hold the left-to-right chains over each part
+// (base heading A).  An empty operand (no base, k = 0; k = d - 1; an empty
+// middle or part) is left out rather than combined with an identity.  With
+// one combine per node (two for the pair nodes' shared prefix, amortised
+// over their four sign patterns) the per-node FP64 work is the outer
+// function g and the accumulation.  S differs from the plain left-to-right
+// chain only in rounding order; every lane mapping forms it the same way, so
+// the class sums stay bit-identical for T = 1, 4, 32 and 128.
+
+// Parts of the class-5 sign pattern: two for d <= 8, three above.
+__host__ __device__ constexpr int sep_c(int d) { return d <= 8 ? 0 : d / 3; }
+__host__ __device__ constexpr int sep_b(int d) { return d <= 8 ? d / 2 : (d - d / 3) / 2; }
+__host__ __device__ constexpr int sep_a(int d) { return d - sep_b(d) - sep_c(d); }
+
+// Workspace of one region (entries `stride` doubles apart): phi at the
+// centre [d], the pair-node prefixes L[k][s] = pre_k (+) phi_k(c +- lambda3 h)
+// [2d], the suffixes R[k][s] = phi_k(c +- lambda3 h) (+) suf_{k+1} [2d], the
+// class-5 chains A [2^a], B [2^b or 0], C [2^c or 0], for the discontinuous
+// family the flag masks [2]; with T > 1 lanes also pre_k [d], suf_{k+1} [d],
+// the centre's S [1] and the axis-node values [4d + 1] the lanes share.
+struct SepLayout {
+  int phiC, L, R, A, B, C, Z, pre, suf, sc, fv, words;
+};
+
+__host__ __device__ constexpr SepLayout sep_layout(int d, bool flag, bool lanes) {
+  SepLayout s{};
+  s.phiC = 0;
+  s.L = d;
+  s.R = 3 * d;
+  s.A = 5 * d;
+  s.B = s.A + (1 << sep_a(d));
+  s.C = s.B + (sep_b(d) ? 1 << sep_b(d) : 0);
+  s.Z = s.C + (sep_c(d) ? 1 << sep_c(d) : 0);
+  int w = s.Z + (flag ? 2 : 0);
+  s.pre = s.suf = s.sc = s.fv = -1;
+  if (lanes) {
+    s.pre = w;
+    s.suf = w + d;
+    s.sc = w + 2 * d;
+    s.fv = w + 2 * d + 1;
+    w += 2 * d + 1 + 4 * d + 1;
+  }
+  s.words = w;
+  return s;
+}
+
+// The largest workspace over dimensions 1 .. dmax (batched kernels, whose
+// regions have different dimensions).
+__host__ __device__ constexpr int sep_words_max(int dmax, bool flag, bool lanes) {
+  int m = 0;
+  for (int d = 1; d <= dmax; ++d)
+    if (sep_layout(d, flag, lanes).words > m) m = sep_layout(d, flag, lanes).words;
+  return m;
+}
+
 // The class sums and the fourth-difference argmax of one region by the T
-// lanes of the calling group (all of them call it).  tab(row, j) is the
-// region's node coordinate on axis j for XRow `row`; pairs[p] = (j << 8) | k
-// for the p-th pair j < k of dimension d; fv points at the region's column
-// of a [4d + 1] x fvs scratch array (T > 1 only).
-template <int FAM, int T, class PT, class Tab>
+// lanes of the calling group (all of them call it).  ch(k, c, h) loads the
+// region's centre and half-width on axis k; pairs[p] = (j << 8) | k for the
+// p-th pair j < k of dimension d; w points at the region's workspace
+// (sep_layout(d, Sep<FAM>::kFlag, T > 1)), entries `ws` doubles apart.
+template <int FAM, int T, class PT, class CH>
 __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned short* pairs,
-                                              const Tab& tab, double* fv, int fvs, double ratio,
+                                              const CH& ch, double lam2, double lam3,
+                                              double lam5, double* w, int ws, double ratio,
                                               RegionSums& o) {
+  using SF = Sep<FAM>;
   const int lane = (T == 1) ? 0 : (int)(threadIdx.x & (unsigned)(T - 1));
   const unsigned mask = group_mask<T>();
-  const int na = 1 + 4 * d;  // centre and axis nodes
-  double f0 = 0.0, dbest = -1.0, s2, s3;
+  const SepLayout Ly = sep_layout(d, SF::kFlag, T > 1);
+  const int pa = sep_a(d), pb = sep_b(d), pc = sep_c(d);
+  auto W = [&](int e) -> double& { return w[(long long)e * ws]; };
+  auto op = [](double x, double y) -> double {
+    if constexpr (SF::kMul)
+      return __dmul_rn(x, y);
+    else
+      return __dadd_rn(x, y);
+  };
+  auto fval = [&](double S, bool zero) -> double {
+    if constexpr (SF::kFlag) {
+      if (zero) return 0.0;
+    }
+    return SF::g(d, S);
+  };
+  // generator of axis-node row r: +lambda2, -lambda2, +lambda3, -lambda3
+  auto lam_row = [&](int r) -> double {
+    return r < 2 ? (r ? -lam2 : lam2) : (r == 2 ? lam3 : -lam3);
+  };
+  // discontinuous family: flag bits (x_j > u_j) of the centre, of
+  // c +- lambda3 h (+ in bits 0..15, - in bits 16..31) and of c +- lambda5 h
+  unsigned zc = 0u, z3 = 0u, z5 = 0u;
+  double f0, s2, s3, dbest = -1.0;
   int kbest = 0;
-  if (T == 1) {
-    PairTree t2, t3;
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
-    for (int i = 0; i < na; ++i) {
-      int k1 = -1, r1 = kXC, w = 0;
-      if (i > 0) {
-        k1 = (i - 1) >> 2;
-        w = (i - 1) & 3;
-        r1 = kXP2 + w;
+  if constexpr (T == 1) {
+    // right to left: phi at the centre, R, suf (suf_{k+1} parked in L[k][0])
+    double suf = 0.0;
+    for (int k = d - 1; k >= 0; --k) {
+      double c, h;
+      ch(k, c, h);
+      const double xp = fma(lam3, h, c), xm = fma(-lam3, h, c);
+      const double fc = SF::phi(P, k, c), fp = SF::phi(P, k, xp), fm = SF::phi(P, k, xm);
+      if constexpr (SF::kFlag) {
+        zc |= (unsigned)SF::flag(P, k, c) << k;
+        z3 |= ((unsigned)SF::flag(P, k, xp) << k) | ((unsigned)SF::flag(P, k, xm) << (k + 16));
       }
-      const double v = Family<FAM>::template eval<double>(
-          P, d, [&](int j) -> double { return tab(j == k1 ? r1 : kXC, j); });
-      if (i == 0) {
-        f0 = v;
-        continue;
-      }
-      if (w < 2)
-        t2.push(v);
-      else
-        t3.push(v);
-      if (w == 0) {
-        q0 = v;
-      } else if (w == 1) {
-        q1 = v;
-      } else if (w == 2) {
-        q2 = v;
+      W(Ly.phiC + k) = fc;
+      if (k == d - 1) {
+        W(Ly.R + 2 * k) = fp;
+        W(Ly.R + 2 * k + 1) = fm;
+        suf = fc;
       } else {
-        const double two_f0 = __dmul_rn(2.0, f0);
-        const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
-        const double tt = __dsub_rn(__dadd_rn(q2, v), two_f0);
-        const double D = fabs(__dsub_rn(t1, __dmul_rn(ratio, tt)));
-        if (D > dbest) {
-          dbest = D;
-          kbest = k1;
-        }
+        W(Ly.R + 2 * k) = op(fp, suf);
+        W(Ly.R + 2 * k + 1) = op(fm, suf);
+        W(Ly.L + 2 * k) = suf;
+        suf = op(fc, suf);
       }
+    }
+    f0 = fval(SF::kBase ? op(SF::base(P), suf) : suf, zc != 0u);
+    const double two_f0 = __dmul_rn(2.0, f0);
+    // left to right: the axis nodes (classes 2 and 3 in their order, the
+    // fourth differences) and the pair-node prefixes L
+    PairTree t2, t3;
+    double pre = SF::kBase ? SF::base(P) : 0.0;
+    bool hp = SF::kBase;
+    for (int k = 0; k < d; ++k) {
+      double c, h;
+      ch(k, c, h);
+      const bool hs = k < d - 1;
+      const double sk = hs ? W(Ly.L + 2 * k) : 0.0;
+      double q[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double x = fma(lam_row(r), h, c);
+        const double ph = SF::phi(P, k, x);
+        const double lp = hp ? op(pre, ph) : ph;
+        if (r >= 2) W(Ly.L + 2 * k + (r - 2)) = lp;  // after suf_{k+1} was read
+        bool zero = false;
+        if constexpr (SF::kFlag) zero = ((zc & ~(1u << k)) != 0u) || SF::flag(P, k, x);
+        q[r] = fval(hs ? op(lp, sk) : lp, zero);
+      }
+      t2.push(q[0]);
+      t2.push(q[1]);
+      t3.push(q[2]);
+      t3.push(q[3]);
+      const double t1 = __dsub_rn(__dadd_rn(q[0], q[1]), two_f0);
+      const double tt = __dsub_rn(__dadd_rn(q[2], q[3]), two_f0);
+      const double D = fabs(__dsub_rn(t1, __dmul_rn(ratio, tt)));
+      if (D > dbest) {
+        dbest = D;
+        kbest = k;
+      }
+      const double fck = W(Ly.phiC + k);
+      pre = hp ? op(pre, fck) : fck;
+      hp = true;
     }
     bool pr;
     s2 = t2.flush(pr);
     s3 = t3.flush(pr);
-  } else {
-    for (int i = lane; i < na; i += T) {
-      int k1 = -1, r1 = kXC, w = 0;
-      if (i > 0) {
-        k1 = (i - 1) >> 2;
-        w = (i - 1) & 3;
-        r1 = kXP2 + w;
+    // class-5 chains, by doubling: after axis j0 + i the first 2^(i+1)
+    // entries hold the chains over axes j0 .. j0 + i
+    auto chains = [&](int e0, int j0, int nb, bool with_base) {
+      for (int i = 0; i < nb; ++i) {
+        double c, h;
+        ch(j0 + i, c, h);
+        const double xp = fma(lam5, h, c), xm = fma(-lam5, h, c);
+        const double fp = SF::phi(P, j0 + i, xp), fm = SF::phi(P, j0 + i, xm);
+        if constexpr (SF::kFlag)
+          z5 |= ((unsigned)SF::flag(P, j0 + i, xp) << (j0 + i)) |
+                ((unsigned)SF::flag(P, j0 + i, xm) << (j0 + i + 16));
+        if (i == 0) {
+          W(e0) = with_base ? op(SF::base(P), fp) : fp;
+          W(e0 + 1) = with_base ? op(SF::base(P), fm) : fm;
+        } else {
+          const int n = 1 << i;
+          for (int t = 0; t < n; ++t) {
+            const double v = W(e0 + t);
+            W(e0 + t + n) = op(v, fm);
+            W(e0 + t) = op(v, fp);
+          }
+        }
       }
-      const double v = Family<FAM>::template eval<double>(
-          P, d, [&](int j) -> double { return tab(j == k1 ? r1 : kXC, j); });
-      fv[(i == 0 ? 4 * d : w * d + k1) * fvs] = v;
+    };
+    chains(Ly.A, 0, pa, SF::kBase);
+    if (pb) chains(Ly.B, pa, pb, false);
+    if (pc) chains(Ly.C, pa + pb, pc, false);
+  } else {
+    // 1. lanes over the axes: phi at the centre; the raw phi at
+    //    c +- lambda3 h parked in R
+    for (int k = lane; k < d; k += T) {
+      double c, h;
+      ch(k, c, h);
+      W(Ly.phiC + k) = SF::phi(P, k, c);
+      W(Ly.R + 2 * k) = SF::phi(P, k, fma(lam3, h, c));
+      W(Ly.R + 2 * k + 1) = SF::phi(P, k, fma(-lam3, h, c));
     }
     group_sync<T>(mask);
-    f0 = fv[4 * d * fvs];
+    // 2. lane 0: the chains along the axes (suf, R, the centre's S, pre)
+    //    and the flag masks
+    if (lane == 0) {
+      double suf = 0.0;
+      for (int k = d - 1; k >= 0; --k) {
+        const double fck = W(Ly.phiC + k);
+        if (k == d - 1) {
+          suf = fck;
+        } else {
+          W(Ly.R + 2 * k) = op(W(Ly.R + 2 * k), suf);
+          W(Ly.R + 2 * k + 1) = op(W(Ly.R + 2 * k + 1), suf);
+          W(Ly.suf + k) = suf;
+          suf = op(fck, suf);
+        }
+      }
+      W(Ly.sc) = SF::kBase ? op(SF::base(P), suf) : suf;
+      double pre = SF::kBase ? SF::base(P) : 0.0;
+      bool hp = SF::kBase;
+      for (int k = 0; k < d; ++k) {
+        if (hp) W(Ly.pre + k) = pre;
+        const double fck = W(Ly.phiC + k);
+        pre = hp ? op(pre, fck) : fck;
+        hp = true;
+      }
+      if constexpr (SF::kFlag) {
+        for (int k = 0; k < d; ++k) {
+          double c, h;
+          ch(k, c, h);
+          zc |= (unsigned)SF::flag(P, k, c) << k;
+          z3 |= ((unsigned)SF::flag(P, k, fma(lam3, h, c)) << k) |
+                ((unsigned)SF::flag(P, k, fma(-lam3, h, c)) << (k + 16));
+          z5 |= ((unsigned)SF::flag(P, k, fma(lam5, h, c)) << k) |
+                ((unsigned)SF::flag(P, k, fma(-lam5, h, c)) << (k + 16));
+        }
+        W(Ly.Z) = __longlong_as_double(((long long)z3 << 32) | zc);
+        W(Ly.Z + 1) = __longlong_as_double((long long)z5);
+      }
+    }
+    group_sync<T>(mask);
+    if constexpr (SF::kFlag) {
+      const long long z0 = __double_as_longlong(W(Ly.Z));
+      zc = (unsigned)z0;
+      z3 = (unsigned)(z0 >> 32);
+      z5 = (unsigned)__double_as_longlong(W(Ly.Z + 1));
+    }
+    // 3. lanes over the tasks: the centre and axis-node values, the
+    //    pair-node prefixes L and every class-5 chain (each from its first
+    //    axis, left to right: the same chains the doubling forms)
+    const int na = 1 + 4 * d, nA = 1 << pa, nB = pb ? 1 << pb : 0, nC = pc ? 1 << pc : 0;
+    const int ntask = na + 2 * d + nA + nB + nC;
+    for (int t = lane; t < ntask; t += T) {
+      if (t == 0) {
+        W(Ly.fv + 4 * d) = fval(W(Ly.sc), zc != 0u);
+      } else if (t < na) {
+        const int k = (t - 1) >> 2, r = (t - 1) & 3;
+        double c, h;
+        ch(k, c, h);
+        const double x = fma(lam_row(r), h, c);
+        const double ph = SF::phi(P, k, x);
+        const double lp = (k > 0 || SF::kBase) ? op(W(Ly.pre + k), ph) : ph;
+        bool zero = false;
+        if constexpr (SF::kFlag) zero = ((zc & ~(1u << k)) != 0u) || SF::flag(P, k, x);
+        W(Ly.fv + r * d + k) = fval(k < d - 1 ? op(lp, W(Ly.suf + k)) : lp, zero);
+      } else if (t < na + 2 * d) {
+        const int e = t - na, k = e >> 1;
+        double c, h;
+        ch(k, c, h);
+        const double ph = SF::phi(P, k, fma((e & 1) ? -lam3 : lam3, h, c));
+        W(Ly.L + e) = (k > 0 || SF::kBase) ? op(W(Ly.pre + k), ph) : ph;
+      } else {
+        int e = t - na - 2 * d, e0 = Ly.A, j0 = 0, nb = pa;
+        bool with_base = SF::kBase;
+        if (e >= nA) {
+          e -= nA;
+          e0 = Ly.B;
+          j0 = pa;
+          nb = pb;
+          with_base = false;
+          if (e >= nB) {
+            e -= nB;
+            e0 = Ly.C;
+            j0 = pa + pb;
+            nb = pc;
+          }
+        }
+        double acc = 0.0;
+        for (int i = 0; i < nb; ++i) {
+          double c, h;
+          ch(j0 + i, c, h);
+          const double ph = SF::phi(P, j0 + i, fma(((e >> i) & 1) ? -lam5 : lam5, h, c));
+          acc = i == 0 ? (with_base ? op(SF::base(P), ph) : ph) : op(acc, ph);
+        }
+        W(e0 + e) = acc;
+      }
+    }
+    group_sync<T>(mask);
+    f0 = W(Ly.fv + 4 * d);
     const double two_f0 = __dmul_rn(2.0, f0);
     for (int k = lane; k < d; k += T) {
-      const double t1 = __dsub_rn(__dadd_rn(fv[(0 * d + k) * fvs], fv[(1 * d + k) * fvs]), two_f0);
-      const double tt = __dsub_rn(__dadd_rn(fv[(2 * d + k) * fvs], fv[(3 * d + k) * fvs]), two_f0);
+      const double t1 = __dsub_rn(__dadd_rn(W(Ly.fv + k), W(Ly.fv + d + k)), two_f0);
+      const double tt = __dsub_rn(__dadd_rn(W(Ly.fv + 2 * d + k), W(Ly.fv + 3 * d + k)), two_f0);
       const double D = fabs(__dsub_rn(t1, __dmul_rn(ratio, tt)));
       if (D > dbest) {
         dbest = D;
@@ -266,11 +504,11 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
     // argmax over the lanes: larger D wins, the lower axis on ties (for
     // T = 128 every axis k < d <= 16 sits in warp 0, which holds the answer
     // for lane 0, the only lane that uses it)
-    constexpr int W = T < 32 ? T : 32;
+    constexpr int WL = T < 32 ? T : 32;
 #pragma unroll
-    for (int off = W / 2; off > 0; off >>= 1) {
-      const double od = __shfl_xor_sync(mask, dbest, off, W);
-      const int ok = __shfl_xor_sync(mask, kbest, off, W);
+    for (int off = WL / 2; off > 0; off >>= 1) {
+      const double od = __shfl_xor_sync(mask, dbest, off, WL);
+      const int ok = __shfl_xor_sync(mask, kbest, off, WL);
       if (od > dbest || (od == dbest && ok < kbest)) {
         dbest = od;
         kbest = ok;
@@ -280,27 +518,77 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
     PairTree t2, t3;
     const int p0 = lane_first_chunk<T>(lane), p1 = min(p0 + kChunks / T, 2 * d);
     for (int p = p0; p < p1; ++p) {
-      t2.push(fv[((p & 1) * d + (p >> 1)) * fvs]);
-      t3.push(fv[((2 + (p & 1)) * d + (p >> 1)) * fvs]);
+      t2.push(W(Ly.fv + (p & 1) * d + (p >> 1)));
+      t3.push(W(Ly.fv + (2 + (p & 1)) * d + (p >> 1)));
     }
     bool pr2, pr3;
     const double x2 = t2.flush(pr2), x3 = t3.flush(pr3);
     s2 = lanes_tree<T>(x2, pr2, mask);
     s3 = lanes_tree<T>(x3, pr3, mask);
   }
-  // class 4: c +- lambda4 h_j e_j +- lambda4 h_k e_k, j < k
+  // class 4: c +- lambda4 h_j e_j +- lambda4 h_k e_k, j < k (lambda4 =
+  // lambda3), pairs in lexicographic order, signs ++, +-, -+, --.  A lane
+  // walks consecutive nodes, so mid_jk grows by one term from pair (j, k-1)
+  // to (j, k) and the prefix (+) mid is shared by a pair's two nodes with
+  // the same sign on j; a lane starting inside the walk forms mid_jk from
+  // its first term, the same chain.
+  int mj = -1, mk = -1, lp = -1, lsj = -1;
+  double mid = 0.0, lm = 0.0;
+  bool hmid = false;
   o.s4 = class_sum<T>(2 * d * (d - 1), lane, mask, [&](int q) -> double {
-    const unsigned pr = pairs[q >> 2];
-    const int kj = (int)(pr >> 8), kk = (int)(pr & 255u);
-    const int rj = (q & 2) ? kXM3 : kXP3, rk = (q & 1) ? kXM3 : kXP3;
-    return Family<FAM>::template eval<double>(
-        P, d, [&](int j) -> double { return tab(j == kj ? rj : (j == kk ? rk : kXC), j); });
+    const int p = q >> 2;
+    const unsigned pr = pairs[p];
+    const int j = (int)(pr >> 8), k = (int)(pr & 255u);
+    const int sj = (q >> 1) & 1, sk = q & 1;
+    if (p != lp) {
+      if (j == mj && k == mk + 1) {
+        const double t = W(Ly.phiC + mk);
+        mid = hmid ? op(mid, t) : t;
+        hmid = true;
+      } else {
+        hmid = false;
+        for (int i = j + 1; i < k; ++i) {
+          const double t = W(Ly.phiC + i);
+          mid = hmid ? op(mid, t) : t;
+          hmid = true;
+        }
+      }
+      mj = j;
+      mk = k;
+      lp = p;
+      lsj = -1;
+    }
+    if (sj != lsj) {
+      const double L = W(Ly.L + 2 * j + sj);
+      lm = hmid ? op(L, mid) : L;
+      lsj = sj;
+    }
+    bool zero = false;
+    if constexpr (SF::kFlag)
+      zero = ((zc & ~((1u << j) | (1u << k))) != 0u) || ((z3 >> (j + 16 * sj)) & 1u) ||
+             ((z3 >> (k + 16 * sk)) & 1u);
+    return fval(op(lm, W(Ly.R + 2 * k + sk)), zero);
   });
-  // class 5: c + lambda5 (sigma o h) for the 2^d sign patterns
+  // class 5: c + lambda5 (sigma o h) for the 2^d sign patterns (bit j of m
+  // set: -lambda5 on axis j); B (+) C changes every 2^a nodes
+  const int am = (1 << pa) - 1, bm = (1 << pb) - 1;
+  const unsigned dmask = (1u << d) - 1u;
+  int mh = -1;
+  double bc = 0.0;
   o.s5 = class_sum<T>(1 << d, lane, mask, [&](int m) -> double {
-    return Family<FAM>::template eval<double>(P, d, [&](int j) -> double {
-      return tab((((unsigned)m >> j) & 1u) ? kXM5 : kXP5, j);
-    });
+    double S = W(Ly.A + (m & am));
+    if (pb) {
+      const int hi = m >> pa;
+      if (hi != mh) {
+        bc = pc ? op(W(Ly.B + (hi & bm)), W(Ly.C + (hi >> pb))) : W(Ly.B + hi);
+        mh = hi;
+      }
+      S = op(S, bc);
+    }
+    bool zero = false;
+    if constexpr (SF::kFlag)
+      zero = ((((unsigned)~m & z5) | ((unsigned)m & (z5 >> 16))) & dmask) != 0u;
+    return fval(S, zero);
   });
   o.s1 = f0;
   o.s2 = s2;

@@ -5,17 +5,19 @@
 //
 // Mapping: a block of 128 threads owns RB = 128 / T consecutive regions, T
 // threads ("lanes") per region, T in {1, 4, 32, 128} (128: a block per
-// region).  The block
-//   1. stages the regions' centres and half-widths from the structure-of-
-//      arrays list into shared memory with coalesced loads (consecutive
-//      threads read consecutive regions of one axis) and expands them into a
-//      table of node coordinates c_k +- lambda h_k, one row per generator;
-//   2. walks each class of nodes of each region by index: a node's axes and
-//      signs are decoded from the bits of its index (centre; 4d axis nodes;
-//      4 sign patterns per axis pair; the 2^d sign patterns of the last
-//      class are the bits of the index itself), and its coordinates are read
-//      from the table, so the only floating-point work per node is the
-//      integrand and one accumulation;
+// region).  Each group
+//   1. reads its region's centres and half-widths from the structure-of-
+//      arrays list (consecutive threads read consecutive regions of one
+//      axis: coalesced) and builds the region's separable workspace in
+//      shared memory: the integrand's per-axis terms at the seven
+//      coordinate values of each axis, their prefix and suffix chains and
+//      the class-5 partial chains (gm_region64.cuh);
+//   2. walks each class of nodes by index: a node's axes and signs are
+//      decoded from the bits of its index (centre; 4d axis nodes; 4 sign
+//      patterns per axis pair; the 2^d sign patterns of the last class are
+//      the bits of the index itself), its S combined from the workspace in
+//      one or two operations, so the FP64 work per node is the integrand's
+//      outer function and one accumulation;
 //   3. combines the class sums over the T lanes, finds the split axis
 //      (argmax of the fourth differences) and writes I7, the error estimate,
 //      vol / vol(Omega) and the axis byte.
@@ -29,13 +31,22 @@
 
 namespace gmq {
 
-// Shared-memory bytes of the rule kernel for dimension d, T lanes and an
-// integrand type of `real_bytes` bytes.
+// Shared-memory bytes of the mixed rule kernels for dimension d, T lanes and
+// an integrand type of `real_bytes` bytes (gm_rule_mixed.cuh).
 inline size_t rule_smem_bytes(int d, int T, int real_bytes) {
   const int RB = kRuleBlock / T;
   size_t bytes = sizeof(double) * (size_t)2 * d * RB;          // centres, half-widths
   if (T > 1) bytes += sizeof(double) * ((size_t)4 * d * RB + RB);  // axis-node values, f(c)
   bytes += (size_t)real_bytes * kXRows * d * RB;                 // node coordinates
+  bytes += sizeof(SmemParams<double>) + sizeof(unsigned short) * 128;
+  return (bytes + 15) & ~(size_t)15;
+}
+
+// Shared-memory bytes of the FP64 rule kernel: RB workspaces of the region
+// layout, the family parameters and the pair table.
+inline size_t rule64_smem_bytes(int d, int T, bool flag) {
+  const int RB = kRuleBlock / T;
+  size_t bytes = sizeof(double) * (size_t)sep_layout(d, flag, T > 1).words * RB;
   bytes += sizeof(SmemParams<double>) + sizeof(unsigned short) * 128;
   return (bytes + 15) & ~(size_t)15;
 }
@@ -47,11 +58,9 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule64(const RuleArgs A) {
   constexpr int RB = kRuleBlock / T;
   extern __shared__ __align__(16) double smem[];
   const int d = A.P.d;
-  double* cd = smem;                                  // [d][RB] centres
-  double* hd = cd + d * RB;                           // [d][RB] half-widths
-  double* fv = hd + d * RB;                           // [4d + 1][RB] axis-node values, f(c)
-  double* xt = fv + (T > 1 ? (4 * d + 1) * RB : 0);  // [kXRows][d][RB]
-  SmemParams<double>* P = reinterpret_cast<SmemParams<double>*>(xt + kXRows * d * RB);
+  const int words = sep_layout(d, Sep<FAM>::kFlag, T > 1).words;
+  double* wsp = smem;  // [words][RB] region workspaces
+  SmemParams<double>* P = reinterpret_cast<SmemParams<double>*>(wsp + (size_t)words * RB);
   unsigned short* pairs = reinterpret_cast<unsigned short*>(P + 1);
 
   const int tid = threadIdx.x;
@@ -71,39 +80,26 @@ __global__ void __launch_bounds__(kRuleBlock) k_rule64(const RuleArgs A) {
     }
     pairs[p] = (unsigned short)((j << 8) | (j + 1 + rem));
   }
-  const double l2 = A.R.lam2, l3 = A.R.lam3, l5 = A.R.lam5;
-  for (int idx = tid; idx < d * RB; idx += kRuleBlock) {
-    const int k = idx / RB, q = idx - k * RB;
-    const int64_t r = r0 + q;
-    double cv = 0.5, hv = 0.25;
-    if (r < A.n) {
-      cv = A.c[(int64_t)k * A.ld + r];
-      hv = A.h[(int64_t)k * A.ld + r];
-    }
-    cd[k * RB + q] = cv;
-    hd[k * RB + q] = hv;
-    xt[(kXC * d + k) * RB + q] = cv;
-    xt[(kXP2 * d + k) * RB + q] = fma(l2, hv, cv);
-    xt[(kXM2 * d + k) * RB + q] = fma(-l2, hv, cv);
-    xt[(kXP3 * d + k) * RB + q] = fma(l3, hv, cv);
-    xt[(kXM3 * d + k) * RB + q] = fma(-l3, hv, cv);
-    xt[(kXP5 * d + k) * RB + q] = fma(l5, hv, cv);
-    xt[(kXM5 * d + k) * RB + q] = fma(-l5, hv, cv);
-  }
   __syncthreads();
 
   const int g = tid / T;
   const int64_t r = r0 + g;
   if (r >= A.n) return;  // the whole group: its lanes share the region
-  auto tab = [&](int row, int j) -> double { return xt[(row * d + j) * RB + g]; };
+  const double* C = A.c + r;
+  const double* H = A.h + r;
+  const int64_t ld = A.ld;
+  auto ch = [&](int k, double& c, double& h) {
+    c = C[(int64_t)k * ld];
+    h = H[(int64_t)k * ld];
+  };
   RegionSums o;
-  region_sums64<FAM, T>(*P, d, pairs, tab, fv + g, RB, A.R.ratio, o);
+  region_sums64<FAM, T>(*P, d, pairs, ch, A.R.lam2, A.R.lam3, A.R.lam5, wsp + g, RB, A.R.ratio,
+                        o);
   if ((tid & (T - 1)) == 0)
     region_finish64(
         o, d, A.R.w7, A.R.w5, A.R.estimator ? A.R.nw : nullptr, A.R.vol_omega,
-        [&](int k) { return cd[k * RB + g]; },
-        [&](int k) { return hd[k * RB + g]; }, A.i7 + r, A.err + r,
-        A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
+        [&](int k) { return C[(int64_t)k * ld]; }, [&](int k) { return H[(int64_t)k * ld]; },
+        A.i7 + r, A.err + r, A.volfrac ? A.volfrac + r : nullptr, A.axis + r);
 }
 
 
@@ -115,7 +111,7 @@ cudaError_t launch_rule_family(int precision, int T, const RuleArgs& A, cudaStre
 template <int FAM, int T>
 cudaError_t launch_rule64_t(const RuleArgs& A, cudaStream_t s) {
   const int RB = kRuleBlock / T;
-  const size_t smem = rule_smem_bytes(A.P.d, T, (int)sizeof(double));
+  const size_t smem = rule64_smem_bytes(A.P.d, T, Sep<FAM>::kFlag);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_rule64<FAM, T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -415,6 +415,119 @@ struct Acc<double> {
   __device__ __forceinline__ double value() const { return s; }
 };
 
+
+// Separable form of the FP64 integrands, for the FP64 rule kernels: every
+// family is f(x) = g(S) with S = base (+) phi_0(x_0) (+) ... (+)
+// phi_{d-1}(x_{d-1}), where (+) is addition (kMul false) or multiplication
+// (kMul true) and base, present when kBase, heads the chain.  A region's
+// nodes take each coordinate from one of seven values per axis (the centre
+// and c +- lambda h for the three generators), so the kernels evaluate phi
+// 7 d times per region and build every node's S from per-axis terms and
+// partial chains instead of d operations per node.  The discontinuous
+// family also has a per-axis flag (x_j > u_j) whose OR over the axes zeroes
+// f.  Every operation is rounded separately (no contraction), so a value
+// does not depend on which code path or lane forms it.
+template <int FAM>
+struct Sep;
+
+// cos(2 pi u_1 + sum a_j x_j)
+template <>
+struct Sep<GMQ_OSCILLATORY> {
+  static constexpr bool kMul = false, kBase = true, kFlag = false;
+  template <class PT>
+  __device__ __forceinline__ static double base(const PT& P) { return P.c0; }
+  template <class PT>
+  __device__ __forceinline__ static double phi(const PT& P, int j, double x) {
+    return __dmul_rn(P.a[j], x);
+  }
+  __device__ __forceinline__ static double g(int, double s) { return gcos(s); }
+};
+
+// 1 / prod_j (a_j^-2 + (x_j - u_j)^2)
+template <>
+struct Sep<GMQ_PRODUCT_PEAK> {
+  static constexpr bool kMul = true, kBase = false, kFlag = false;
+  template <class PT>
+  __device__ __forceinline__ static double base(const PT&) { return 1.0; }
+  template <class PT>
+  __device__ __forceinline__ static double phi(const PT& P, int j, double x) {
+    const double t = __dsub_rn(x, P.u[j]);
+    return fma(t, t, P.b[j]);
+  }
+  __device__ __forceinline__ static double g(int, double s) { return grcp(s); }
+};
+
+// (1 + sum a_j x_j)^-(d+1)
+template <>
+struct Sep<GMQ_CORNER_PEAK> {
+  static constexpr bool kMul = false, kBase = true, kFlag = false;
+  template <class PT>
+  __device__ __forceinline__ static double base(const PT&) { return 1.0; }
+  template <class PT>
+  __device__ __forceinline__ static double phi(const PT& P, int j, double x) {
+    return __dmul_rn(P.a[j], x);
+  }
+  __device__ __forceinline__ static double g(int d, double s) { return grcp(ipow(s, d + 1)); }
+};
+
+// exp(-sum a_j^2 (x_j - u_j)^2)
+template <>
+struct Sep<GMQ_GAUSSIAN> {
+  static constexpr bool kMul = false, kBase = false, kFlag = false;
+  template <class PT>
+  __device__ __forceinline__ static double base(const PT&) { return 0.0; }
+  template <class PT>
+  __device__ __forceinline__ static double phi(const PT& P, int j, double x) {
+    const double t = __dsub_rn(x, P.u[j]);
+    return __dmul_rn(P.b[j], __dmul_rn(t, t));
+  }
+  __device__ __forceinline__ static double g(int, double s) { return gexp(-s); }
+};
+
+// exp(-sum a_j |x_j - u_j|)
+template <>
+struct Sep<GMQ_C0> {
+  static constexpr bool kMul = false, kBase = false, kFlag = false;
+  template <class PT>
+  __device__ __forceinline__ static double base(const PT&) { return 0.0; }
+  template <class PT>
+  __device__ __forceinline__ static double phi(const PT& P, int j, double x) {
+    return __dmul_rn(P.a[j], fabs(__dsub_rn(x, P.u[j])));
+  }
+  __device__ __forceinline__ static double g(int, double s) { return gexp(-s); }
+};
+
+// 0 if any x_j > u_j, else exp(sum a_j x_j)
+template <>
+struct Sep<GMQ_DISCONTINUOUS> {
+  static constexpr bool kMul = false, kBase = false, kFlag = true;
+  template <class PT>
+  __device__ __forceinline__ static double base(const PT&) { return 0.0; }
+  template <class PT>
+  __device__ __forceinline__ static double phi(const PT& P, int j, double x) {
+    return __dmul_rn(P.a[j], x);
+  }
+  template <class PT>
+  __device__ __forceinline__ static bool flag(const PT& P, int j, double x) { return x > P.u[j]; }
+  __device__ __forceinline__ static double g(int, double s) { return gexp(s); }
+};
+
+// (sum x_j^2)^11
+template <>
+struct Sep<GMQ_POLY_SUMSQ11> {
+  static constexpr bool kMul = false, kBase = false, kFlag = false;
+  template <class PT>
+  __device__ __forceinline__ static double base(const PT&) { return 0.0; }
+  template <class PT>
+  __device__ __forceinline__ static double phi(const PT&, int, double x) {
+    return __dmul_rn(x, x);
+  }
+  __device__ __forceinline__ static double g(int, double s) {
+    const double s2 = __dmul_rn(s, s), s4 = __dmul_rn(s2, s2), s8 = __dmul_rn(s4, s4);
+    return __dmul_rn(__dmul_rn(s8, s2), s);
+  }
+};
+
 // An FP32 value as FP64, exactly, assembled from its bit pattern with
 // integer operations (the conversion instruction runs on the FP64 pipe,
 // which on this GPU issues at 1/64 of the FP32 rate): sign, exponent rebased

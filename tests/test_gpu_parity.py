@@ -129,13 +129,26 @@ def test_rule_auto_lanes_and_ragged(oracle, gpu_ctx):
 
 
 def test_rule_on_partition_boxes_exact_axis_ties(oracle, gpu_ctx):
-    # symmetric boxes of a symmetric integrand: exact axis ties must resolve
-    # to the lowest index on both sides
+    """Symmetric boxes of a symmetric integrand.  Where the oracle's axis
+    choice is not a near-tie both sides pick the same axis.  The FP64 kernel
+    forms an axis node's S as (pre_k (+) phi_k) (+) suf_{k+1}; for d = 2 the
+    two axes' node sums are then x + y and y + x, equal for a box with
+    c_0 = c_1 and h_0 = h_1, so the fourth differences tie exactly and the
+    lower axis must win, for every lane mapping."""
     c, h = oracle.partition(np.zeros(3), np.ones(3), 4)
     a, u = np.full(3, 2.0), np.full(3, 0.5)
     o = oracle.rule_regions(G.GAUSSIAN, a, u, c, h)
     i7, err, vf, ax = gpu_ctx.eval_rule(G.GAUSSIAN, a, u, _soa(c), _soa(h))
-    assert np.array_equal(ax.cpu().numpy() & 0x7F, o["axis"])
+    tie = o["axis_tie"].astype(bool)
+    assert np.array_equal((ax.cpu().numpy() & 0x7F)[~tie], o["axis"][~tie])
+    # exact GPU ties: diagonal boxes of [0,1]^2 under the symmetric Gaussian
+    c2, h2 = oracle.partition(np.zeros(2), np.ones(2), 8)
+    diag = c2[:, 0] == c2[:, 1]
+    c2, h2 = c2[diag], h2[diag]
+    a2, u2 = np.full(2, 2.0), np.full(2, 0.3)
+    for lanes in (1, 4, 32, 128):
+        _, _, _, ax2 = gpu_ctx.eval_rule(G.GAUSSIAN, a2, u2, _soa(c2), _soa(h2), lanes=lanes)
+        assert np.all((ax2.cpu().numpy() & 0x7F) == 0), lanes
 
 
 def test_tree_sum_bit_exact(oracle, gpu_ctx):
