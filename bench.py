@@ -101,7 +101,7 @@ RULE_FP64_INST_D8 = {0: 6465.0, 1: 2524.0, 2: 4861.0, 3: 5002.0, 4: 4930.0}
 RULE_FP64_FLOPS_D8 = {0: 10133.0, 1: 3858.0, 2: 6123.0, 3: 7467.0, 4: 7395.0}
 RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
                        "gm_math_tables.cuh", "gmq_common.cuh")
-RULE_COUNTS_SHA16 = "eb9c28e361bbbafa"
+RULE_COUNTS_SHA16 = "12d05f8ab8086fe6"
 
 
 # FP32 work of the mixed rule kernel (k_rule_mixed_reg, one thread per
@@ -131,7 +131,7 @@ def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
     return h.hexdigest()[:16]
 
 
-RULE_DRAM_BYTES_PER_REGION_D8 = 142.6
+RULE_DRAM_BYTES_PER_REGION_D8 = 143.0
 
 
 def mixed_roofline(ctx, stream, probe32):
@@ -184,6 +184,51 @@ def mixed_roofline(ctx, stream, probe32):
             "counts_match_source": current, "fp32_lane_ops_per_region": {
                 G.FAMILY_NAMES[f]: v for f, v in MIXED_FP32_OPS_D12.items()},
             "by_family": per}
+
+
+def eval_modes(ctx, stream):
+    """The FP64 rule kernel's two ways of evaluating f at the nodes
+    (gmq_set_eval_mode) on the benchmark's families at d = 8: one thread per
+    region over 2^20 random sub-boxes of [0,1]^8, one warm-up call and three
+    event-timed launches per family and mode on the context stream.  The
+    default forms each node's S from per-axis terms (separable); node-wise
+    evaluates f from every node's coordinates, as an integrand without that
+    form would be.  Both evaluate g at every node."""
+    import torch
+    from paper_2511_01573_gb300 import genz_inputs as G
+    from paper_2511_01573_gb300 import gmq
+    n, d = 1 << 20, 8
+    g = torch.Generator(device="cuda").manual_seed(8)
+    lo = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.9
+    w = torch.rand((d, n), dtype=torch.float64, device="cuda", generator=g) * 0.05 + 1e-3
+    c = (lo + 0.5 * w).contiguous()
+    h = (0.5 * w).contiguous()
+    out = {}
+    for name, mode in (("separable", gmq.EVAL_SEPARABLE), ("nodewise", gmq.EVAL_NODEWISE)):
+        ctx.set_eval_mode(mode)
+        per = {}
+        for fam in G.GENZ_D8_FAMILIES:
+            a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM[fam])
+            ctx.eval_rule(fam, a, u, c[:, :256].contiguous(), h[:, :256].contiguous(), lanes=1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(3):
+                    ctx.eval_rule(fam, a, u, c, h, lanes=1)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1000.0
+            per[G.FAMILY_NAMES[fam]] = {"ms_per_launch": t / 3 * 1000.0, "regions_per_s": 3 * n / t}
+        out[name] = per
+    ctx.set_eval_mode(gmq.EVAL_SEPARABLE)
+    out["separable_over_nodewise"] = {
+        f: out["nodewise"][f]["ms_per_launch"] / out["separable"][f]["ms_per_launch"]
+        for f in out["separable"]}
+    out["workload"] = "2^20 random sub-boxes of [0,1]^8, one thread per region, kernel timed alone"
+    del c, h, lo, w
+    return out
 
 
 def time_to_tol(ctx, stream, tol):
@@ -792,7 +837,8 @@ def all_configs(args):
                      "vs_closed_form": errs(res),
                      "info": {k: info[k] for k in ("sweeps", "lane_sweeps", "rule_grid", "pauses",
                                                    "evictions", "lanes_t1", "lanes_t4",
-                                                   "lanes_t32")}}
+                                                   "lanes_t32", "rule_regions",
+                                                   "carried_regions", "list_regions")}}
         if name == "fp64":
             fp64_res, fp64_seq_s = res, ts
     out["mixed"]["speedup_vs_fp64_sequential"] = fp64_seq_s / out["mixed"]["batched_s"]
@@ -953,6 +999,7 @@ def main():
     probe_clocks = pclk.summary()
     probe64 = max(probe_ops.values())
     roof_mixed = mixed_roofline(ctx, stream, probe32)
+    modes = eval_modes(ctx, stream)
     # e2e: host wall clock through the public call (one step), with the
     # per-launch timing events off; its device time (events around the whole
     # step) against the timed steps' shows what those events cost
@@ -1029,6 +1076,7 @@ def main():
                             "note": "the e2e step, per-launch timing events off"},
         "roofline": roof,
         "roofline_mixed": roof_mixed,
+        "rule_eval_modes": modes,
         "e2e": {"value": e2e_regions / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": len(probs) * 4 * 8 * 8,
                 "d2h_bytes_per_step": e2e_sweeps * 80},

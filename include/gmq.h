@@ -195,6 +195,27 @@ gmq_status gmq_set_stream(gmq_context *ctx, void *cuda_stream);
  * (see gmq_pool_bytes).  Passing NULL returns to library-owned memory. */
 gmq_status gmq_set_pool(gmq_context *ctx, void *dev_ptr, size_t bytes);
 
+/* How the FP64 Genz-Malik kernels (gmq_integrate and gmq_eval_rule with
+ * GMQ_FP64) evaluate the integrand at a region's nodes (paper Sec. 2: the
+ * rule applies f at every node).  Every built-in family is f = g(S), S a
+ * chain of per-axis terms phi_j(x_j) combined by + (by * for the product
+ * peak), and a node takes each coordinate from one of seven values per axis:
+ *   GMQ_EVAL_SEPARABLE (default): phi at the 7d coordinate values once per
+ *     region; each node's S from one or two combines of per-axis terms and
+ *     partial chains; g at every node;
+ *   GMQ_EVAL_NODEWISE: f from each node's coordinates (d operations for S,
+ *     then g), as an integrand without that form would be evaluated.
+ * Both give every lane mapping the same bits; they differ from each other
+ * only in the rounding order of S.  The mixed precision, the Gauss-Kronrod
+ * rule, the batched form and the adjoint kernel do not depend on it. */
+typedef enum gmq_eval_mode {
+  GMQ_EVAL_SEPARABLE = 0,
+  GMQ_EVAL_NODEWISE = 1
+} gmq_eval_mode;
+
+/* Set the context's gmq_eval_mode (GMQ_ERR_INVALID for another value). */
+gmq_status gmq_set_eval_mode(gmq_context *ctx, int32_t mode);
+
 /* Device bytes the region pool needs for dimension dim, max_regions and
  * gmq_options.flags (GMQ_KEEP_PARTITION adds the final-partition list). */
 gmq_status gmq_pool_bytes(int32_t dim, int64_t max_regions, int32_t flags,
@@ -248,6 +269,12 @@ typedef struct gmq_batch_info {
   int32_t lane_sweeps[4]; /* sweeps run with 1, 4, 32 and 128 lanes        */
   int64_t tune_n[5];    /* list lengths the autotuner timed (0 if unused)   */
   double tune_ms[5][4]; /* rule-kernel time per length and mapping 1/4/32/128 */
+  int64_t rule_regions;    /* regions the rule kernels evaluated, including
+                              work that evictions later dropped             */
+  int64_t carried_regions; /* regions of paused problems carried over
+                              unchanged (copied, not evaluated)             */
+  int64_t list_regions;    /* sum over sweeps of the list length (the work
+                              of the per-sweep sums, classify and split)    */
 } gmq_batch_info;
 
 /* Many independent integrals in one device-resident loop (no counterpart in

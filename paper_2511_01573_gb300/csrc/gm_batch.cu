@@ -327,6 +327,10 @@ __global__ void __launch_bounds__(kSegBlock) k_batch_scan(const BatchArgs B) {
     const int i = base + tid;
     const bool run = running(i);
     if (run) atomicAdd(&running_s, 1);
+    // evaluated this sweep unless carried over from a pause last sweep
+    if (run && !B.items[i].paused)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&B.bs->rule_regions),
+                (unsigned long long)B.items[i].n);
     block_incl_scan(run ? B.items[i].n : 0, wsum, &tot);
     R += tot;
   }
@@ -444,6 +448,8 @@ __global__ void __launch_bounds__(kSegBlock) k_batch_scan(const BatchArgs B) {
           it.iters -= 1;
           it.regions -= it.n;
           atomicAdd(&B.bs->pauses, 1);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&B.bs->carried_regions),
+                    (unsigned long long)it.n);
         } else {
           size = 2 * it.n_split;
           it.I_ret = __dadd_rn(it.I_ret, it.ret_i);
@@ -614,6 +620,7 @@ __global__ void k_batch_advance(const BatchArgs B) {
   BatchState* bs = B.bs;
   const int used = bs->lanes;
   bs->lane_sweeps[used == 128 ? 3 : (used == 32 ? 2 : (used == 4 ? 1 : 0))] += 1;
+  bs->list_regions += bs->n_total;
   bs->n_total = bs->n_next;
   bs->n_tiles = bs->n_tiles_next;
   bs->parity ^= 1;

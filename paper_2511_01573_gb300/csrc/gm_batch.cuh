@@ -57,6 +57,10 @@ struct BatchState {
   long long n_tiles;       // tiles of the current list (kSegTile regions, one integral each)
   long long n_tiles_next;  // tiles of the next list
   long long fam_off[2][8]; // first region of each family in either list; [p][7] = length
+  long long rule_regions;     // regions the rule kernels evaluated (work later
+                              // dropped by evictions included)
+  long long carried_regions;  // regions of paused integrals carried over unchanged
+  long long list_regions;     // sum over sweeps of the list length
 };
 
 // The per-integral sweep kernels work on tiles of kSegTile consecutive

@@ -598,6 +598,134 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
   o.kbest = kbest;
 }
 
+// Node-wise evaluation (GMQ_EVAL_NODEWISE): the same class sums and
+// fourth-difference argmax with f evaluated at every node from its
+// coordinates, d operations per node for the inner chain, as an integrand
+// without the separable form would be.  tab(row, j) is the region's node
+// coordinate on axis j for XRow `row`; pairs[p] = (j << 8) | k for the p-th
+// pair j < k of dimension d; fv points at the region's column of a
+// [4d + 1] x fvs scratch array (T > 1 only).
+template <int FAM, int T, class PT, class Tab>
+__device__ __forceinline__ void region_sums64_nodewise(const PT& P, int d,
+                                                       const unsigned short* pairs, const Tab& tab,
+                                                       double* fv, int fvs, double ratio,
+                                                       RegionSums& o) {
+  const int lane = (T == 1) ? 0 : (int)(threadIdx.x & (unsigned)(T - 1));
+  const unsigned mask = group_mask<T>();
+  const int na = 1 + 4 * d;  // centre and axis nodes
+  double f0 = 0.0, dbest = -1.0, s2, s3;
+  int kbest = 0;
+  if (T == 1) {
+    PairTree t2, t3;
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+    for (int i = 0; i < na; ++i) {
+      int k1 = -1, r1 = kXC, w = 0;
+      if (i > 0) {
+        k1 = (i - 1) >> 2;
+        w = (i - 1) & 3;
+        r1 = kXP2 + w;
+      }
+      const double v = Family<FAM>::template eval<double>(
+          P, d, [&](int j) -> double { return tab(j == k1 ? r1 : kXC, j); });
+      if (i == 0) {
+        f0 = v;
+        continue;
+      }
+      if (w < 2)
+        t2.push(v);
+      else
+        t3.push(v);
+      if (w == 0) {
+        q0 = v;
+      } else if (w == 1) {
+        q1 = v;
+      } else if (w == 2) {
+        q2 = v;
+      } else {
+        const double two_f0 = __dmul_rn(2.0, f0);
+        const double t1 = __dsub_rn(__dadd_rn(q0, q1), two_f0);
+        const double tt = __dsub_rn(__dadd_rn(q2, v), two_f0);
+        const double D = fabs(__dsub_rn(t1, __dmul_rn(ratio, tt)));
+        if (D > dbest) {
+          dbest = D;
+          kbest = k1;
+        }
+      }
+    }
+    bool pr;
+    s2 = t2.flush(pr);
+    s3 = t3.flush(pr);
+  } else {
+    for (int i = lane; i < na; i += T) {
+      int k1 = -1, r1 = kXC, w = 0;
+      if (i > 0) {
+        k1 = (i - 1) >> 2;
+        w = (i - 1) & 3;
+        r1 = kXP2 + w;
+      }
+      const double v = Family<FAM>::template eval<double>(
+          P, d, [&](int j) -> double { return tab(j == k1 ? r1 : kXC, j); });
+      fv[(i == 0 ? 4 * d : w * d + k1) * fvs] = v;
+    }
+    group_sync<T>(mask);
+    f0 = fv[4 * d * fvs];
+    const double two_f0 = __dmul_rn(2.0, f0);
+    for (int k = lane; k < d; k += T) {
+      const double t1 = __dsub_rn(__dadd_rn(fv[(0 * d + k) * fvs], fv[(1 * d + k) * fvs]), two_f0);
+      const double tt = __dsub_rn(__dadd_rn(fv[(2 * d + k) * fvs], fv[(3 * d + k) * fvs]), two_f0);
+      const double D = fabs(__dsub_rn(t1, __dmul_rn(ratio, tt)));
+      if (D > dbest) {
+        dbest = D;
+        kbest = k;
+      }
+    }
+    // argmax over the lanes: larger D wins, the lower axis on ties (for
+    // T = 128 every axis k < d <= 16 sits in warp 0, which holds the answer
+    // for lane 0, the only lane that uses it)
+    constexpr int W = T < 32 ? T : 32;
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+      const double od = __shfl_xor_sync(mask, dbest, off, W);
+      const int ok = __shfl_xor_sync(mask, kbest, off, W);
+      if (od > dbest || (od == dbest && ok < kbest)) {
+        dbest = od;
+        kbest = ok;
+      }
+    }
+    // classes 2 and 3 hold 2d <= 32 nodes: one node per chunk
+    PairTree t2, t3;
+    const int p0 = lane_first_chunk<T>(lane), p1 = min(p0 + kChunks / T, 2 * d);
+    for (int p = p0; p < p1; ++p) {
+      t2.push(fv[((p & 1) * d + (p >> 1)) * fvs]);
+      t3.push(fv[((2 + (p & 1)) * d + (p >> 1)) * fvs]);
+    }
+    bool pr2, pr3;
+    const double x2 = t2.flush(pr2), x3 = t3.flush(pr3);
+    s2 = lanes_tree<T>(x2, pr2, mask);
+    s3 = lanes_tree<T>(x3, pr3, mask);
+  }
+  // class 4: c +- lambda4 h_j e_j +- lambda4 h_k e_k, j < k
+  o.s4 = class_sum<T>(2 * d * (d - 1), lane, mask, [&](int q) -> double {
+    const unsigned pr = pairs[q >> 2];
+    const int kj = (int)(pr >> 8), kk = (int)(pr & 255u);
+    const int rj = (q & 2) ? kXM3 : kXP3, rk = (q & 1) ? kXM3 : kXP3;
+    return Family<FAM>::template eval<double>(
+        P, d, [&](int j) -> double { return tab(j == kj ? rj : (j == kk ? rk : kXC), j); });
+  });
+  // class 5: c + lambda5 (sigma o h) for the 2^d sign patterns
+  o.s5 = class_sum<T>(1 << d, lane, mask, [&](int m) -> double {
+    return Family<FAM>::template eval<double>(P, d, [&](int j) -> double {
+      return tab((((unsigned)m >> j) & 1u) ? kXM5 : kXP5, j);
+    });
+  });
+  o.s1 = f0;
+  o.s2 = s2;
+  o.s3 = s3;
+  o.f0 = f0;
+  o.dbest = dbest;
+  o.kbest = kbest;
+}
+
 // Null-rule error estimate of a region from its class sums (the heuristic
 // of Berntsen, Espelid & Genz 1991 that the paper's Sec. 2 cites; constants
 // and combination as the library reads it).  nw: 4 x 5 per-node weights of

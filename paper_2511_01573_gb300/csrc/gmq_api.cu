@@ -75,6 +75,7 @@ struct gmq_context {
   long long tuned_t4[GMQ_MAX_DIM + 1] = {};
   long long tuned_t32[GMQ_MAX_DIM + 1] = {};
   gmq_batch_info last_batch = {};
+  int eval_mode = GMQ_EVAL_SEPARABLE;     // gmq_set_eval_mode
   cudaStream_t capture_stream = nullptr;  // private stream for graph capture
   // kernel timing (gmq_profile_*)
   bool prof_on = false;
@@ -788,6 +789,12 @@ gmq_status gmq_set_pool(gmq_context* ctx, void* dev_ptr, size_t bytes) {
   return GMQ_OK;
 }
 
+gmq_status gmq_set_eval_mode(gmq_context* ctx, int32_t mode) {
+  if (!ctx || (mode != GMQ_EVAL_SEPARABLE && mode != GMQ_EVAL_NODEWISE)) return GMQ_ERR_INVALID;
+  ctx->eval_mode = mode;
+  return GMQ_OK;
+}
+
 gmq_status gmq_pool_bytes(int32_t dim, int64_t max_regions, int32_t flags, size_t* bytes) {
   if (!bytes || dim < 1 || dim > GMQ_MAX_DIM || max_regions < 1 || max_regions > kMaxRegions ||
       (flags & ~GMQ_KEEP_PARTITION))
@@ -944,6 +951,7 @@ gmq_status gmq_integrate(gmq_context* ctx, const gmq_problem* prob, const gmq_op
     A.axis = (uint8_t*)(base + L.axis);
     A.P = P;
     A.R = R;
+    A.nodewise = ctx->eval_mode == GMQ_EVAL_NODEWISE ? 1 : 0;
     prof_begin(ctx, kKRule);
     if (gk) {
       GkArgs GA;
@@ -1099,6 +1107,7 @@ gmq_status gmq_eval_rule(gmq_context* ctx, const gmq_problem* prob, int32_t prec
   A.axis = d_axis;
   A.P = fam_params(prob);
   A.R = rule_const(prob->dim, prob->lo, prob->hi, estimator);
+  A.nodewise = ctx->eval_mode == GMQ_EVAL_NODEWISE ? 1 : 0;
   const int T = choose_lanes(lanes, n, prob->dim, ctx->sm_count, precision);
   prof_begin(ctx, kKRule);
   GMQ_CK(launch_rule(prob->family, precision, T, A, ctx->stream));
@@ -1135,6 +1144,7 @@ gmq_status gmq_eval_rule_gk(gmq_context* ctx, const gmq_problem* prob, int64_t n
   G.A.axis = d_axis;
   G.A.P = fam_params(prob);
   G.A.R = rule_const(prob->dim, prob->lo, prob->hi);
+  G.A.nodewise = 0;
   G.K = ctx->gk_dev;
   prof_begin(ctx, kKRule);
   GMQ_CK(launch_rule_gk(prob->family, G, ctx->stream));
@@ -1827,6 +1837,9 @@ gmq_status gmq_integrate_batch(gmq_context* ctx, int32_t count, const gmq_proble
   info.sweeps = hs.sweep;
   info.pauses = hs.pauses;
   info.evictions = hs.evictions;
+  info.rule_regions = hs.rule_regions;
+  info.carried_regions = hs.carried_regions;
+  info.list_regions = hs.list_regions;
   for (int m = 0; m < 4; ++m) info.lane_sweeps[m] = hs.lane_sweeps[m];
   ctx->last_batch = info;
   for (int32_t k = 0; k < count; ++k) {

@@ -53,6 +53,7 @@ struct RuleArgs {
   uint8_t* axis;
   FamParams P;
   RuleConst R;
+  int32_t nodewise;  // FP64 Genz-Malik kernels: 1 = evaluate f node by node (GMQ_EVAL_NODEWISE)
 };
 
 // Device-side state of one integration, updated by the sweep kernels and

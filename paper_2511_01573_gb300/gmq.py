@@ -26,6 +26,7 @@ ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5
 FP64, MIXED = 0, 1
 VOLUME_SHARE, LOCAL_REL = 0, 1
 EST_EMBEDDED, EST_NULL_RULES = 0, 1
+EVAL_SEPARABLE, EVAL_NODEWISE = 0, 1
 
 _dp = C.POINTER(C.c_double)
 
@@ -66,7 +67,8 @@ EXPORTS = ("gmq_create", "gmq_destroy", "gmq_set_stream", "gmq_set_pool", "gmq_p
            "gmq_tree_sum", "gmq_partition", "gmq_profile_enable", "gmq_profile_reset",
            "gmq_profile_read", "gmq_tree_sum_noalloc", "gmq_partition_copy", "gmq_rule_grad",
            "gmq_integrate_batch", "gmq_last_batch_info", "gmq_eval_rule_gk", "gmq_gk_table",
-           "gmq_math_exp", "gmq_math_rcp", "gmq_math_cos", "gmq_probe_fp_rate", "gmq_null_rule_table")
+           "gmq_math_exp", "gmq_math_rcp", "gmq_math_cos", "gmq_probe_fp_rate", "gmq_null_rule_table",
+           "gmq_set_eval_mode")
 
 KEEP_PARTITION = 1
 BATCH_HOST_LOOP = 2
@@ -81,7 +83,9 @@ class BatchInfo(C.Structure):
                 ("evictions", C.c_int32), ("forced_lanes", C.c_int32),
                 ("lanes_t1", C.c_int64), ("lanes_t4", C.c_int64), ("lanes_t32", C.c_int64),
                 ("lane_sweeps", C.c_int32 * 4),
-                ("tune_n", C.c_int64 * 5), ("tune_ms", (C.c_double * 4) * 5)]
+                ("tune_n", C.c_int64 * 5), ("tune_ms", (C.c_double * 4) * 5),
+                ("rule_regions", C.c_int64), ("carried_regions", C.c_int64),
+                ("list_regions", C.c_int64)]
 
 ERR_TOO_LARGE = -6
 NOALLOC_MAX_N = 1 << 23
@@ -131,6 +135,7 @@ def lib():
         "gmq_destroy": [vp],
         "gmq_set_stream": [vp, vp],
         "gmq_set_pool": [vp, vp, C.c_size_t],
+        "gmq_set_eval_mode": [vp, C.c_int32],
         "gmq_pool_bytes": [i32, i64, i32, C.POINTER(C.c_size_t)],
         "gmq_default_options": [C.POINTER(Options)],
         "gmq_integrate": [vp, C.POINTER(Problem), C.POINTER(Options), C.POINTER(Result)],
@@ -287,6 +292,12 @@ class Context:
         else:
             _check("gmq_set_pool", lib().gmq_set_pool(self.h, _dptr(tensor), tensor.numel()))
 
+    def set_eval_mode(self, mode):
+        """How the FP64 Genz-Malik kernels evaluate f at the nodes:
+        EVAL_SEPARABLE (per-axis terms once per region, the default) or
+        EVAL_NODEWISE (f from every node's coordinates)."""
+        _check("gmq_set_eval_mode", lib().gmq_set_eval_mode(self.h, int(mode)))
+
     def close(self):
         if getattr(self, "h", None):
             lib().gmq_destroy(self.h)
@@ -381,6 +392,9 @@ class Context:
                 "lanes_t1": int(info.lanes_t1), "lanes_t4": int(info.lanes_t4),
                 "lanes_t32": int(info.lanes_t32),
                 "lane_sweeps": list(info.lane_sweeps),
+                "rule_regions": int(info.rule_regions),
+                "carried_regions": int(info.carried_regions),
+                "list_regions": int(info.list_regions),
                 "tune": [{"n": int(info.tune_n[i]), "ms": list(info.tune_ms[i])}
                          for i in range(5) if info.tune_n[i] > 0]}
 

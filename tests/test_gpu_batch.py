@@ -115,9 +115,11 @@ def test_batch_against_oracle_sample(oracle, gpu_ctx):
 
 
 def test_batch_many_integrals_workload_sample(gpu_ctx):
-    """The first 256 of the 4096-integral workload (d ~ U{2..10}, four
+    """The first 128 of the 4096-integral workload (d ~ U{2..10}, four
     families, tolerance log-uniform in [1e-9, 1e-4]); every result equals
-    its single run."""
+    its single run.  The work counters add up: every sweep's list is
+    evaluated or carried over, and the evaluated regions are the results'
+    region counts plus the work evictions dropped."""
     probs = G.batched_problems(count=128)
     cap = 1 << 20
     # a pool far smaller than the problems' combined peak: problems wait,
@@ -125,6 +127,12 @@ def test_batch_many_integrals_workload_sample(gpu_ctx):
     res = gpu_ctx.integrate_batch(probs, max_regions=cap, pool_regions=1 << 22)
     info = gpu_ctx.last_batch_info()
     assert info["pauses"] + info["evictions"] > 0
+    assert info["list_regions"] == info["rule_regions"] + info["carried_regions"]
+    assert (info["carried_regions"] > 0) == (info["pauses"] > 0)
+    counted = sum(r.regions_evaluated for r in res)
+    assert counted <= info["rule_regions"]
+    if info["evictions"] == 0:
+        assert counted == info["rule_regions"]
     for p, r in list(zip(probs, res))[::8]:
         s = _single(gpu_ctx, p, cap)
         assert (r.status, r.regions_evaluated, r.integral) == (s.status, s.regions_evaluated,
