@@ -68,6 +68,8 @@ def parse():
                     help="report the other workloads at full size (d=3; d=12 FP64 against "
                          "mixed; the 4096 batched integrals; the 1024 gradient sets)")
     ap.add_argument("--seeds-d12", type=int, default=10)
+    ap.add_argument("--only", default="c1,c3,c4,c5",
+                    help="--all-configs: the workloads to run (c1, c3, c4, c5)")
     ap.add_argument("--grad-sets", type=int, default=1024)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--gk", action="store_true",
@@ -101,7 +103,7 @@ RULE_FP64_INST_D8 = {0: 6465.0, 1: 2524.0, 2: 4861.0, 3: 5002.0, 4: 4930.0}
 RULE_FP64_FLOPS_D8 = {0: 10133.0, 1: 3858.0, 2: 6123.0, 3: 7467.0, 4: 7395.0}
 RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
                        "gm_math_tables.cuh", "gmq_common.cuh")
-RULE_COUNTS_SHA16 = "12d05f8ab8086fe6"
+RULE_COUNTS_SHA16 = "6bb5b9ff12f26ffb"
 
 
 # FP32 work of the mixed rule kernel (k_rule_mixed_reg, one thread per
@@ -115,7 +117,7 @@ RULE_COUNTS_SHA16 = "12d05f8ab8086fe6"
 MIXED_FP32_OPS_D12 = {2: 116237.0, 3: 134179.0}
 MIXED_COUNTS_SOURCES = ("gm_rule_mixed.cuh", "gm_region32.cuh", "gm_region64.cuh",
                         "gmq_families.cuh", "gm_math_tables.cuh", "gmq_common.cuh")
-MIXED_COUNTS_SHA16 = "b26bbce2194aedb8"
+MIXED_COUNTS_SHA16 = "4eff0ad7419d8038"
 
 
 def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
@@ -131,7 +133,7 @@ def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
     return h.hexdigest()[:16]
 
 
-RULE_DRAM_BYTES_PER_REGION_D8 = 143.0
+RULE_DRAM_BYTES_PER_REGION_D8 = 142.7
 
 
 def mixed_roofline(ctx, stream, probe32):
@@ -776,112 +778,126 @@ def all_configs(args):
         print(json.dumps({key: val}), flush=True)
 
     rep = {}
-    # C1: product peak on [0,1]^3, a = 5, u = 1/2, tol 1e-6, cap 1e5
-    p = G.product_peak_d3()
-    ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=100000)
-    r, t = timed(lambda: ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=100000))
-    ex = (10 * math.atan(2.5)) ** 3
-    emit("product_peak_d3", {"s": t, "regions": r.regions_evaluated, "sweeps": r.iterations,
-                             "status": r.status, "error_estimate": r.error,
-                             "rel_err_vs_closed_form": abs(r.integral - ex) / ex})
-    # C3: d = 12 corner peak and Gaussian, FP64 against the mixed form
-    rows = []
-    for tol in (1e-4, 1e-5, 1e-6, 1e-7):
-        for fam in (G.CORNER_PEAK, G.GAUSSIAN):
-            for sd in range(1, args.seeds_d12 + 1):
-                a, u = G.seed_genz(sd, fam, 12, G.GENZ_TARGET_SUM[fam])
-                ex = _closed(fam, a, u)
-                r64, t64 = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=1 << 22))
-                rmx, tmx = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=1 << 22,
-                                                       precision=gmq.MIXED))
-                rows.append({"family": G.FAMILY_NAMES[fam], "seed": sd, "tol": tol,
-                             "fp64_s": t64, "mixed_s": tmx, "fp64_regions": r64.regions_evaluated,
-                             "mixed_regions": rmx.regions_evaluated, "fp64_status": r64.status,
-                             "mixed_status": rmx.status,
-                             "fp64_rel_err": abs(r64.integral - ex) / abs(ex),
-                             "mixed_rel_err": abs(rmx.integral - ex) / abs(ex),
-                             "mixed_rel_diff_vs_fp64": abs(rmx.integral - r64.integral)
-                             / abs(r64.integral)})
-    emit("d12_fp64_vs_mixed", rows)
-    # C4: the 4096 batched integrals, FP64 and mixed, batched and one by one
-    probs = G.batched_problems(count=4096)[: args.batch_count]
-    bcap = 1 << 22  # per problem
-    exact = [_closed(q.family, q.a, q.u) for q in probs]
+    only = set(args.only.split(","))
+    if "c1" in only:
+        # C1: product peak on [0,1]^3, a = 5, u = 1/2, tol 1e-6, cap 1e5
+        p = G.product_peak_d3()
+        ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=100000)
+        r, t = timed(lambda: ctx.integrate(p.family, p.a, p.u, p.rel_tol, max_regions=100000))
+        ex = (10 * math.atan(2.5)) ** 3
+        emit("product_peak_d3", {"s": t, "regions": r.regions_evaluated, "sweeps": r.iterations,
+                                 "status": r.status, "error_estimate": r.error,
+                                 "rel_err_vs_closed_form": abs(r.integral - ex) / ex})
+    if "c3" in only:
+        # C3: d = 12 corner peak and Gaussian, FP64 against the mixed form
+        rows = []
+        for tol in (1e-4, 1e-5, 1e-6, 1e-7):
+            for fam in (G.CORNER_PEAK, G.GAUSSIAN):
+                for sd in range(1, args.seeds_d12 + 1):
+                    a, u = G.seed_genz(sd, fam, 12, G.GENZ_TARGET_SUM[fam])
+                    ex = _closed(fam, a, u)
+                    r64, t64 = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=1 << 22))
+                    rmx, tmx = timed(lambda: ctx.integrate(fam, a, u, tol, max_regions=1 << 22,
+                                                           precision=gmq.MIXED))
+                    rows.append({"family": G.FAMILY_NAMES[fam], "seed": sd, "tol": tol,
+                                 "fp64_s": t64, "mixed_s": tmx, "fp64_regions": r64.regions_evaluated,
+                                 "mixed_regions": rmx.regions_evaluated, "fp64_status": r64.status,
+                                 "mixed_status": rmx.status,
+                                 "fp64_rel_err": abs(r64.integral - ex) / abs(ex),
+                                 "mixed_rel_err": abs(rmx.integral - ex) / abs(ex),
+                                 "mixed_rel_diff_vs_fp64": abs(rmx.integral - r64.integral)
+                                 / abs(r64.integral)})
+        emit("d12_fp64_vs_mixed", rows)
+    if "c4" in only:
+        # C4: the 4096 batched integrals, FP64 and mixed, batched and one by one
+        probs = G.batched_problems(count=4096)[: args.batch_count]
+        bcap = 1 << 22  # per problem
+        exact = [_closed(q.family, q.a, q.u) for q in probs]
 
-    def errs(res):
-        rel = [abs(x.integral - e) / abs(e) / q.rel_tol
-               for x, e, q in zip(res, exact, probs) if x.status == 0]
-        return {"converged": len(rel), "within_tol": sum(1 for v in rel if v <= 1.0),
-                "max_err_over_tol": max(rel) if rel else None,
-                "median_err_over_tol": statistics.median(rel) if rel else None}
+        def errs(res):
+            rel = [abs(x.integral - e) / abs(e) / q.rel_tol
+                   for x, e, q in zip(res, exact, probs) if x.status == 0]
+            fam = {}
+            for x, e, q in zip(res, exact, probs):
+                if x.status == 0:
+                    v = abs(x.integral - e) / abs(e) / q.rel_tol
+                    c = fam.setdefault(G.FAMILY_NAMES[q.family], [0, 0, 0.0])
+                    c[0] += 1
+                    c[1] += int(v <= 1.0)
+                    c[2] = max(c[2], float(v))
+            return {"converged": len(rel), "within_tol": sum(1 for v in rel if v <= 1.0),
+                    "max_err_over_tol": max(rel) if rel else None,
+                    "median_err_over_tol": statistics.median(rel) if rel else None,
+                    "by_family_converged_within_max": fam}
 
-    out = {"problems": len(probs)}
-    for name, prec in (("fp64", gmq.FP64), ("mixed", gmq.MIXED)):
-        ctx.integrate_batch(probs[:16], max_regions=bcap, precision=prec)
-        res, tb = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27,
-                                                    precision=prec))
-        info = ctx.last_batch_info()
-        # one call per integral; the mixed batch runs one lane per region, so
-        # the single mixed calls that it reproduces bit for bit do too
-        lanes = 1 if prec == gmq.MIXED else 0
-        seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
-                                               precision=prec, lanes=lanes) for q in probs])
-        st = {}
-        for x in res:
-            st[str(x.status)] = st.get(str(x.status), 0) + 1
-        out[name] = {"batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
-                     "regions": sum(x.regions_evaluated for x in res), "statuses": st,
-                     "identical_to_single_runs": sum(
-                         1 for a, b in zip(seq, res)
-                         if a.integral == b.integral and a.regions_evaluated == b.regions_evaluated),
-                     "vs_closed_form": errs(res),
-                     "info": {k: info[k] for k in ("sweeps", "lane_sweeps", "rule_grid", "pauses",
-                                                   "evictions", "lanes_t1", "lanes_t4",
-                                                   "lanes_t32", "rule_regions",
-                                                   "carried_regions", "list_regions")}}
-        if name == "fp64":
-            fp64_res, fp64_seq_s = res, ts
-    out["mixed"]["speedup_vs_fp64_sequential"] = fp64_seq_s / out["mixed"]["batched_s"]
-    out["mixed"]["max_rel_diff_vs_fp64"] = max(
-        abs(m.integral - f.integral) / abs(f.integral) for m, f in zip(res, fp64_res)
-        if f.integral != 0.0)
-    emit("batch", out)
-    # C5: gradients of the d = 6 Gaussian over frozen partitions, tol 1e-8
-    sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
-    errs_g, errs_i, tf, tg, t_retry = [], [], 0.0, 0.0, 0.0
-    caps = (1 << 24, 1 << 26, 1 << 28)
-    needed = {c: 0 for c in caps}
-    for a, u in sets:
-        at = torch.tensor(a, requires_grad=True)
-        ut = torch.tensor(u, requires_grad=True)
-        # the final partition (retired leaves plus the last list) must fit in
-        # max_regions: sets that outgrow it run again with four times the room
-        for cap in caps:
-            w0 = time.perf_counter()
-            try:
-                I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx,
-                                                  max_regions=cap))
-                break
-            except RuntimeError:
-                torch.cuda.synchronize()
-                t_retry += time.perf_counter() - w0
-                if cap == caps[-1]:
-                    raise
-        needed[cap] += 1
-        _, t2 = timed(lambda: I.backward())
-        tf += t1
-        tg += t2
-        Iex, gex = _closed_gauss(a, u)
-        g = list(at.grad.numpy()) + list(ut.grad.numpy())
-        errs_g.append(max(abs(x - y) for x, y in zip(g, gex)) / max(abs(y) for y in gex))
-        errs_i.append(abs(float(I.detach()) - Iex) / abs(Iex))
-    emit("gaussian_d6_gradients", {
-        "sets": len(sets), "forward_s": tf, "adjoint_s": tg,
-        "attempts_without_room_s": t_retry,
-        "sets_by_partition_room": {f"2^{c.bit_length() - 1}": k for c, k in needed.items()},
-        "max_rel_grad_err_vs_closed_form": max(errs_g),
-        "median_rel_grad_err_vs_closed_form": statistics.median(errs_g),
-        "max_rel_integral_err_vs_closed_form": max(errs_i)})
+        out = {"problems": len(probs)}
+        for name, prec in (("fp64", gmq.FP64), ("mixed", gmq.MIXED)):
+            ctx.integrate_batch(probs[:16], max_regions=bcap, precision=prec)
+            res, tb = timed(lambda: ctx.integrate_batch(probs, max_regions=bcap, pool_regions=1 << 27,
+                                                        precision=prec))
+            info = ctx.last_batch_info()
+            # one call per integral; the mixed batch runs one lane per region, so
+            # the single mixed calls that it reproduces bit for bit do too
+            lanes = 1 if prec == gmq.MIXED else 0
+            seq, ts = timed(lambda: [ctx.integrate(q.family, q.a, q.u, q.rel_tol, max_regions=bcap,
+                                                   precision=prec, lanes=lanes) for q in probs])
+            st = {}
+            for x in res:
+                st[str(x.status)] = st.get(str(x.status), 0) + 1
+            out[name] = {"batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
+                         "regions": sum(x.regions_evaluated for x in res), "statuses": st,
+                         "identical_to_single_runs": sum(
+                             1 for a, b in zip(seq, res)
+                             if a.integral == b.integral and a.regions_evaluated == b.regions_evaluated),
+                         "vs_closed_form": errs(res),
+                         "info": {k: info[k] for k in ("sweeps", "lane_sweeps", "rule_grid", "pauses",
+                                                       "evictions", "lanes_t1", "lanes_t4",
+                                                       "lanes_t32", "rule_regions",
+                                                       "carried_regions", "list_regions")}}
+            if name == "fp64":
+                fp64_res, fp64_seq_s = res, ts
+        out["mixed"]["speedup_vs_fp64_sequential"] = fp64_seq_s / out["mixed"]["batched_s"]
+        out["mixed"]["max_rel_diff_vs_fp64"] = max(
+            abs(m.integral - f.integral) / abs(f.integral) for m, f in zip(res, fp64_res)
+            if f.integral != 0.0)
+        emit("batch", out)
+    if "c5" in only:
+        # C5: gradients of the d = 6 Gaussian over frozen partitions, tol 1e-8
+        sets = G.gaussian_grad_sets(count=1024, dim=6)[: args.grad_sets]
+        errs_g, errs_i, tf, tg, t_retry = [], [], 0.0, 0.0, 0.0
+        caps = (1 << 24, 1 << 26, 1 << 28)
+        needed = {c: 0 for c in caps}
+        for a, u in sets:
+            at = torch.tensor(a, requires_grad=True)
+            ut = torch.tensor(u, requires_grad=True)
+            # the final partition (retired leaves plus the last list) must fit in
+            # max_regions: sets that outgrow it run again with four times the room
+            for cap in caps:
+                w0 = time.perf_counter()
+                try:
+                    I, t1 = timed(lambda: AG.integral(at, ut, rel_tol=1e-8, context=ctx,
+                                                      max_regions=cap))
+                    break
+                except RuntimeError:
+                    torch.cuda.synchronize()
+                    t_retry += time.perf_counter() - w0
+                    if cap == caps[-1]:
+                        raise
+            needed[cap] += 1
+            _, t2 = timed(lambda: I.backward())
+            tf += t1
+            tg += t2
+            Iex, gex = _closed_gauss(a, u)
+            g = list(at.grad.numpy()) + list(ut.grad.numpy())
+            errs_g.append(max(abs(x - y) for x, y in zip(g, gex)) / max(abs(y) for y in gex))
+            errs_i.append(abs(float(I.detach()) - Iex) / abs(Iex))
+        emit("gaussian_d6_gradients", {
+            "sets": len(sets), "forward_s": tf, "adjoint_s": tg,
+            "attempts_without_room_s": t_retry,
+            "sets_by_partition_room": {f"2^{c.bit_length() - 1}": k for c, k in needed.items()},
+            "max_rel_grad_err_vs_closed_form": max(errs_g),
+            "median_rel_grad_err_vs_closed_form": statistics.median(errs_g),
+            "max_rel_integral_err_vs_closed_form": max(errs_i)})
     if args.gk:
         # the tensor-product Gauss-Kronrod rule against Genz-Malik, d = 2..6
         gk_rows = []

@@ -327,10 +327,6 @@ __global__ void __launch_bounds__(kSegBlock) k_batch_scan(const BatchArgs B) {
     const int i = base + tid;
     const bool run = running(i);
     if (run) atomicAdd(&running_s, 1);
-    // evaluated this sweep unless carried over from a pause last sweep
-    if (run && !B.items[i].paused)
-      atomicAdd(reinterpret_cast<unsigned long long*>(&B.bs->rule_regions),
-                (unsigned long long)B.items[i].n);
     block_incl_scan(run ? B.items[i].n : 0, wsum, &tot);
     R += tot;
   }
@@ -448,7 +444,7 @@ __global__ void __launch_bounds__(kSegBlock) k_batch_scan(const BatchArgs B) {
           it.iters -= 1;
           it.regions -= it.n;
           atomicAdd(&B.bs->pauses, 1);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&B.bs->carried_regions),
+          atomicAdd(reinterpret_cast<unsigned long long*>(&B.bs->carried_next),
                     (unsigned long long)it.n);
         } else {
           size = 2 * it.n_split;
@@ -620,7 +616,12 @@ __global__ void k_batch_advance(const BatchArgs B) {
   BatchState* bs = B.bs;
   const int used = bs->lanes;
   bs->lane_sweeps[used == 128 ? 3 : (used == 32 ? 2 : (used == 4 ? 1 : 0))] += 1;
+  // the current list's regions were evaluated unless carried over
   bs->list_regions += bs->n_total;
+  bs->rule_regions += bs->n_total - bs->carried_cur;
+  bs->carried_regions += bs->carried_next;
+  bs->carried_cur = bs->carried_next;
+  bs->carried_next = 0;
   bs->n_total = bs->n_next;
   bs->n_tiles = bs->n_tiles_next;
   bs->parity ^= 1;

@@ -61,6 +61,8 @@ struct BatchState {
                               // dropped by evictions included)
   long long carried_regions;  // regions of paused integrals carried over unchanged
   long long list_regions;     // sum over sweeps of the list length
+  long long carried_cur;      // regions of the current list carried over (not evaluated)
+  long long carried_next;     // regions this sweep's scan carries into the next list
 };
 
 // The per-integral sweep kernels work on tiles of kSegTile consecutive

@@ -130,36 +130,29 @@ __device__ __forceinline__ void region_mixed_flat(const PT& P, int d, const unsi
   o.kbest = kbest;
 }
 
-// Dimension D known at compile time (3 <= D <= 16), one thread per region,
-// everything in registers.  The integrand's separable form (SepF<FAM>: f =
-// g(S), S = base (+) phi_0(x_0) (+) ... (+) phi_{D-1}(x_{D-1})) is used as
-// in the FP64 kernels: phi at the 7 D coordinate values of the region once,
-// and each node's S from one combine of per-axis terms and partial chains
-// (FP32):
-//   centre            S = base (+) suf_0;  suf_k = phi_k(c) (+) suf_{k+1}
-//   axis node k       S = (pre_k (+) phi_k(x)) (+) suf_{k+1};
-//                     pre_k = base (+) phi_0(c) (+) ... (+) phi_{k-1}(c)
-//   pair node j < k   S = ((pre_j (+) phi_j(x_j)) (+) mid_jk) (+)
-//                         (phi_k(x_k) (+) suf_{k+1})
-//   class-5 node m    S = A[m_A] (+) (B[m_B] (+) C[m_C]) over the axis
-//                     groups [0, 4), [4, 8), [8, D) (fewer for small D).
-// Every node is evaluated together with its partner (paired FP32
-// instructions: g2, and the last combine), the partner being the node that
-// differs from it in one coordinate only: the two signs of +-lambda2 e_k
-// and of +-lambda3 e_k; for a pair j < k, the two signs on axis k with the
-// same sign on axis j; in the last class, the two signs on axis 0.  The
-// class sums add the node values one by one in definition order (sign
-// patterns in ascending order, even and odd patterns in two accumulators).
-// Loops whose bodies hold the integrand run over the pair's first axis and
-// over the sign-pattern blocks at run time, which keeps the kernel's code
-// small enough for the instruction cache.  Pf holds the FP32 parameters (read once
-// into registers); tab(row, j) is the FP32 node coordinate.
+// Dimension D known at compile time (3 <= D <= 16).  Every node is
+// evaluated together with its partner in one paired FP32 evaluation
+// (Family2::eval2), the partner being the node that differs from it in one
+// coordinate only: the two signs of +-lambda2 e_k and of +-lambda3 e_k; for
+// a pair j < k, the two signs on axis k with the same sign on axis j; in the
+// sign-pattern class, the two signs on axis 0.  The nodes of classes 1-4 are
+// formed from the centre held in registers and the one or two coordinates
+// they move (read from the table), with the moved axis k known at compile
+// time (unrolled over k, the pair's first axis j in a loop).  The 2^D
+// sign-pattern nodes are walked in Gray-code order over a register-resident
+// node vector: consecutive patterns differ in one coordinate, which moves
+// between c_k + l5 h_k and c_k - l5 h_k by XOR-ing the two FP32 bit
+// patterns.  In an aligned group of eight patterns the coordinates that
+// change are axes 0, 1, 0, 2, 0, 1, 0, so the group is four axis-0 pairs,
+// with axes 1, 2, 1 stepping between them; the axis changed on entering the
+// group (>= 3) is picked with a predicated select.  Every class sum adds its
+// node values one by one in definition order (Gray-code order for the last
+// class), as the one-node-at-a-time walk did.  Pf holds the FP32 parameters
+// (read once into registers).
 template <int FAM, int D, class PT, class Tab>
 __device__ __forceinline__ void region_mixed_walk(const PT& Pf, const Tab& tab, double ratio,
                                                   RegionSums& o) {
-  static_assert(D >= 3 && D <= 16, "the register walk needs D >= 3");
-  using SF = SepF<FAM>;
-  constexpr bool kMul = Sep<FAM>::kMul, kBase = Sep<FAM>::kBase, kFlag = Sep<FAM>::kFlag;
+  static_assert(D >= 3 && D <= 16, "the Gray walk needs D >= 3");
   RegParams<D> rp;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -168,79 +161,27 @@ __device__ __forceinline__ void region_mixed_walk(const PT& Pf, const Tab& tab, 
     rp.b[j] = Pf.b[j];
   }
   rp.c0 = Pf.c0;
-  auto op = [](float x, float y) -> float {
-    if constexpr (kMul)
-      return __fmul_rn(x, y);
-    else
-      return __fadd_rn(x, y);
-  };
-  auto op2 = [](float2 x, float2 y) -> float2 {
-    if constexpr (kMul)
-      return __fmul2_rn(x, y);
-    else
-      return __fadd2_rn(x, y);
-  };
-  // discontinuous family: flag bits (x_j > u_j) of the centre, of
-  // c +- lambda3 h (+ in bits 0..15, - in 16..31) and of c +- lambda5 h
-  unsigned zc = 0u, z3 = 0u, z5 = 0u;
-  auto g2z = [&](float2 S, bool zx, bool zy) -> float2 {
-    float2 v = SF::g2(D, S);
-    if constexpr (kFlag) {
-      if (zx) v.x = 0.0f;
-      if (zy) v.y = 0.0f;
-    }
-    return v;
-  };
   Acc<float> S1, S2, S3, S4, S5;
   double dbest = -1.0;
   int kbest = 0;
-  float fc[D], suf[D];
+  float xc[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    const float xc = tab(kXC, j);
-    fc[j] = SF::phi(rp, j, xc);
-    if constexpr (kFlag) zc |= (unsigned)SF::flag(rp, j, xc) << j;
-  }
-  suf[D - 1] = fc[D - 1];
-#pragma unroll
-  for (int k = D - 2; k >= 0; --k) suf[k] = op(fc[k], suf[k + 1]);
+  for (int j = 0; j < D; ++j) xc[j] = tab(kXC, j);
   // class 1: the centre
-  {
-    const float sc = kBase ? op(SF::base(rp), suf[0]) : suf[0];
-    const float vc = g2z(make_float2(sc, sc), zc != 0u, zc != 0u).x;
-    S1.add(vc);
-    o.f0 = f2d_exact(vc);
-  }
-  const double two_f0 = __dmul_rn(2.0, o.f0);
-  // classes 2 and 3: per axis k the pairs (+l2, -l2) and (+l3, -l3), the
-  // fourth difference of axis k, and the pair-node prefixes L3 and
-  // suffixes R3 of the +-lambda3 values
-  float2 L3[D], R3[D];
-  float pre = kBase ? SF::base(rp) : 0.0f;
+  const float vc = Family<FAM>::template eval<float>(rp, D, [&](int j) -> float { return xc[j]; });
+  S1.add(vc);
+  const double f0 = f2d_exact(vc);
+  const double two_f0 = __dmul_rn(2.0, f0);
+  // classes 2 and 3: per axis k the pairs (+l2, -l2) and (+l3, -l3), and
+  // the fourth difference of axis k
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const bool hp = k > 0 || kBase;
-    const float2 x2 = make_float2(tab(kXP2, k), tab(kXM2, k));
-    const float2 x3 = make_float2(tab(kXP3, k), tab(kXM3, k));
-    const float2 ph2 = SF::phi2(rp, k, x2), ph3 = SF::phi2(rp, k, x3);
-    const float2 lp2 = hp ? op2(bc2(pre), ph2) : ph2;
-    const float2 lp3 = hp ? op2(bc2(pre), ph3) : ph3;
-    L3[k] = lp3;
-    R3[k] = k < D - 1 ? op2(ph3, bc2(suf[k + 1])) : ph3;
-    const float2 s2 = k < D - 1 ? op2(lp2, bc2(suf[k + 1])) : lp2;
-    const float2 s3 = k < D - 1 ? op2(lp3, bc2(suf[k + 1])) : lp3;
-    bool z2x = false, z2y = false, z3x = false, z3y = false;
-    if constexpr (kFlag) {
-      const bool zo = (zc & ~(1u << k)) != 0u;
-      const bool fp3 = SF::flag(rp, k, x3.x), fm3 = SF::flag(rp, k, x3.y);
-      z3 |= ((unsigned)fp3 << k) | ((unsigned)fm3 << (k + 16));
-      z2x = zo || SF::flag(rp, k, x2.x);
-      z2y = zo || SF::flag(rp, k, x2.y);
-      z3x = zo || fp3;
-      z3y = zo || fm3;
-    }
-    const float2 v2 = g2z(s2, z2x, z2y);
-    const float2 v3 = g2z(s3, z3x, z3y);
+    const float2 p2 = make_float2(tab(kXP2, k), tab(kXM2, k));
+    const float2 p3 = make_float2(tab(kXP3, k), tab(kXM3, k));
+    const float2 v2 = Family2<FAM>::eval2(
+        rp, D, [&](int j) -> float2 { return j == k ? p2 : bc2(xc[j]); });
+    const float2 v3 = Family2<FAM>::eval2(
+        rp, D, [&](int j) -> float2 { return j == k ? p3 : bc2(xc[j]); });
     S2.add(v2.x);
     S2.add(v2.y);
     S3.add(v3.x);
@@ -252,36 +193,20 @@ __device__ __forceinline__ void region_mixed_walk(const PT& Pf, const Tab& tab, 
       dbest = Dk;
       kbest = k;
     }
-    pre = hp ? op(pre, fc[k]) : fc[k];
   }
-  // class 4: pairs j < k, sign patterns ++, +-, -+, -- (the pairs on axis
-  // k); the first axis j in a loop (its prefix picked from the unrolled
-  // table), mid_jk grown by one term from (j, k - 1) to (j, k)
+  // class 4: pairs j < k, sign patterns ++, +-, -+, -- (the pairs on axis k)
   for (int j = 0; j < D - 1; ++j) {
-    float2 Lj = L3[0];
-#pragma unroll
-    for (int t = 1; t < D - 1; ++t)
-      if (t == j) Lj = L3[t];
-    float mid = 0.0f;
+    const float pj = tab(kXP3, j), mj = tab(kXM3, j);
 #pragma unroll
     for (int k = 1; k < D; ++k) {
       if (k > j) {
-        if (k > j + 1) mid = (k > j + 2) ? op(mid, fc[k - 1]) : fc[k - 1];
-        const float2 lm = (k > j + 1) ? op2(Lj, bc2(mid)) : Lj;
-        const float2 sa = op2(bc2(lm.x), R3[k]);
-        const float2 sb = op2(bc2(lm.y), R3[k]);
-        bool zax = false, zay = false, zbx = false, zby = false;
-        if constexpr (kFlag) {
-          const bool zo = (zc & ~((1u << j) | (1u << k))) != 0u;
-          const bool fjp = (z3 >> j) & 1u, fjm = (z3 >> (j + 16)) & 1u;
-          const bool fkp = (z3 >> k) & 1u, fkm = (z3 >> (k + 16)) & 1u;
-          zax = zo || fjp || fkp;
-          zay = zo || fjp || fkm;
-          zbx = zo || fjm || fkp;
-          zby = zo || fjm || fkm;
-        }
-        const float2 va = g2z(sa, zax, zay);
-        const float2 vb = g2z(sb, zbx, zby);
+        const float2 pk = make_float2(tab(kXP3, k), tab(kXM3, k));
+        const float2 va = Family2<FAM>::eval2(rp, D, [&](int i) -> float2 {
+          return i == k ? pk : bc2(i == j ? pj : xc[i]);
+        });
+        const float2 vb = Family2<FAM>::eval2(rp, D, [&](int i) -> float2 {
+          return i == k ? pk : bc2(i == j ? mj : xc[i]);
+        });
         S4.add(va.x);
         S4.add(va.y);
         S4.add(vb.x);
@@ -289,77 +214,50 @@ __device__ __forceinline__ void region_mixed_walk(const PT& Pf, const Tab& tab, 
       }
     }
   }
-  // class 5: the 2^D sign patterns m (bit j set: -lambda5 on axis j) in
-  // ascending order, S = A[m_A] (+) (B_q (+) C_q), m = m_A + 2^LA q: A (the
-  // chains over axes 0 .. LA-1) in registers, B_q and C_q (the chains over
-  // the next LB axes and the rest, picked by the bits of q) formed once per
-  // 2^LA patterns.  Patterns with even and odd m go to two accumulators.
-  constexpr int LA = D < 4 ? D : 4;
-  constexpr int LB = (D - LA) < 4 ? (D - LA) : 4;
-  constexpr int NH = D - LA > 0 ? D - LA : 1;
-  float A[1 << LA], p5h[NH], m5h[NH];
+  // class 5: Gray-code walk over the 2^D sign patterns in registers
+  float x[D];
+  unsigned tog[D];
 #pragma unroll
-  for (int i = 0; i < LA; ++i) {
-    const float xp = tab(kXP5, i), xm = tab(kXM5, i);
-    const float fp = SF::phi(rp, i, xp), fm = SF::phi(rp, i, xm);
-    if constexpr (kFlag)
-      z5 |= ((unsigned)SF::flag(rp, i, xp) << i) | ((unsigned)SF::flag(rp, i, xm) << (i + 16));
-    if (i == 0) {
-      A[0] = kBase ? op(SF::base(rp), fp) : fp;
-      A[1] = kBase ? op(SF::base(rp), fm) : fm;
-    } else {
-#pragma unroll
-      for (int t = 0; t < (1 << i); ++t) {
-        A[t + (1 << i)] = op(A[t], fm);
-        A[t] = op(A[t], fp);
-      }
-    }
+  for (int k = 0; k < D; ++k) {
+    const float p5 = tab(kXP5, k), m5 = tab(kXM5, k);
+    x[k] = p5;
+    tog[k] = __float_as_uint(p5) ^ __float_as_uint(m5);
   }
+  auto flip = [&](int k) { x[k] = __uint_as_float(__float_as_uint(x[k]) ^ tog[k]); };
+  // the pattern x and its axis-0 partner, in walk order
+  auto pair5 = [&]() {
+    const float2 x0 = make_float2(x[0], __uint_as_float(__float_as_uint(x[0]) ^ tog[0]));
+    const float2 v = Family2<FAM>::eval2(rp, D, [&](int i) -> float2 {
+      return i == 0 ? x0 : bc2(x[i]);
+    });
+    S5.add(v.x);
+    S5.add(v.y);
+  };
+  for (unsigned tb = 0; tb < (1u << D); tb += 8u) {
+    if (tb) {
+      const int jb = __ffs(tb) - 1;
 #pragma unroll
-  for (int i = 0; i < D - LA; ++i) {
-    const int j = LA + i;
-    const float xp = tab(kXP5, j), xm = tab(kXM5, j);
-    p5h[i] = SF::phi(rp, j, xp);
-    m5h[i] = SF::phi(rp, j, xm);
-    if constexpr (kFlag)
-      z5 |= ((unsigned)SF::flag(rp, j, xp) << j) | ((unsigned)SF::flag(rp, j, xm) << (j + 16));
-  }
-  const unsigned dmask = (1u << D) - 1u;
-  Acc<float> S5b;
-  for (int q = 0; q < (1 << (D - LA)); ++q) {
-    float bc = 0.0f;
-    if constexpr (D > LA) {
-      float bq = 0.0f, cq = 0.0f;
-#pragma unroll
-      for (int i = 0; i < D - LA; ++i) {
-        const float t = ((q >> i) & 1) ? m5h[i] : p5h[i];
-        if (i < LB)
-          bq = i == 0 ? t : op(bq, t);
-        else
-          cq = i == LB ? t : op(cq, t);
-      }
-      bc = D - LA > LB ? op(bq, cq) : bq;
+      for (int k = 3; k < D; ++k)
+        if (k == jb) flip(k);
     }
-#pragma unroll
-    for (int lo = 0; lo < (1 << LA); lo += 2) {
-      float2 S = make_float2(A[lo], A[lo + 1]);
-      if constexpr (D > LA) S = op2(S, bc2(bc));
-      bool zx = false, zy = false;
-      if constexpr (kFlag) {
-        const unsigned m = (unsigned)lo | ((unsigned)q << LA);
-        zx = ((((~m) & z5) | (m & (z5 >> 16))) & dmask) != 0u;
-        zy = ((((~(m + 1u)) & z5) | ((m + 1u) & (z5 >> 16))) & dmask) != 0u;
-      }
-      const float2 v = g2z(S, zx, zy);
-      S5.add(v.x);
-      S5b.add(v.y);
-    }
+    pair5();  // patterns 0, 1 of the group
+    flip(0);
+    flip(1);
+    pair5();  // 2, 3
+    flip(0);
+    flip(2);
+    pair5();  // 4, 5
+    flip(0);
+    flip(1);
+    pair5();  // 6, 7
+    flip(0);  // the group ends on pattern 7
   }
   o.s1 = S1.value();
   o.s2 = S2.value();
   o.s3 = S3.value();
   o.s4 = S4.value();
-  o.s5 = __dadd_rn(S5.value(), S5b.value());
+  o.s5 = S5.value();
+  o.f0 = f0;
   o.dbest = dbest;
   o.kbest = kbest;
 }

@@ -528,148 +528,6 @@ struct Sep<GMQ_POLY_SUMSQ11> {
   }
 };
 
-// The separable form in FP32 (mixed kernels' register walk): the same
-// per-axis terms and outer functions as Sep<FAM> (kMul, kBase, kFlag are
-// Sep<FAM>'s), scalar and paired.  phi2 runs phi's operations on both
-// lanes (each lane rounded as the scalar instruction rounds it) and g2 the
-// outer function of Family2<FAM>::eval2, so a lane's value does not depend
-// on which node it was paired with.
-template <int FAM>
-struct SepF;
-
-template <>
-struct SepF<GMQ_OSCILLATORY> {
-  template <class PT>
-  __device__ __forceinline__ static float base(const PT& P) { return P.c0; }
-  template <class PT>
-  __device__ __forceinline__ static float phi(const PT& P, int j, float x) {
-    return __fmul_rn(P.a[j], x);
-  }
-  template <class PT>
-  __device__ __forceinline__ static float2 phi2(const PT& P, int j, float2 x) {
-    return __fmul2_rn(bc2(P.a[j]), x);
-  }
-  __device__ __forceinline__ static float2 g2(int, float2 s) { return gm_cosf2(s); }
-};
-
-template <>
-struct SepF<GMQ_PRODUCT_PEAK> {
-  template <class PT>
-  __device__ __forceinline__ static float base(const PT&) { return 1.0f; }
-  template <class PT>
-  __device__ __forceinline__ static float phi(const PT& P, int j, float x) {
-    const float t = __fadd_rn(x, -P.u[j]);
-    return __fmaf_rn(t, t, P.b[j]);
-  }
-  template <class PT>
-  __device__ __forceinline__ static float2 phi2(const PT& P, int j, float2 x) {
-    const float2 t = __fadd2_rn(x, bc2(-P.u[j]));
-    return __ffma2_rn(t, t, bc2(P.b[j]));
-  }
-  __device__ __forceinline__ static float2 g2(int, float2 s) {
-    return make_float2(grcp(s.x), grcp(s.y));
-  }
-};
-
-template <>
-struct SepF<GMQ_CORNER_PEAK> {
-  template <class PT>
-  __device__ __forceinline__ static float base(const PT&) { return 1.0f; }
-  template <class PT>
-  __device__ __forceinline__ static float phi(const PT& P, int j, float x) {
-    return __fmul_rn(P.a[j], x);
-  }
-  template <class PT>
-  __device__ __forceinline__ static float2 phi2(const PT& P, int j, float2 x) {
-    return __fmul2_rn(bc2(P.a[j]), x);
-  }
-  __device__ __forceinline__ static float2 g2(int d, float2 s) {
-    // s^(d+1) by binary powering (as ipow), both lanes at once
-    int e = d + 1;
-    while (!(e & 1)) {
-      s = __fmul2_rn(s, s);
-      e >>= 1;
-    }
-    float2 r = s;
-    while (e >>= 1) {
-      s = __fmul2_rn(s, s);
-      if (e & 1) r = __fmul2_rn(r, s);
-    }
-    return make_float2(grcp(r.x), grcp(r.y));
-  }
-};
-
-template <>
-struct SepF<GMQ_GAUSSIAN> {
-  template <class PT>
-  __device__ __forceinline__ static float base(const PT&) { return 0.0f; }
-  template <class PT>
-  __device__ __forceinline__ static float phi(const PT& P, int j, float x) {
-    const float t = __fadd_rn(x, -P.u[j]);
-    return __fmul_rn(P.b[j], __fmul_rn(t, t));
-  }
-  template <class PT>
-  __device__ __forceinline__ static float2 phi2(const PT& P, int j, float2 x) {
-    const float2 t = __fadd2_rn(x, bc2(-P.u[j]));
-    return __fmul2_rn(bc2(P.b[j]), __fmul2_rn(t, t));
-  }
-  __device__ __forceinline__ static float2 g2(int, float2 s) {
-    return make_float2(gexp(-s.x), gexp(-s.y));
-  }
-};
-
-template <>
-struct SepF<GMQ_C0> {
-  template <class PT>
-  __device__ __forceinline__ static float base(const PT&) { return 0.0f; }
-  template <class PT>
-  __device__ __forceinline__ static float phi(const PT& P, int j, float x) {
-    return __fmul_rn(P.a[j], fabsf(__fadd_rn(x, -P.u[j])));
-  }
-  template <class PT>
-  __device__ __forceinline__ static float2 phi2(const PT& P, int j, float2 x) {
-    return __fmul2_rn(bc2(P.a[j]), abs2(__fadd2_rn(x, bc2(-P.u[j]))));
-  }
-  __device__ __forceinline__ static float2 g2(int, float2 s) {
-    return make_float2(gexp(-s.x), gexp(-s.y));
-  }
-};
-
-template <>
-struct SepF<GMQ_DISCONTINUOUS> {
-  template <class PT>
-  __device__ __forceinline__ static float base(const PT&) { return 0.0f; }
-  template <class PT>
-  __device__ __forceinline__ static float phi(const PT& P, int j, float x) {
-    return __fmul_rn(P.a[j], x);
-  }
-  template <class PT>
-  __device__ __forceinline__ static float2 phi2(const PT& P, int j, float2 x) {
-    return __fmul2_rn(bc2(P.a[j]), x);
-  }
-  template <class PT>
-  __device__ __forceinline__ static bool flag(const PT& P, int j, float x) { return x > P.u[j]; }
-  __device__ __forceinline__ static float2 g2(int, float2 s) {
-    return make_float2(gexp(s.x), gexp(s.y));
-  }
-};
-
-template <>
-struct SepF<GMQ_POLY_SUMSQ11> {
-  template <class PT>
-  __device__ __forceinline__ static float base(const PT&) { return 0.0f; }
-  template <class PT>
-  __device__ __forceinline__ static float phi(const PT&, int, float x) { return __fmul_rn(x, x); }
-  template <class PT>
-  __device__ __forceinline__ static float2 phi2(const PT&, int, float2 x) {
-    return __fmul2_rn(x, x);
-  }
-  __device__ __forceinline__ static float2 g2(int, float2 s) {
-    const float2 s2 = __fmul2_rn(s, s), s4 = __fmul2_rn(s2, s2), s8 = __fmul2_rn(s4, s4);
-    return __fmul2_rn(__fmul2_rn(s8, s2), s);
-  }
-};
-
 // An FP32 value as FP64, exactly, assembled from its bit pattern with
 // integer operations (the conversion instruction runs on the FP64 pipe,
 // which on this GPU issues at 1/64 of the FP32 rate): sign, exponent rebased
