@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--seeds", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-tol", action="store_true")
+    ap.add_argument("--no-nodewise-step", action="store_true",
+                    help="skip the comparison step with node-wise FP64 evaluation")
     ap.add_argument("--probe-rule", default=None,
                     help="profiling probe: family codes (e.g. 0,1,2,3,4); runs the rule "
                          "kernel 3 times per family on 2^20 random regions (--dim, default 8) "
@@ -1031,6 +1033,24 @@ def main():
     e2e_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     unprofiled_ms = e0.elapsed_time(e1)
+    # the same step with the FP64 rule evaluating f from every node's
+    # coordinates (GMQ_EVAL_NODEWISE): the integrand as a whole at every
+    # node, for comparison with the separable node sums of the timed steps
+    nodewise = None
+    if not args.no_nodewise_step:
+        ctx.set_eval_mode(gmq.EVAL_NODEWISE)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        nw_regions, _ = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.set_eval_mode(gmq.EVAL_SEPARABLE)
+        nw_ms = e0.elapsed_time(e1)
+        nodewise = {"value": nw_regions / (nw_ms / 1000.0), "unit": UNIT, "ms_per_step": nw_ms,
+                    "regions_per_step": nw_regions,
+                    "note": "one step of the same workload with GMQ_EVAL_NODEWISE (f from every "
+                            "node's coordinates), timed like the e2e step"}
     tt = time_to_tol(ctx, stream, 1e-6) if not args.no_time_to_tol else None
 
     ms_step = total_ms / args.steps
@@ -1088,6 +1108,7 @@ def main():
                    "parallelism": f"replicas{ws}"},
         "gpu_launches": launches,
         "kernels": prof,
+        "nodewise_step": nodewise,
         "unprofiled_step": {"ms": unprofiled_ms, "timed_ms_per_step": total_ms / args.steps,
                             "note": "the e2e step, per-launch timing events off"},
         "roofline": roof,
