@@ -101,11 +101,11 @@ CAP = 1 << 24
 # again (tests/test_bench_counts.py fails until they are), and until then
 # the roofline reports no fraction.  Family codes: 0 oscillatory, 1 product
 # peak, 2 corner peak, 3 Gaussian, 4 C0.
-RULE_FP64_INST_D8 = {0: 6465.0, 1: 2524.0, 2: 4861.0, 3: 5002.0, 4: 4930.0}
-RULE_FP64_FLOPS_D8 = {0: 10133.0, 1: 3858.0, 2: 6123.0, 3: 7467.0, 4: 7395.0}
+RULE_FP64_INST_D8 = {0: 5663.0, 1: 2524.0, 2: 4861.0, 3: 4200.0, 4: 4128.0}
+RULE_FP64_FLOPS_D8 = {0: 8930.0, 1: 3858.0, 2: 6123.0, 3: 6264.0, 4: 6192.0}
 RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
                        "gm_math_tables.cuh", "gmq_common.cuh")
-RULE_COUNTS_SHA16 = "6bb5b9ff12f26ffb"
+RULE_COUNTS_SHA16 = "7ed61cba9c42187b"
 
 
 # FP32 work of the mixed rule kernel (k_rule_mixed_reg, one thread per
@@ -119,7 +119,7 @@ RULE_COUNTS_SHA16 = "6bb5b9ff12f26ffb"
 MIXED_FP32_OPS_D12 = {2: 116237.0, 3: 134179.0}
 MIXED_COUNTS_SOURCES = ("gm_rule_mixed.cuh", "gm_region32.cuh", "gm_region64.cuh",
                         "gmq_families.cuh", "gm_math_tables.cuh", "gmq_common.cuh")
-MIXED_COUNTS_SHA16 = "4eff0ad7419d8038"
+MIXED_COUNTS_SHA16 = "e21368066797b384"
 
 
 def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):

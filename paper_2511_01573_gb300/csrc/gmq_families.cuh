@@ -20,29 +20,71 @@ struct SmemParams {
   Real c0;
 };
 
+// The integer n = round(x K) of a range reduction, and n as an FP64 value,
+// without FP64 instructions (the FP64 pipe issues at 1/64 of the FP32 rate):
+// x is rounded to FP32 by integer operations on its bit pattern
+// (round-to-nearest on the magnitude; |x| < 2^-126 gives 0), x K + 1.5 2^23
+// is one FP32 fused multiply-add whose rounding to an integer leaves
+// n + 2^22 in the low mantissa bits, and n is assembled into an FP64 bit
+// pattern from its leading-zero count.  Valid for |x K| < 2^21; the FP32
+// copy of x and of K put n within 0.5 + 2^-23 |x K| of x K, so for the
+// callers' ranges (|x K| < 2^18) the reduced argument exceeds its usual
+// bound by at most 3 %.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e < 897u) return 0.0f;
+  const unsigned b = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float((b + ((lo >> 28) & 1u)) | (hi & 0x80000000u));
+}
+
+__device__ __forceinline__ int round_mul_int(double x, float k) {
+  const float t = __fmaf_rn(d2f_bits(x), k, 12582912.0f);  // 1.5 * 2^23
+  return (int)(__float_as_uint(t) & 0x7fffffu) - 0x400000;
+}
+
+__device__ __forceinline__ double int_to_double_bits(int n) {
+  if (n == 0) return 0.0;
+  const unsigned a = n < 0 ? (unsigned)(-n) : (unsigned)n;
+  const int lz = __clz(a);
+  const unsigned m = (a << lz) << 1;  // the bits below the leading one, at the top
+  const unsigned hi = (n < 0 ? 0x80000000u : 0u) | ((unsigned)(1023 + 31 - lz) << 20) | (m >> 12);
+  return __hiloint2double((int)hi, (int)(m << 20));
+}
+
 // FP64 exponential by Tang's table-driven method (P. T. P. Tang, ACM TOMS
-// 15(2), 1989): x = (2048 m + j) ln2/2048 + r with |r| <= ln2/4096, so
+// 15(2), 1989): x = (2048 m + j) ln2/2048 + r with |r| <= ln2/4096 (up to
+// 3 % more for |x| < 64, where n = 2048 m + j comes from round_mul_int), so
 // exp(x) = 2^m 2^(j/2048) exp(r); exp(r) - 1 is its Taylor polynomial of
-// degree 3 (truncation below 3.5e-17), 2^(j/2048) comes from a 2048-entry
-// table (16 KB) and 2^m is added to the exponent field.  Eight FP64
-// instructions (the library exp measured ~16.6 in the rule kernels), within
-// about one ulp of the exact value (gm_math_tables.cuh holds the constants,
-// computed in 60-digit decimal arithmetic).  |x| >= 512 (which covers the
-// overflow and subnormal ranges) and NaN go to the library exp.
+// degree 3 (truncation below 4e-17), 2^(j/2048) comes from a 2048-entry
+// table (16 KB) and 2^m is added to the exponent field.  Six FP64
+// instructions for |x| < 64 and eight for 64 <= |x| < 512 (the library exp
+// measured ~16.6 in the rule kernels), within about one ulp of the exact
+// value (gm_math_tables.cuh holds the constants, computed in 60-digit
+// decimal arithmetic).  |x| >= 512 (which covers the overflow and subnormal
+// ranges) and NaN go to the library exp.
 __device__ __forceinline__ double gm_exp(double x) {
   // |x| < 512, tested on the high word (no FP64 compare)
-  if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40800000u) return exp(x);
-  const double shifter = 6755399441055744.0;  // 1.5 * 2^52: low word of t = nearest integer
-  const double t = fma(x, kExpInvL, shifter);
-  const int n = __double2loint(t);            // round(x * 2048 / ln2)
-  const double nd = __dsub_rn(t, shifter);    // the same integer as a double (exact)
+  const unsigned ahi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+  if (ahi >= 0x40800000u) return exp(x);
+  int n;
+  double nd;
+  if (ahi < 0x40500000u) {  // |x| < 64
+    n = round_mul_int(x, (float)kExpInvL);
+    nd = int_to_double_bits(n);
+  } else {
+    const double shifter = 6755399441055744.0;  // 1.5 * 2^52: low word of t = nearest integer
+    const double t = fma(x, kExpInvL, shifter);
+    n = __double2loint(t);                      // round(x * 2048 / ln2)
+    nd = __dsub_rn(t, shifter);                 // the same integer as a double (exact)
+  }
   double r = fma(-nd, kExpL1, x);             // exact (fused: x - n L1 fits 53 bits)
   r = fma(-nd, kExpL2, r);
   double q = fma(r, 1.0 / 6.0, 0.5);
   q = fma(q, r, 1.0);
   const double em1 = __dmul_rn(q, r);         // exp(r) - 1
   const double T = __ldg(&kExp2Tab[n & ((1 << kExpTabBits) - 1)]);
-  const double y = fma(T, em1, T);            // 2^(j/2048) exp(r), in [2^(-1/4096), 2^(4095/4096)]
+  const double y = fma(T, em1, T);            // 2^(j/2048) exp(r), in [2^(-1/2048), 2^(2049/2048)]
   const unsigned hi = (unsigned)__double2hiint(y) + ((unsigned)(n >> kExpTabBits) << 20);
   return __hiloint2double((int)hi, __double2loint(y));
 }
@@ -75,16 +117,25 @@ __device__ __forceinline__ float gexp(float x) { return expf(x); }
 // error is below 2^-70 for |x| < 2^16), |r| <= pi/256; cos(x) = C_j cos(r) -
 // S_j sin(r), j = n mod 256, with C_j = cos(j pi/128), S_j = sin(j pi/128)
 // from 256-entry tables, cos(r) - 1 and sin(r) by their Taylor polynomials of
-// degree 6 and 5 (truncation below 1e-17).  Thirteen FP64 instructions;
-// absolute error within a few units of 2^-53.  |x| >= 2^16 and non-finite x:
+// degree 6 and 5 (truncation below 1e-17).  Eleven FP64 instructions for
+// |x| < 1024 (n from round_mul_int), thirteen above; absolute error within
+// a few units of 2^-53.  |x| >= 2^16 and non-finite x:
 // the library cos.
 __device__ __forceinline__ double gm_cos(double x) {
   // |x| < 2^16, tested on the high word (no FP64 compare)
-  if (((unsigned)__double2hiint(x) & 0x7fffffffu) >= 0x40f00000u) return cos(x);
-  const double shifter = 6755399441055744.0;  // 1.5 * 2^52
-  const double t = fma(x, kCosInvQ, shifter);
-  const int n = __double2loint(t);            // round(x * 128 / pi)
-  const double nd = __dsub_rn(t, shifter);
+  const unsigned ahi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+  if (ahi >= 0x40f00000u) return cos(x);
+  int n;
+  double nd;
+  if (ahi < 0x40900000u) {  // |x| < 1024: n from round_mul_int
+    n = round_mul_int(x, (float)kCosInvQ);
+    nd = int_to_double_bits(n);
+  } else {
+    const double shifter = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(x, kCosInvQ, shifter);
+    n = __double2loint(t);                      // round(x * 128 / pi)
+    nd = __dsub_rn(t, shifter);
+  }
   double r = fma(-nd, kCosP1, x);             // exact
   r = fma(-nd, kCosP2, r);
   const double z = __dmul_rn(r, r);
