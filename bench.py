@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--probe-grad", default=None,
                     help="profiling probe: family codes; the adjoint kernel on 2^18 random "
                          "d=8 regions, three calls per family")
+    ap.add_argument("--eval-mode", type=int, default=0,
+                    help="with --probe-rule / --probe-grad: gmq_set_eval_mode (0 separable, "
+                         "1 node-wise)")
     ap.add_argument("--host-loop", action="store_true",
                     help="with --probe-batch: the host-driven sweep loop instead of the graph")
     ap.add_argument("--kernel-sweep", action="store_true",
@@ -105,7 +108,7 @@ RULE_FP64_INST_D8 = {0: 5663.0, 1: 2524.0, 2: 4861.0, 3: 4200.0, 4: 4128.0}
 RULE_FP64_FLOPS_D8 = {0: 8930.0, 1: 3858.0, 2: 6123.0, 3: 6264.0, 4: 6192.0}
 RULE_COUNTS_SOURCES = ("gm_rule.cuh", "gm_region64.cuh", "gmq_families.cuh",
                        "gm_math_tables.cuh", "gmq_common.cuh")
-RULE_COUNTS_SHA16 = "7ed61cba9c42187b"
+RULE_COUNTS_SHA16 = "bccec7300843b738"
 
 
 # FP32 work of the mixed rule kernel (k_rule_mixed_reg, one thread per
@@ -119,7 +122,7 @@ RULE_COUNTS_SHA16 = "7ed61cba9c42187b"
 MIXED_FP32_OPS_D12 = {2: 116237.0, 3: 134179.0}
 MIXED_COUNTS_SOURCES = ("gm_rule_mixed.cuh", "gm_region32.cuh", "gm_region64.cuh",
                         "gmq_families.cuh", "gm_math_tables.cuh", "gmq_common.cuh")
-MIXED_COUNTS_SHA16 = "e21368066797b384"
+MIXED_COUNTS_SHA16 = "fa462faf95c74eae"
 
 
 def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
@@ -135,7 +138,7 @@ def rule_source_fingerprint(files=RULE_COUNTS_SOURCES):
     return h.hexdigest()[:16]
 
 
-RULE_DRAM_BYTES_PER_REGION_D8 = 142.7
+RULE_DRAM_BYTES_PER_REGION_D8 = 142.6
 
 
 def mixed_roofline(ctx, stream, probe32):
@@ -505,6 +508,7 @@ def probe_rule(args):
     c = (lo + 0.5 * w).contiguous()
     h = (0.5 * w).contiguous()
     ctx = gmq.Context(0)
+    ctx.set_eval_mode(args.eval_mode)
     ctx.profile(True)
     for fam in (int(x) for x in args.probe_rule.split(",")):
         a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM.get(fam, 2.0))
@@ -522,8 +526,8 @@ def probe_rule(args):
 
 
 def probe_grad(args):
-    """The adjoint kernel (k_rule_grad: f and its 2d parameter derivatives at
-    every node) alone on 2^18 random sub-boxes of [0,1]^8 (17 output rows,
+    """The adjoint kernel (k_rule_grad_sep, or k_rule_grad with --eval-mode 1)
+    alone on 2^18 random sub-boxes of [0,1]^8 (17 output rows,
     about 70 MB of inputs and outputs), three calls per family, for ncu
     captures; prints the event-timed rate of the kernel and of the row sums."""
     import torch
@@ -536,6 +540,7 @@ def probe_grad(args):
     c = (lo + 0.5 * w).contiguous()
     h = (0.5 * w).contiguous()
     ctx = gmq.Context(0)
+    ctx.set_eval_mode(args.eval_mode)
     ctx.profile(True)
     for fam in (int(x) for x in args.probe_grad.split(",")):
         a, u = G.seed_genz(1, fam, d, G.GENZ_TARGET_SUM.get(fam, 2.0))

@@ -206,8 +206,11 @@ gmq_status gmq_set_pool(gmq_context *ctx, void *dev_ptr, size_t bytes);
  *   GMQ_EVAL_NODEWISE: f from each node's coordinates (d operations for S,
  *     then g), as an integrand without that form would be evaluated.
  * Both give every lane mapping the same bits; they differ from each other
- * only in the rounding order of S.  The mixed precision, the Gauss-Kronrod
- * rule, the batched form and the adjoint kernel do not depend on it. */
+ * only in the rounding order of S.  gmq_rule_grad follows it too: the
+ * separable mode forms the gradient from per-axis, per-coordinate sums of
+ * w g'(S) over the nodes, the node-wise mode differentiates f at every
+ * node.  The mixed precision, the Gauss-Kronrod rule and the batched form
+ * do not depend on it. */
 typedef enum gmq_eval_mode {
   GMQ_EVAL_SEPARABLE = 0,
   GMQ_EVAL_NODEWISE = 1

@@ -1914,6 +1914,7 @@ gmq_status gmq_rule_grad(gmq_context* ctx, const gmq_problem* prob, int64_t n,
   A.ldo = ldo;
   A.P = fam_params(prob);
   A.R = rule_const(d, prob->lo, prob->hi);
+  A.nodewise = ctx->eval_mode == GMQ_EVAL_NODEWISE ? 1 : 0;
   cudaStream_t strm = ctx->stream;
   cudaError_t e;
   prof_begin(ctx, kKRule);

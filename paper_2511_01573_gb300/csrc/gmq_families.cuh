@@ -150,6 +150,42 @@ __device__ __forceinline__ double gm_cos(double x) {
 }
 __device__ __forceinline__ double gcos(double x) { return gm_cos(x); }
 
+// sin(x) and cos(x) together (the adjoint of the oscillatory family): the
+// same reduction and polynomials as gm_cos, with sin(x) = S_j cos(r) +
+// C_j sin(r) two more fused multiply-adds; outside the fast range the
+// library's sincos.
+__device__ __forceinline__ void gm_sincos(double x, double* sn, double* cs) {
+  const unsigned ahi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+  if (ahi >= 0x40f00000u) {
+    sincos(x, sn, cs);
+    return;
+  }
+  int n;
+  double nd;
+  if (ahi < 0x40900000u) {
+    n = round_mul_int(x, (float)kCosInvQ);
+    nd = int_to_double_bits(n);
+  } else {
+    const double shifter = 6755399441055744.0;
+    const double t = fma(x, kCosInvQ, shifter);
+    n = __double2loint(t);
+    nd = __dsub_rn(t, shifter);
+  }
+  double r = fma(-nd, kCosP1, x);
+  r = fma(-nd, kCosP2, r);
+  const double z = __dmul_rn(r, r);
+  double c = fma(z, -1.0 / 720.0, 1.0 / 24.0);
+  c = fma(c, z, -0.5);
+  const double cm1 = __dmul_rn(c, z);
+  const double sp = fma(z, 1.0 / 120.0, -1.0 / 6.0);
+  const double sr = fma(__dmul_rn(r, z), sp, r);
+  const int j = n & ((1 << kCosTabBits) - 1);
+  const double C = __ldg(&kCosTab[j]), S = __ldg(&kSinTab[j]);
+  *cs = fma(-S, sr, fma(C, cm1, C));
+  *sn = fma(C, sr, fma(S, cm1, S));
+}
+
+
 // FP32 cosine of the mixed form's oscillatory integrand, by Cody and
 // Waite's reduction (W. J. Cody, W. Waite, Software Manual for the
 // Elementary Functions, 1980): x = n pi/2 + r, n the nearest integer to

@@ -121,3 +121,28 @@ def test_unknown_mode_rejected(gpu_ctx):
     from paper_2511_01573_gb300 import gmq
     with pytest.raises(gmq.GmqError):
         gpu_ctx.set_eval_mode(2)
+
+
+@pytest.mark.parametrize("fam", range(7))
+@pytest.mark.parametrize("d", [1, 2, 4, 6, 9, 12])
+def test_adjoint_modes_agree(oracle, gpu_ctx, fam, d):
+    """gmq_rule_grad: the separable per-row sums against the node-wise
+    derivatives and against the oracle on random boxes (1e-12 of the largest
+    component, as the adjoint tests hold the node-wise kernel)."""
+    from paper_2511_01573_gb300 import gmq
+    a, u = G.seed_uniform(13 + d, fam, d, 0.5, 3.0)
+    if fam == G.DISCONTINUOUS:
+        u = 0.3 + 0.6 * u
+    c, h = G.random_boxes(90 + d, {1: 400, 2: 300, 4: 120, 6: 60, 9: 12, 12: 4}[d], d)
+    go, qo = oracle.rule_grad(fam, a, u, c, h)
+    res = {}
+    try:
+        for mode in (gmq.EVAL_SEPARABLE, gmq.EVAL_NODEWISE):
+            gpu_ctx.set_eval_mode(mode)
+            res[mode] = gpu_ctx.rule_grad(fam, a, u, _soa(c), _soa(h))
+    finally:
+        gpu_ctx.set_eval_mode(gmq.EVAL_SEPARABLE)
+    scale = np.max(np.abs(go)) + abs(qo)
+    for mode, (g, q) in res.items():
+        assert abs(q - qo) <= 1e-12 * max(abs(qo), scale), (mode, q, qo)
+        assert np.all(np.abs(np.asarray(g) - go) <= 1e-12 * scale), (mode, g, go)
