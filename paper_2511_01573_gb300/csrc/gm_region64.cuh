@@ -292,7 +292,9 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
   double f0, s2, s3, dbest = -1.0;
   int kbest = 0;
   if constexpr (T == 1) {
-    // right to left: phi at the centre, R, suf (suf_{k+1} parked in L[k][0])
+    // right to left: phi at the centre, R, suf (suf_{k+1} parked in L[k][0],
+    // phi at c +- lambda3 h parked in the class-5 chain area, which holds at
+    // least 2d entries and is filled only after the axis nodes)
     double suf = 0.0;
     for (int k = d - 1; k >= 0; --k) {
       double c, h;
@@ -304,6 +306,8 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
         z3 |= ((unsigned)SF::flag(P, k, xp) << k) | ((unsigned)SF::flag(P, k, xm) << (k + 16));
       }
       W(Ly.phiC + k) = fc;
+      W(Ly.A + 2 * k) = fp;
+      W(Ly.A + 2 * k + 1) = fm;
       if (k == d - 1) {
         W(Ly.R + 2 * k) = fp;
         W(Ly.R + 2 * k + 1) = fm;
@@ -330,12 +334,20 @@ __device__ __forceinline__ void region_sums64(const PT& P, int d, const unsigned
       double q[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const double x = fma(lam_row(r), h, c);
-        const double ph = SF::phi(P, k, x);
+        double ph;
+        bool fx = false;
+        if (r < 2) {
+          const double x = fma(lam_row(r), h, c);
+          ph = SF::phi(P, k, x);
+          if constexpr (SF::kFlag) fx = SF::flag(P, k, x);
+        } else {
+          ph = W(Ly.A + 2 * k + (r - 2));  // parked by the first pass
+          if constexpr (SF::kFlag) fx = (z3 >> (k + 16 * (r - 2))) & 1u;
+        }
         const double lp = hp ? op(pre, ph) : ph;
         if (r >= 2) W(Ly.L + 2 * k + (r - 2)) = lp;  // after suf_{k+1} was read
         bool zero = false;
-        if constexpr (SF::kFlag) zero = ((zc & ~(1u << k)) != 0u) || SF::flag(P, k, x);
+        if constexpr (SF::kFlag) zero = ((zc & ~(1u << k)) != 0u) || fx;
         q[r] = fval(hs ? op(lp, sk) : lp, zero);
       }
       t2.push(q[0]);
